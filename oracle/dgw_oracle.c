@@ -1,0 +1,768 @@
+/*
+ * dgw_oracle.c -- plain, slow, FP64 CPU oracle for the WENO-stabilized RKDG method
+ * of Vedral, "Dissipative WENO stabilization of high-order discontinuous Galerkin
+ * methods for hyperbolic problems" (arXiv 2309.12019).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this
+ * file: only the tests, the smoke check and the CPU-baseline leg of the benchmark use
+ * it.  It shares no code, header, table or constant with the CUDA library.
+ *
+ * Everything is written from the definitions, element by element, in physical
+ * coordinates, with Gauss-Legendre quadrature and Legendre polynomials built from
+ * their three-term recurrence.  No sum factorisation, no precomputed operator
+ * matrices, no fusion.  Section / equation references are to the paper:
+ *
+ *   Sec. 2, Eq. (fesol)   modal expansion U_h^e = sum_j U_j phi_j (Legendre basis here;
+ *                          the paper notes the method does not depend on the basis)
+ *   Sec. 2, Eq. (weak2)   M dU/dt = R(U): volume term  int grad(phi_i).F(U_h)
+ *                          minus face term int phi_i H(U-,U+,n)
+ *   Sec. 2                local Lax-Friedrichs flux H_LLF with the exact maximal
+ *                          wave speed s+ = max_{w in [0,1]} |F'(w U- + (1-w) U+).n|
+ *   Sec. 2, Eq. (ssp)     optimal three-stage third-order SSP Runge-Kutta
+ *   Sec. 3, Eq. (lostab)  low-order stabilization  nu_e int grad(phi_i).grad(U_h)
+ *   Sec. 3, Eq. (visc)    nu_e = lambda_e h_e / (2p), lambda_e = ||F'(U_h)||_inf on K_e
+ *   Sec. 3, Eq. (astab)   adaptive stabilization  gamma_e nu_e int grad(phi_i).grad(U_h)
+ *   Sec. 4, Eq. (sensor)  gamma_e = min(1, ||U - U*||_e / ||U||_e)^q
+ *   Sec. 4                scaled Sobolev seminorm sum_{1<=|k|<=p} h^{2|k|-d} int |D^k v|^2
+ *   Sec. 4, Eq. (gensensor) thresholded sensor (gamma = 0 when the ratio is below b)
+ *   Sec. 4                HWENO reconstruction U* = sum_l w_l U_{h,l}
+ *   Sec. 5 (setup)        q = 1, linear weights 1 - m_e*0.01 (own cell), 0.01 (neighbours)
+ *
+ * Readings where the paper is silent (it defers the HWENO construction to another
+ * paper that is not reproduced in it):
+ *   R1 candidates: for every face neighbour K_l that exists, U_{h,l}^e is the
+ *      neighbour's polynomial continued analytically into K_e, with its mean over K_e
+ *      replaced by the mean of U_h^e (Hermite data: cell average of K_e, all derivatives
+ *      of K_l).  U_{h,0}^e = U_h^e.  Missing neighbours (non-periodic boundary) are
+ *      left out, so m_e shrinks.
+ *   R2 U* lives in V_p(K_e) (Q_p on quadrilaterals).
+ *   R3 nonlinear weights w_l = wt_l / sum_m wt_m, wt_l = lin_l / (eps_w + beta_l)^2 with
+ *      beta_l = ||U_{h,l}^e||_e^2 (the same seminorm).
+ *   R4 the seminorm sums over all multi-indices 1 <= |k| <= p, mixed ones included.
+ *   R5 guard: numerator <= eps_s gives gamma = 0; otherwise a zero denominator gives
+ *      gamma = 1; otherwise gamma = min(1, r)^q, and gamma = 0 if r < b.
+ *   R6 gamma is recomputed from the state each residual evaluation (every RK stage).
+ *   R7 lambda_e = max |F'(U_h)|_2 over the element's volume and face Gauss points
+ *      (unless a fixed value is given, as the paper does for the KPP problem).
+ *   R8 boundary ghosts: periodic wrap; inflow-zero sets U+ = 0 where F'(U-).n < 0 and
+ *      U+ = U- elsewhere; outflow sets U+ = U-.
+ *
+ * Mode ordering: k = i + (p+1)*j, i the Legendre degree along x, j along y (1D: k = i).
+ * State layout: U[k*E + e], element e = iy*nx + ix.
+ *
+ * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off [-fopenmp].
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAXP 3
+#define ORC_MAXK ((ORC_MAXP + 1) * (ORC_MAXP + 1))
+#define ORC_MAXNQ 32
+
+enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW_ZERO = 1, ORC_BC_OUTFLOW = 2 };
+enum { ORC_FLUX_ADVECT = 0, ORC_FLUX_ROTATION = 1, ORC_FLUX_BURGERS = 2, ORC_FLUX_KPP = 3 };
+enum { ORC_STAB_DG = 0, ORC_STAB_LO = 1, ORC_STAB_WENO = 2 };
+
+typedef struct {
+    int dim, nx, ny, p;
+    double x0, x1, y0, y1;
+    int bc[4];               /* faces -x, +x, -y, +y */
+    int flux;
+    double a[2];             /* advection velocity / Burgers direction */
+    double center[2];        /* rotation centre */
+    double omega;            /* rotation rate: v = omega*(cy - y, x - cx) */
+    double lambda_nu;        /* > 0: fixed lambda_e for nu_e */
+    int stab;
+    double q, b, w_nbr, eps_w, eps_s;
+} orc_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Legendre polynomials                                                       */
+/* ------------------------------------------------------------------------- */
+
+/* P_n(x) by the three-term recurrence (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1}. */
+static double leg(int n, double x)
+{
+    if (n == 0) return 1.0;
+    double pm = 1.0, pc = x;
+    for (int k = 1; k < n; ++k) {
+        double pn = ((2.0 * k + 1.0) * x * pc - k * pm) / (k + 1.0);
+        pm = pc;
+        pc = pn;
+    }
+    return pc;
+}
+
+#define ORC_MAXDEG 8
+
+/* Monomial coefficients of P_n (n <= ORC_MAXDEG), from the same recurrence applied to
+ * coefficient arrays: mono[n][m] is the coefficient of x^m. */
+static double g_mono[ORC_MAXDEG + 1][ORC_MAXDEG + 1];
+
+static void build_monomials(void)
+{
+    memset(g_mono, 0, sizeof g_mono);
+    g_mono[0][0] = 1.0;
+    g_mono[1][1] = 1.0;
+    for (int k = 1; k < ORC_MAXDEG; ++k) {
+        for (int m = 0; m <= k; ++m) g_mono[k + 1][m + 1] += (2.0 * k + 1.0) * g_mono[k][m] / (k + 1.0);
+        for (int m = 0; m <= k - 1; ++m) g_mono[k + 1][m] -= k * g_mono[k - 1][m] / (k + 1.0);
+    }
+}
+
+/* a-th derivative of P_n at x: differentiate the monomial form a times, then Horner. */
+static double leg_d(int n, int a, double x)
+{
+    if (a == 0) return leg(n, x);
+    if (a > n) return 0.0;
+    double c[ORC_MAXDEG + 1];
+    for (int m = 0; m <= n; ++m) c[m] = g_mono[n][m];
+    for (int t = 0; t < a; ++t)
+        for (int m = 0; m <= n; ++m) c[m] = (m + 1 <= n) ? (m + 1) * c[m + 1] : 0.0;
+    double s = 0.0;
+    for (int m = n - a; m >= 0; --m) s = s * x + c[m];
+    return s;
+}
+
+/* Gauss-Legendre rule on [-1,1]: Newton iteration on P_n from the Chebyshev guess. */
+static void gauss_legendre_newton(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = leg(n, z), p1 = leg(n - 1, z);
+            double dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = leg(n, z), p1 = leg(n - 1, z);
+        double dp = n * (z * p0 - p1) / (z * z - 1.0);
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* Rules for n = 1..ORC_MAXNQ, computed once. */
+static double g_gx[ORC_MAXNQ + 1][ORC_MAXNQ], g_gw[ORC_MAXNQ + 1][ORC_MAXNQ];
+static int g_ready = 0;
+
+static void orc_init(void)
+{
+    if (g_ready) return;
+    build_monomials();
+    for (int n = 1; n <= ORC_MAXNQ; ++n) gauss_legendre_newton(n, g_gx[n], g_gw[n]);
+    g_ready = 1;
+}
+
+void orc_gauss_legendre(int n, double* x, double* w)
+{
+    orc_init();
+    for (int i = 0; i < n; ++i) { x[i] = g_gx[n][i]; w[i] = g_gw[n][i]; }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geometry and basis                                                         */
+/* ------------------------------------------------------------------------- */
+
+static int nmodes1(const orc_problem* P) { return P->p + 1; }
+static int nmodes(const orc_problem* P) { return P->dim == 1 ? P->p + 1 : (P->p + 1) * (P->p + 1); }
+static long nelem(const orc_problem* P) { return P->dim == 1 ? (long)P->nx : (long)P->nx * P->ny; }
+static double hx_of(const orc_problem* P) { return (P->x1 - P->x0) / P->nx; }
+static double hy_of(const orc_problem* P) { return P->dim == 1 ? 1.0 : (P->y1 - P->y0) / P->ny; }
+
+static void elem_center(const orc_problem* P, long e, double* xc, double* yc)
+{
+    int ix = (int)(e % P->nx), iy = (int)(e / P->nx);
+    *xc = P->x0 + (ix + 0.5) * hx_of(P);
+    *yc = P->dim == 1 ? 0.0 : P->y0 + (iy + 0.5) * hy_of(P);
+}
+
+/* Basis function phi_k (or one of its reference derivatives) of an element whose
+ * centre is (xc,yc), evaluated at the physical point (x,y).  Points outside the
+ * element give the analytic continuation (used for the Hermite candidates). */
+static double phi_d(const orc_problem* P, int k, int kx, int ky,
+                    double xc, double yc, double x, double y)
+{
+    int n1 = nmodes1(P);
+    int i = k % n1, j = k / n1;
+    double xi = 2.0 * (x - xc) / hx_of(P);
+    double v = leg_d(i, kx, xi) * pow(2.0 / hx_of(P), kx);
+    if (P->dim == 2) {
+        double eta = 2.0 * (y - yc) / hy_of(P);
+        v *= leg_d(j, ky, eta) * pow(2.0 / hy_of(P), ky);
+    }
+    return v;
+}
+
+/* Physical derivative D^(kx,ky) of sum_k c_k phi_k at (x,y). */
+static double poly_d(const orc_problem* P, const double* c, int kx, int ky,
+                     double xc, double yc, double x, double y)
+{
+    double s = 0.0;
+    for (int k = 0; k < nmodes(P); ++k) s += c[k] * phi_d(P, k, kx, ky, xc, yc, x, y);
+    return s;
+}
+
+static void load_elem(const orc_problem* P, const double* U, long e, double* c)
+{
+    long E = nelem(P);
+    for (int k = 0; k < nmodes(P); ++k) c[k] = U[k * E + e];
+}
+
+/* Quadrature over element e with nq points per direction: fills physical points and
+ * weights (weights include the Jacobian).  Returns the point count. */
+static int elem_quad(const orc_problem* P, long e, int nq, double* qx, double* qy, double* qw)
+{
+    double gx[ORC_MAXNQ], gw[ORC_MAXNQ], xc, yc;
+    orc_gauss_legendre(nq, gx, gw);
+    elem_center(P, e, &xc, &yc);
+    double hx = hx_of(P), hy = hy_of(P);
+    int n = 0;
+    if (P->dim == 1) {
+        for (int a = 0; a < nq; ++a) {
+            qx[n] = xc + 0.5 * hx * gx[a]; qy[n] = 0.0; qw[n] = gw[a] * 0.5 * hx; ++n;
+        }
+    } else {
+        for (int b = 0; b < nq; ++b)
+            for (int a = 0; a < nq; ++a) {
+                qx[n] = xc + 0.5 * hx * gx[a];
+                qy[n] = yc + 0.5 * hy * gx[b];
+                qw[n] = gw[a] * gw[b] * 0.25 * hx * hy;
+                ++n;
+            }
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Flux functions (scalar conservation laws of the paper's scalar examples)   */
+/* ------------------------------------------------------------------------- */
+
+static void rot_velocity(const orc_problem* P, double x, double y, double v[2])
+{
+    v[0] = P->omega * (P->center[1] - y);
+    v[1] = P->omega * (x - P->center[0]);
+}
+
+static void flux_F(const orc_problem* P, double u, double x, double y, double F[2])
+{
+    switch (P->flux) {
+    case ORC_FLUX_ADVECT: F[0] = P->a[0] * u; F[1] = P->a[1] * u; break;
+    case ORC_FLUX_ROTATION: { double v[2]; rot_velocity(P, x, y, v); F[0] = v[0] * u; F[1] = v[1] * u; } break;
+    case ORC_FLUX_BURGERS: F[0] = P->a[0] * 0.5 * u * u; F[1] = P->a[1] * 0.5 * u * u; break;
+    case ORC_FLUX_KPP: F[0] = sin(u); F[1] = cos(u); break;
+    default: F[0] = F[1] = NAN;
+    }
+    if (P->dim == 1) F[1] = 0.0;
+}
+
+static void flux_dF(const orc_problem* P, double u, double x, double y, double v[2])
+{
+    switch (P->flux) {
+    case ORC_FLUX_ADVECT: v[0] = P->a[0]; v[1] = P->a[1]; break;
+    case ORC_FLUX_ROTATION: rot_velocity(P, x, y, v); break;
+    case ORC_FLUX_BURGERS: v[0] = P->a[0] * u; v[1] = P->a[1] * u; break;
+    case ORC_FLUX_KPP: v[0] = cos(u); v[1] = -sin(u); break;
+    default: v[0] = v[1] = NAN;
+    }
+    if (P->dim == 1) v[1] = 0.0;
+}
+
+/* Exact s+ = max over the segment between um and up of |F'(u).n| (Sec. 2).
+ * Normals are axis-aligned on the Cartesian meshes used here. */
+static double wave_speed(const orc_problem* P, double um, double up, double x, double y,
+                         const double n[2])
+{
+    double lo = um < up ? um : up, hi = um < up ? up : um;
+    switch (P->flux) {
+    case ORC_FLUX_ADVECT: return fabs(P->a[0] * n[0] + P->a[1] * n[1]);
+    case ORC_FLUX_ROTATION: { double v[2]; rot_velocity(P, x, y, v); return fabs(v[0] * n[0] + v[1] * n[1]); }
+    case ORC_FLUX_BURGERS: {
+        /* F'(u).n = (a.n) u is linear in u: its modulus peaks at an endpoint. */
+        double an = fabs(P->a[0] * n[0] + P->a[1] * n[1]);
+        return an * (fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi));
+    }
+    case ORC_FLUX_KPP: {
+        /* x-normal: |F'.n| = |cos u|, maximal (=1) at multiples of pi;
+         * y-normal: |F'.n| = |sin u|, maximal (=1) at pi/2 + multiples of pi.
+         * Between two maxima the modulus is unimodal with its minimum inside, so
+         * without an interior maximum the segment maximum sits at an endpoint. */
+        int xnormal = fabs(n[0]) > 0.5;
+        double shift = xnormal ? 0.0 : 0.5 * M_PI;
+        double kmin = ceil((lo - shift) / M_PI);
+        if (kmin * M_PI + shift <= hi) return 1.0;
+        double glo = xnormal ? fabs(cos(lo)) : fabs(sin(lo));
+        double ghi = xnormal ? fabs(cos(hi)) : fabs(sin(hi));
+        return glo > ghi ? glo : ghi;
+    }
+    default: return NAN;
+    }
+}
+
+/* Local Lax-Friedrichs flux H(U-,U+,n) = n.(F(U-)+F(U+))/2 - s+/2 (U+ - U-) (Sec. 2). */
+double orc_llf(const orc_problem* P, double um, double up, double x, double y, double nx, double ny)
+{
+    orc_init();
+    double n[2] = {nx, ny}, Fm[2], Fp[2];
+    flux_F(P, um, x, y, Fm);
+    flux_F(P, up, x, y, Fp);
+    double s = wave_speed(P, um, up, x, y, n);
+    return 0.5 * (n[0] * (Fm[0] + Fp[0]) + n[1] * (Fm[1] + Fp[1])) - 0.5 * s * (up - um);
+}
+
+double orc_wave_speed(const orc_problem* P, double um, double up, double x, double y, double nx, double ny)
+{
+    orc_init();
+    double n[2] = {nx, ny};
+    return wave_speed(P, um, up, x, y, n);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Mesh connectivity                                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Neighbour of e across face f (0:-x 1:+x 2:-y 3:+y), or -1 at a non-periodic
+ * boundary.  *sx,*sy receive the neighbour's centre as if it sat next to e
+ * (periodic neighbours are placed adjacent, not at their wrapped position). */
+static long neighbour(const orc_problem* P, long e, int f, double* sx, double* sy)
+{
+    int ix = (int)(e % P->nx), iy = (int)(e / P->nx);
+    int jx = ix, jy = iy;
+    double xc, yc;
+    elem_center(P, e, &xc, &yc);
+    double ox = 0.0, oy = 0.0;
+    if (f == 0) { jx = ix - 1; ox = -hx_of(P); }
+    if (f == 1) { jx = ix + 1; ox = hx_of(P); }
+    if (f == 2) { jy = iy - 1; oy = -hy_of(P); }
+    if (f == 3) { jy = iy + 1; oy = hy_of(P); }
+    if (jx < 0 || jx >= P->nx) {
+        if (P->bc[f] != ORC_BC_PERIODIC) return -1;
+        jx = (jx + P->nx) % P->nx;
+    }
+    if (P->dim == 2 && (jy < 0 || jy >= P->ny)) {
+        if (P->bc[f] != ORC_BC_PERIODIC) return -1;
+        jy = (jy + P->ny) % P->ny;
+    }
+    if (sx) *sx = xc + ox;
+    if (sy) *sy = yc + oy;
+    return (long)jy * P->nx + jx;
+}
+
+static int nfaces(const orc_problem* P) { return 2 * P->dim; }
+
+/* Face f of element e: Gauss points (physical), weights (with face Jacobian), normal. */
+static int face_quad(const orc_problem* P, long e, int f, int nq,
+                     double* qx, double* qy, double* qw, double n[2])
+{
+    double xc, yc, gx[ORC_MAXNQ], gw[ORC_MAXNQ];
+    elem_center(P, e, &xc, &yc);
+    double hx = hx_of(P), hy = hy_of(P);
+    n[0] = n[1] = 0.0;
+    if (f == 0) n[0] = -1.0;
+    if (f == 1) n[0] = 1.0;
+    if (f == 2) n[1] = -1.0;
+    if (f == 3) n[1] = 1.0;
+    if (P->dim == 1) {
+        qx[0] = xc + 0.5 * hx * n[0]; qy[0] = 0.0; qw[0] = 1.0;
+        return 1;
+    }
+    orc_gauss_legendre(nq, gx, gw);
+    for (int a = 0; a < nq; ++a) {
+        if (f < 2) { qx[a] = xc + 0.5 * hx * n[0]; qy[a] = yc + 0.5 * hy * gx[a]; qw[a] = gw[a] * 0.5 * hy; }
+        else       { qx[a] = xc + 0.5 * hx * gx[a]; qy[a] = yc + 0.5 * hy * n[1]; qw[a] = gw[a] * 0.5 * hx; }
+    }
+    return nq;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Scaled Sobolev seminorm and WENO sensor (Sec. 4)                           */
+/* ------------------------------------------------------------------------- */
+
+/* ||v||_e^2 = sum_{1<=|k|<=p} h^{2|k|-d} int_{K_e} |D^k v|^2 dx, v = sum c_k phi_k of e. */
+static double seminorm2(const orc_problem* P, long e, const double* c)
+{
+    double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+    double xc, yc;
+    elem_center(P, e, &xc, &yc);
+    int nq = elem_quad(P, e, P->p + 2, qx, qy, qw);
+    double h = hx_of(P);
+    double s = 0.0;
+    int kymax = P->dim == 2 ? P->p : 0;
+    for (int ky = 0; ky <= kymax; ++ky)
+        for (int kx = 0; kx <= P->p; ++kx) {
+            int K = kx + ky;
+            if (K < 1 || K > P->p) continue;
+            double integral = 0.0;
+            for (int t = 0; t < nq; ++t) {
+                double d = poly_d(P, c, kx, ky, xc, yc, qx[t], qy[t]);
+                integral += qw[t] * d * d;
+            }
+            s += pow(h, 2.0 * K - P->dim) * integral;
+        }
+    return s;
+}
+
+/* Hermite candidate from neighbour polynomial cn (centre sx,sy): its continuation into
+ * K_e projected onto V_p(K_e) (exact: the integrand is a polynomial), then the mode-0
+ * coefficient (the mean over K_e) replaced by that of U_h^e. */
+static void candidate(const orc_problem* P, long e, const double* ce, const double* cn,
+                      double sx, double sy, double* cl)
+{
+    double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+    double xc, yc;
+    elem_center(P, e, &xc, &yc);
+    int nq = elem_quad(P, e, P->p + 2, qx, qy, qw);
+    double val[ORC_MAXNQ * ORC_MAXNQ];
+    for (int t = 0; t < nq; ++t) val[t] = poly_d(P, cn, 0, 0, sx, sy, qx[t], qy[t]);
+    for (int k = 0; k < nmodes(P); ++k) {
+        double num = 0.0, den = 0.0;
+        for (int t = 0; t < nq; ++t) {
+            double ph = phi_d(P, k, 0, 0, xc, yc, qx[t], qy[t]);
+            num += qw[t] * ph * val[t];
+            den += qw[t] * ph * ph;
+        }
+        cl[k] = num / den;
+    }
+    cl[0] = ce[0];
+}
+
+/* Sensor of element e.  Returns gamma_e; optional outputs: ratio, m_e, weights. */
+static double sensor_elem(const orc_problem* P, const double* U, long e,
+                          double* ratio_out, double* weights_out)
+{
+    int K = nmodes(P);
+    double ce[ORC_MAXK], cand[5][ORC_MAXK], cn[ORC_MAXK];
+    load_elem(P, U, e, ce);
+    memcpy(cand[0], ce, sizeof(double) * K);
+    int m = 0;
+    for (int f = 0; f < nfaces(P); ++f) {
+        double sx, sy;
+        long nb = neighbour(P, e, f, &sx, &sy);
+        if (nb < 0) continue;
+        load_elem(P, U, nb, cn);
+        ++m;
+        candidate(P, e, ce, cn, sx, sy, cand[m]);
+    }
+    double lin[5], wt[5], beta[5], wsum = 0.0;
+    lin[0] = 1.0 - m * P->w_nbr;
+    for (int l = 1; l <= m; ++l) lin[l] = P->w_nbr;
+    for (int l = 0; l <= m; ++l) {
+        beta[l] = seminorm2(P, e, cand[l]);
+        wt[l] = lin[l] / ((P->eps_w + beta[l]) * (P->eps_w + beta[l]));
+        wsum += wt[l];
+    }
+    double ustar[ORC_MAXK] = {0}, diff[ORC_MAXK];
+    for (int l = 0; l <= m; ++l) {
+        double w = wt[l] / wsum;
+        if (weights_out) weights_out[l] = w;
+        for (int k = 0; k < K; ++k) ustar[k] += w * cand[l][k];
+    }
+    if (weights_out) for (int l = m + 1; l < 5; ++l) weights_out[l] = 0.0;
+    for (int k = 0; k < K; ++k) diff[k] = ce[k] - ustar[k];
+    double num = sqrt(seminorm2(P, e, diff));
+    double den = sqrt(seminorm2(P, e, ce));
+    double gamma, r;
+    if (num <= P->eps_s) { gamma = 0.0; r = 0.0; }
+    else if (den == 0.0) { gamma = 1.0; r = INFINITY; }
+    else {
+        r = num / den;
+        gamma = pow(r < 1.0 ? r : 1.0, P->q);
+        if (r < P->b) gamma = 0.0;
+    }
+    if (ratio_out) *ratio_out = r;
+    return gamma;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Residual  L = M^{-1} R_stab(U)  (Eq. weak2 with the stabilization of Sec. 3) */
+/* ------------------------------------------------------------------------- */
+
+/* lambda_e: fixed value, or max |F'(U_h)|_2 over the volume and face Gauss points. */
+static double lambda_elem(const orc_problem* P, long e, const double* ce)
+{
+    if (P->lambda_nu > 0.0) return P->lambda_nu;
+    double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+    double xc, yc, v[2], n[2];
+    elem_center(P, e, &xc, &yc);
+    int nq = P->p + 2;
+    double lam = 0.0;
+    int nv = elem_quad(P, e, nq, qx, qy, qw);
+    for (int t = 0; t < nv; ++t) {
+        flux_dF(P, poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]), qx[t], qy[t], v);
+        double s = sqrt(v[0] * v[0] + v[1] * v[1]);
+        if (s > lam) lam = s;
+    }
+    for (int f = 0; f < nfaces(P); ++f) {
+        int nf = face_quad(P, e, f, nq, qx, qy, qw, n);
+        for (int t = 0; t < nf; ++t) {
+            flux_dF(P, poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]), qx[t], qy[t], v);
+            double s = sqrt(v[0] * v[0] + v[1] * v[1]);
+            if (s > lam) lam = s;
+        }
+    }
+    return lam;
+}
+
+static void residual_elem(const orc_problem* P, const double* U, long e, double* Le,
+                          double* gamma_out)
+{
+    int K = nmodes(P);
+    int nq = P->p + 2;
+    double ce[ORC_MAXK], cn[ORC_MAXK], R[ORC_MAXK] = {0};
+    double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+    double fx[ORC_MAXNQ], fy[ORC_MAXNQ], fw[ORC_MAXNQ];
+    double xc, yc, F[2], n[2];
+    load_elem(P, U, e, ce);
+    elem_center(P, e, &xc, &yc);
+
+    /* volume: + int grad(phi_k) . F(U_h) dx */
+    int nv = elem_quad(P, e, nq, qx, qy, qw);
+    for (int t = 0; t < nv; ++t) {
+        double u = poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]);
+        flux_F(P, u, qx[t], qy[t], F);
+        for (int k = 0; k < K; ++k) {
+            double g = phi_d(P, k, 1, 0, xc, yc, qx[t], qy[t]) * F[0];
+            if (P->dim == 2) g += phi_d(P, k, 0, 1, xc, yc, qx[t], qy[t]) * F[1];
+            R[k] += qw[t] * g;
+        }
+    }
+
+    /* faces: - int_{dK} phi_k H(U-, U+, n) ds */
+    for (int f = 0; f < nfaces(P); ++f) {
+        double sx = 0.0, sy = 0.0;
+        long nb = neighbour(P, e, f, &sx, &sy);
+        if (nb >= 0) load_elem(P, U, nb, cn);
+        int nf = face_quad(P, e, f, nq, fx, fy, fw, n);
+        for (int t = 0; t < nf; ++t) {
+            double um = poly_d(P, ce, 0, 0, xc, yc, fx[t], fy[t]);
+            double up;
+            if (nb >= 0) {
+                up = poly_d(P, cn, 0, 0, sx, sy, fx[t], fy[t]);
+            } else if (P->bc[f] == ORC_BC_INFLOW_ZERO) {
+                double v[2];
+                flux_dF(P, um, fx[t], fy[t], v);
+                up = (v[0] * n[0] + v[1] * n[1] < 0.0) ? 0.0 : um;
+            } else {
+                up = um;
+            }
+            double H = orc_llf(P, um, up, fx[t], fy[t], n[0], n[1]);
+            for (int k = 0; k < K; ++k)
+                R[k] -= fw[t] * phi_d(P, k, 0, 0, xc, yc, fx[t], fy[t]) * H;
+        }
+    }
+
+    /* stabilization: - gamma_e nu_e int grad(phi_k) . grad(U_h) dx */
+    double gamma = 0.0;
+    if (P->stab != ORC_STAB_DG && P->p >= 1) {
+        gamma = (P->stab == ORC_STAB_LO) ? 1.0 : sensor_elem(P, U, e, NULL, NULL);
+        double nu = lambda_elem(P, e, ce) * hx_of(P) / (2.0 * P->p);
+        for (int t = 0; t < nv; ++t) {
+            double ux = poly_d(P, ce, 1, 0, xc, yc, qx[t], qy[t]);
+            double uy = P->dim == 2 ? poly_d(P, ce, 0, 1, xc, yc, qx[t], qy[t]) : 0.0;
+            for (int k = 0; k < K; ++k) {
+                double g = phi_d(P, k, 1, 0, xc, yc, qx[t], qy[t]) * ux;
+                if (P->dim == 2) g += phi_d(P, k, 0, 1, xc, yc, qx[t], qy[t]) * uy;
+                R[k] -= gamma * nu * qw[t] * g;
+            }
+        }
+    }
+    if (gamma_out) *gamma_out = gamma;
+
+    /* L = M^{-1} R with M_kk = int phi_k^2 dx (the Legendre basis is orthogonal) */
+    for (int k = 0; k < K; ++k) {
+        double m = 0.0;
+        for (int t = 0; t < nv; ++t) {
+            double ph = phi_d(P, k, 0, 0, xc, yc, qx[t], qy[t]);
+            m += qw[t] * ph * ph;
+        }
+        Le[k] = R[k] / m;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Public entry points (ctypes)                                               */
+/* ------------------------------------------------------------------------- */
+
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+
+int orc_get_threads(void) { return g_threads; }
+
+int orc_check(const orc_problem* P)
+{
+    orc_init();
+    if (P->dim != 1 && P->dim != 2) return -1;
+    if (P->p < 0 || P->p > ORC_MAXP) return -1;
+    if (P->nx < 1 || (P->dim == 2 && P->ny < 1)) return -1;
+    if (P->dim == 2) {
+        double hx = hx_of(P), hy = hy_of(P);
+        if (fabs(hx - hy) > 1e-12 * hx) return -1;
+    }
+    return 0;
+}
+
+void orc_residual(const orc_problem* P, const double* U, double* L)
+{
+    orc_init();
+    long E = nelem(P);
+    int K = nmodes(P);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
+    for (long e = 0; e < E; ++e) {
+        double Le[ORC_MAXK];
+        residual_elem(P, U, e, Le, NULL);
+        for (int k = 0; k < K; ++k) L[k * E + e] = Le[k];
+    }
+}
+
+void orc_sensor(const orc_problem* P, const double* U, double* gamma, double* ratio,
+                double* weights /* E x 5 or NULL */)
+{
+    orc_init();
+    long E = nelem(P);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
+    for (long e = 0; e < E; ++e) {
+        double r, w[5];
+        gamma[e] = sensor_elem(P, U, e, &r, w);
+        if (ratio) ratio[e] = r;
+        if (weights) for (int l = 0; l < 5; ++l) weights[e * 5 + l] = w[l];
+    }
+}
+
+void orc_lambda(const orc_problem* P, const double* U, double* lam)
+{
+    orc_init();
+    long E = nelem(P);
+    for (long e = 0; e < E; ++e) {
+        double ce[ORC_MAXK];
+        load_elem(P, U, e, ce);
+        lam[e] = lambda_elem(P, e, ce);
+    }
+}
+
+/* Optimal third-order SSP Runge-Kutta (Eq. ssp), nsteps steps of size dt, in place. */
+void orc_rk3(const orc_problem* P, double* U, double dt, int nsteps)
+{
+    long N = nelem(P) * nmodes(P);
+    double* L = malloc(sizeof(double) * N);
+    double* U1 = malloc(sizeof(double) * N);
+    double* U2 = malloc(sizeof(double) * N);
+    for (int s = 0; s < nsteps; ++s) {
+        orc_residual(P, U, L);
+        for (long i = 0; i < N; ++i) U1[i] = U[i] + dt * L[i];
+        orc_residual(P, U1, L);
+        for (long i = 0; i < N; ++i) U2[i] = 0.75 * U[i] + 0.25 * U1[i] + 0.25 * dt * L[i];
+        orc_residual(P, U2, L);
+        for (long i = 0; i < N; ++i) U[i] = U[i] / 3.0 + 2.0 / 3.0 * U2[i] + 2.0 / 3.0 * dt * L[i];
+    }
+    free(L); free(U1); free(U2);
+}
+
+/* Sample layout for projection / error: f[e*nq^d + a + nq*b] at the physical points
+ * x = xc + hx/2 * g_a, y = yc + hy/2 * g_b of the nq-point Gauss-Legendre rule. */
+
+/* L2 projection onto V_p: c_k = int f phi_k / int phi_k^2 with nq-point Gauss. */
+void orc_project(const orc_problem* P, int nq, const double* f, double* U)
+{
+    orc_init();
+    long E = nelem(P);
+    int K = nmodes(P);
+    int npt = P->dim == 1 ? nq : nq * nq;
+    for (long e = 0; e < E; ++e) {
+        double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ], xc, yc;
+        elem_center(P, e, &xc, &yc);
+        elem_quad(P, e, nq, qx, qy, qw);
+        for (int k = 0; k < K; ++k) {
+            double num = 0.0, den = 0.0;
+            for (int t = 0; t < npt; ++t) {
+                double ph = phi_d(P, k, 0, 0, xc, yc, qx[t], qy[t]);
+                num += qw[t] * ph * f[e * npt + t];
+                den += qw[t] * ph * ph;
+            }
+            U[k * E + e] = num / den;
+        }
+    }
+}
+
+/* sum_e int_{K_e} |U_h - f| dx with nq-point Gauss and samples f as above. */
+double orc_l1_error(const orc_problem* P, const double* U, int nq, const double* f)
+{
+    orc_init();
+    long E = nelem(P);
+    int npt = P->dim == 1 ? nq : nq * nq;
+    double s = 0.0;
+    for (long e = 0; e < E; ++e) {
+        double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+        double ce[ORC_MAXK], xc, yc;
+        load_elem(P, U, e, ce);
+        elem_center(P, e, &xc, &yc);
+        elem_quad(P, e, nq, qx, qy, qw);
+        for (int t = 0; t < npt; ++t)
+            s += qw[t] * fabs(poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]) - f[e * npt + t]);
+    }
+    return s;
+}
+
+/* Values of U_h at the nq-point Gauss points (same layout as the samples). */
+void orc_eval(const orc_problem* P, const double* U, int nq, double* out)
+{
+    orc_init();
+    long E = nelem(P);
+    int npt = P->dim == 1 ? nq : nq * nq;
+    for (long e = 0; e < E; ++e) {
+        double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+        double ce[ORC_MAXK], xc, yc;
+        load_elem(P, U, e, ce);
+        elem_center(P, e, &xc, &yc);
+        elem_quad(P, e, nq, qx, qy, qw);
+        for (int t = 0; t < npt; ++t) out[e * npt + t] = poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]);
+    }
+}
+
+/* Total mass sum_e int_{K_e} U_h dx (quadrature of the polynomial). */
+double orc_mass(const orc_problem* P, const double* U)
+{
+    orc_init();
+    long E = nelem(P);
+    double s = 0.0;
+    for (long e = 0; e < E; ++e) {
+        double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+        double ce[ORC_MAXK], xc, yc;
+        load_elem(P, U, e, ce);
+        elem_center(P, e, &xc, &yc);
+        int n = elem_quad(P, e, P->p + 2, qx, qy, qw);
+        for (int t = 0; t < n; ++t) s += qw[t] * poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]);
+    }
+    return s;
+}
+
+/* Seminorm^2 of an arbitrary coefficient vector on element 0 (for tests). */
+double orc_seminorm2(const orc_problem* P, const double* c) {
+    orc_init(); return seminorm2(P, 0, c); }
+
+/* Hermite candidate of element e from its face-f neighbour (for tests); returns
+ * 0, or -1 when that neighbour does not exist. */
+int orc_candidate(const orc_problem* P, const double* U, long e, int f, double* cl)
+{
+    orc_init();
+    double sx, sy, ce[ORC_MAXK], cn[ORC_MAXK];
+    long nb = neighbour(P, e, f, &sx, &sy);
+    if (nb < 0) return -1;
+    load_elem(P, U, e, ce);
+    load_elem(P, U, nb, cn);
+    candidate(P, e, ce, cn, sx, sy, cl);
+    return 0;
+}
+
+/* Legendre values for tests. */
+double orc_legendre(int n, int a, double x) {
+    orc_init(); return leg_d(n, a, x); }

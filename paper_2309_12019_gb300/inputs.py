@@ -1,0 +1,153 @@
+"""Seeded synthetic inputs for the scalar conservation laws of the paper's Sec. 5.
+
+This module holds no arithmetic of the method itself: it only places sample points,
+evaluates initial data (closed-form functions of x), draws seeded random states and
+states the time-step recipe.  Both the CUDA path and the CPU oracle consume what it
+produces, and it imports neither of them.
+
+Sample layout (shared by the projection entry points of both sides): for element
+``e = iy*nx + ix`` and the ``nq``-point Gauss-Legendre rule ``g`` on [-1, 1], sample
+``t = a + nq*b`` sits at ``x = xc + hx/2*g[a]``, ``y = yc + hy/2*g[b]``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED = 2309012019
+
+
+def gauss_nodes(nq: int) -> np.ndarray:
+    """Gauss-Legendre nodes on [-1, 1] (NumPy's rule)."""
+    return np.polynomial.legendre.leggauss(nq)[0]
+
+
+def sample_points(dim: int, nx: int, ny: int, box, nq: int = 8):
+    """Physical coordinates of the projection samples, shape (E, nq**dim) each."""
+    g = gauss_nodes(nq)
+    x0, x1, y0, y1 = box
+    hx = (x1 - x0) / nx
+    xc = x0 + (np.arange(nx) + 0.5) * hx
+    if dim == 1:
+        X = xc[:, None] + 0.5 * hx * g[None, :]
+        return X, np.zeros_like(X)
+    hy = (y1 - y0) / ny
+    yc = y0 + (np.arange(ny) + 0.5) * hy
+    # element e = iy*nx + ix; sample t = a + nq*b
+    Xe = np.broadcast_to(xc[None, :], (ny, nx)).reshape(-1)
+    Ye = np.broadcast_to(yc[:, None], (ny, nx)).reshape(-1)
+    ga = np.tile(g, nq)          # a fastest
+    gb = np.repeat(g, nq)
+    X = Xe[:, None] + 0.5 * hx * ga[None, :]
+    Y = Ye[:, None] + 0.5 * hy * gb[None, :]
+    return X, Y
+
+
+# --------------------------------------------------------------------------------------
+# Initial data of the workloads
+# --------------------------------------------------------------------------------------
+
+def u0_cos(x, y=None):
+    """Sec. 5.1 smooth advection datum cos(2 pi (x - 0.5))."""
+    return np.cos(2.0 * np.pi * (x - 0.5))
+
+
+def u0_sin(x, y=None):
+    """Sec. 5.2 Burgers datum sin(2 pi x)."""
+    return np.sin(2.0 * np.pi * x)
+
+
+def u0_mixed_1d(x, y=None):
+    """1D advection profile: square wave on [0.2,0.4], plus a Gaussian exp(-300(x-0.6)^2)
+    everywhere, plus 0.5 sin(2 pi x) on [0.7,0.9]."""
+    u = np.where((x >= 0.2) & (x <= 0.4), 1.0, 0.0)
+    u = u + np.exp(-300.0 * (x - 0.6) ** 2)
+    u = u + np.where((x >= 0.7) & (x <= 0.9), 0.5 * np.sin(2.0 * np.pi * x), 0.0)
+    return u
+
+
+def u0_rotation(x, y):
+    """Solid-body rotation datum (Sec. 5.3): slotted cylinder, cone and hump of radius 0.15."""
+    r_cyl = np.hypot(x - 0.5, y - 0.75)
+    r_cone = np.hypot(x - 0.5, y - 0.25)
+    r_hump = np.hypot(x - 0.25, y - 0.5)
+    u = np.zeros_like(x)
+    cyl = (r_cyl <= 0.15) & ((np.abs(x - 0.5) >= 0.025) | (y >= 0.85))
+    u = np.where(cyl, 1.0, u)
+    u = np.where(r_cone <= 0.15, 1.0 - r_cone / 0.15, u)
+    u = np.where(r_hump <= 0.15, 0.25 + 0.25 * np.cos(np.pi * r_hump / 0.15), u)
+    return u
+
+
+def u0_kpp(x, y):
+    """KPP datum (Sec. 5.5): 7 pi / 2 inside the unit disc, pi / 4 outside."""
+    return np.where(np.hypot(x, y) <= 1.0, 3.5 * np.pi, 0.25 * np.pi)
+
+
+def fourier_steps_params(dim: int, rng: np.random.Generator, nmodes: int = 8, max_steps: int = 3):
+    """Random smooth-plus-steps datum: nmodes Fourier modes with amplitude ~U(0,1) plus
+    0..max_steps unit steps (indicators of random periodic intervals / rectangles)."""
+    amp = rng.uniform(0.0, 1.0, nmodes)
+    phase = rng.uniform(0.0, 2.0 * np.pi, nmodes)
+    if dim == 1:
+        k = rng.integers(1, 9, size=(nmodes, 1))
+    else:
+        k = rng.integers(-4, 5, size=(nmodes, 2))
+        zero = np.all(k == 0, axis=1)
+        k[zero, 0] = 1
+    nsteps = int(rng.integers(0, max_steps + 1))
+    lo = rng.uniform(0.0, 1.0, size=(nsteps, dim))
+    width = rng.uniform(0.05, 0.4, size=(nsteps, dim))
+    return dict(amp=amp, phase=phase, k=k, lo=lo, width=width)
+
+
+def u0_fourier_steps(params, x, y=None):
+    k = params["k"]
+    u = np.zeros_like(x, dtype=np.float64)
+    for j in range(len(params["amp"])):
+        arg = k[j, 0] * x if k.shape[1] == 1 else k[j, 0] * x + k[j, 1] * y
+        u = u + params["amp"][j] * np.sin(2.0 * np.pi * arg + params["phase"][j])
+    for s in range(len(params["lo"])):
+        inside = np.ones_like(x, dtype=bool)
+        coords = [x] if k.shape[1] == 1 else [x, y]
+        for c, lo, w in zip(coords, params["lo"][s], params["width"][s]):
+            inside &= np.mod(c - lo, 1.0) < w
+        u = u + inside.astype(np.float64)
+    return u
+
+
+# --------------------------------------------------------------------------------------
+# Random modal states for parity tests
+# --------------------------------------------------------------------------------------
+
+def random_state(dim: int, p: int, E: int, seed: int, smooth: bool = False,
+                 scale: float = 1.0, offset: float = 0.0) -> np.ndarray:
+    """Seeded random modal coefficients, shape ((p+1)**dim, E).
+
+    ``smooth=True`` lets the coefficient of total degree s decay like 4**-s, which keeps
+    neighbouring elements unrelated (so sensors fire) but the per-element polynomials tame.
+    """
+    rng = np.random.default_rng(seed)
+    K = (p + 1) ** dim
+    U = rng.standard_normal((K, E)) * scale
+    if smooth:
+        for k in range(K):
+            i, j = k % (p + 1), k // (p + 1)
+            U[k] *= 0.25 ** (i + (j if dim == 2 else 0))
+    U[0] += offset
+    return U
+
+
+def cfl_dt(cfl: float, speeds, h) -> float:
+    """Time step of the workloads: dt = CFL / sum_i (max|f_i'| / dx_i)."""
+    return cfl / sum(s / hh for s, hh in zip(speeds, h))
+
+
+def nsteps_to(t_end: float, dt: float):
+    """Whole steps of size dt to t_end, the last one shortened to land on t_end."""
+    n = int(math.floor(t_end / dt + 1e-9))
+    last = t_end - n * dt
+    if last < 1e-12 * dt:
+        return n, dt, 0.0
+    return n, dt, last
