@@ -147,6 +147,8 @@ static void gauss_legendre_newton(int n, double* x, double* w)
     }
 }
 
+static int g_threads = 1;   /* OpenMP threads of the element loops */
+
 /* Rules for n = 1..ORC_MAXNQ, computed once. */
 static double g_gx[ORC_MAXNQ + 1][ORC_MAXNQ], g_gw[ORC_MAXNQ + 1][ORC_MAXNQ];
 static int g_ready = 0;
@@ -182,29 +184,25 @@ static void elem_center(const orc_problem* P, long e, double* xc, double* yc)
     *yc = P->dim == 1 ? 0.0 : P->y0 + (iy + 0.5) * hy_of(P);
 }
 
-/* Basis function phi_k (or one of its reference derivatives) of an element whose
- * centre is (xc,yc), evaluated at the physical point (x,y).  Points outside the
- * element give the analytic continuation (used for the Hermite candidates). */
-static double phi_d(const orc_problem* P, int k, int kx, int ky,
-                    double xc, double yc, double x, double y)
+/* Physical derivative D^(kx,ky) of the basis function phi_k of an element, at the point
+ * whose coordinates in that element's reference frame are (xi, eta), i.e.
+ * x = x_e + h/2 xi (Eq. fesol: U_h^e is a polynomial on K_e).  Points outside [-1,1]^d
+ * give the analytic continuation (used for the Hermite candidates).  Working in the
+ * element's own frame keeps the Gauss nodes exact instead of recovering xi from x. */
+static double phi_d(const orc_problem* P, int k, int kx, int ky, double xi, double eta)
 {
     int n1 = nmodes1(P);
     int i = k % n1, j = k / n1;
-    double xi = 2.0 * (x - xc) / hx_of(P);
     double v = leg_d(i, kx, xi) * pow(2.0 / hx_of(P), kx);
-    if (P->dim == 2) {
-        double eta = 2.0 * (y - yc) / hy_of(P);
-        v *= leg_d(j, ky, eta) * pow(2.0 / hy_of(P), ky);
-    }
+    if (P->dim == 2) v *= leg_d(j, ky, eta) * pow(2.0 / hy_of(P), ky);
     return v;
 }
 
-/* Physical derivative D^(kx,ky) of sum_k c_k phi_k at (x,y). */
-static double poly_d(const orc_problem* P, const double* c, int kx, int ky,
-                     double xc, double yc, double x, double y)
+/* Physical derivative D^(kx,ky) of sum_k c_k phi_k at reference point (xi, eta). */
+static double poly_d(const orc_problem* P, const double* c, int kx, int ky, double xi, double eta)
 {
     double s = 0.0;
-    for (int k = 0; k < nmodes(P); ++k) s += c[k] * phi_d(P, k, kx, ky, xc, yc, x, y);
+    for (int k = 0; k < nmodes(P); ++k) s += c[k] * phi_d(P, k, kx, ky, xi, eta);
     return s;
 }
 
@@ -214,9 +212,11 @@ static void load_elem(const orc_problem* P, const double* U, long e, double* c)
     for (int k = 0; k < nmodes(P); ++k) c[k] = U[k * E + e];
 }
 
-/* Quadrature over element e with nq points per direction: fills physical points and
- * weights (weights include the Jacobian).  Returns the point count. */
-static int elem_quad(const orc_problem* P, long e, int nq, double* qx, double* qy, double* qw)
+/* Quadrature over element e with nq points per direction: physical points (qx, qy),
+ * the same points in the element's reference frame (qr, qs), and weights including
+ * the Jacobian.  Returns the point count. */
+static int elem_quad(const orc_problem* P, long e, int nq, double* qx, double* qy,
+                     double* qr, double* qs, double* qw)
 {
     double gx[ORC_MAXNQ], gw[ORC_MAXNQ], xc, yc;
     orc_gauss_legendre(nq, gx, gw);
@@ -225,13 +225,16 @@ static int elem_quad(const orc_problem* P, long e, int nq, double* qx, double* q
     int n = 0;
     if (P->dim == 1) {
         for (int a = 0; a < nq; ++a) {
-            qx[n] = xc + 0.5 * hx * gx[a]; qy[n] = 0.0; qw[n] = gw[a] * 0.5 * hx; ++n;
+            qx[n] = xc + 0.5 * hx * gx[a]; qy[n] = 0.0;
+            qr[n] = gx[a]; qs[n] = 0.0;
+            qw[n] = gw[a] * 0.5 * hx; ++n;
         }
     } else {
         for (int b = 0; b < nq; ++b)
             for (int a = 0; a < nq; ++a) {
                 qx[n] = xc + 0.5 * hx * gx[a];
                 qy[n] = yc + 0.5 * hy * gx[b];
+                qr[n] = gx[a]; qs[n] = gx[b];
                 qw[n] = gw[a] * gw[b] * 0.25 * hx * hy;
                 ++n;
             }
@@ -327,19 +330,19 @@ double orc_wave_speed(const orc_problem* P, double um, double up, double x, doub
 /* ------------------------------------------------------------------------- */
 
 /* Neighbour of e across face f (0:-x 1:+x 2:-y 3:+y), or -1 at a non-periodic
- * boundary.  *sx,*sy receive the neighbour's centre as if it sat next to e
- * (periodic neighbours are placed adjacent, not at their wrapped position). */
+ * boundary.  *sx,*sy receive the offset of the neighbour's reference frame: a point
+ * with coordinates (xi, eta) in K_e has coordinates (xi + sx, eta + sy) in the
+ * neighbour, which sits next to e (periodic neighbours are placed adjacent, not at
+ * their wrapped position): sx = +2 for the neighbour on the -x side. */
 static long neighbour(const orc_problem* P, long e, int f, double* sx, double* sy)
 {
     int ix = (int)(e % P->nx), iy = (int)(e / P->nx);
     int jx = ix, jy = iy;
-    double xc, yc;
-    elem_center(P, e, &xc, &yc);
     double ox = 0.0, oy = 0.0;
-    if (f == 0) { jx = ix - 1; ox = -hx_of(P); }
-    if (f == 1) { jx = ix + 1; ox = hx_of(P); }
-    if (f == 2) { jy = iy - 1; oy = -hy_of(P); }
-    if (f == 3) { jy = iy + 1; oy = hy_of(P); }
+    if (f == 0) { jx = ix - 1; ox = 2.0; }
+    if (f == 1) { jx = ix + 1; ox = -2.0; }
+    if (f == 2) { jy = iy - 1; oy = 2.0; }
+    if (f == 3) { jy = iy + 1; oy = -2.0; }
     if (jx < 0 || jx >= P->nx) {
         if (P->bc[f] != ORC_BC_PERIODIC) return -1;
         jx = (jx + P->nx) % P->nx;
@@ -348,16 +351,17 @@ static long neighbour(const orc_problem* P, long e, int f, double* sx, double* s
         if (P->bc[f] != ORC_BC_PERIODIC) return -1;
         jy = (jy + P->ny) % P->ny;
     }
-    if (sx) *sx = xc + ox;
-    if (sy) *sy = yc + oy;
+    if (sx) *sx = ox;
+    if (sy) *sy = oy;
     return (long)jy * P->nx + jx;
 }
 
 static int nfaces(const orc_problem* P) { return 2 * P->dim; }
 
-/* Face f of element e: Gauss points (physical), weights (with face Jacobian), normal. */
+/* Face f of element e: Gauss points (physical and in e's reference frame), weights
+ * (with the face Jacobian), outward normal. */
 static int face_quad(const orc_problem* P, long e, int f, int nq,
-                     double* qx, double* qy, double* qw, double n[2])
+                     double* qx, double* qy, double* qr, double* qs, double* qw, double n[2])
 {
     double xc, yc, gx[ORC_MAXNQ], gw[ORC_MAXNQ];
     elem_center(P, e, &xc, &yc);
@@ -368,13 +372,18 @@ static int face_quad(const orc_problem* P, long e, int f, int nq,
     if (f == 2) n[1] = -1.0;
     if (f == 3) n[1] = 1.0;
     if (P->dim == 1) {
-        qx[0] = xc + 0.5 * hx * n[0]; qy[0] = 0.0; qw[0] = 1.0;
+        qx[0] = xc + 0.5 * hx * n[0]; qy[0] = 0.0; qr[0] = n[0]; qs[0] = 0.0; qw[0] = 1.0;
         return 1;
     }
     orc_gauss_legendre(nq, gx, gw);
     for (int a = 0; a < nq; ++a) {
-        if (f < 2) { qx[a] = xc + 0.5 * hx * n[0]; qy[a] = yc + 0.5 * hy * gx[a]; qw[a] = gw[a] * 0.5 * hy; }
-        else       { qx[a] = xc + 0.5 * hx * gx[a]; qy[a] = yc + 0.5 * hy * n[1]; qw[a] = gw[a] * 0.5 * hx; }
+        if (f < 2) {
+            qx[a] = xc + 0.5 * hx * n[0]; qy[a] = yc + 0.5 * hy * gx[a];
+            qr[a] = n[0]; qs[a] = gx[a]; qw[a] = gw[a] * 0.5 * hy;
+        } else {
+            qx[a] = xc + 0.5 * hx * gx[a]; qy[a] = yc + 0.5 * hy * n[1];
+            qr[a] = gx[a]; qs[a] = n[1]; qw[a] = gw[a] * 0.5 * hx;
+        }
     }
     return nq;
 }
@@ -387,9 +396,8 @@ static int face_quad(const orc_problem* P, long e, int f, int nq,
 static double seminorm2(const orc_problem* P, long e, const double* c)
 {
     double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-    double xc, yc;
-    elem_center(P, e, &xc, &yc);
-    int nq = elem_quad(P, e, P->p + 2, qx, qy, qw);
+    double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+    int nq = elem_quad(P, e, P->p + 2, qx, qy, qr, qs, qw);
     double h = hx_of(P);
     double s = 0.0;
     int kymax = P->dim == 2 ? P->p : 0;
@@ -399,7 +407,7 @@ static double seminorm2(const orc_problem* P, long e, const double* c)
             if (K < 1 || K > P->p) continue;
             double integral = 0.0;
             for (int t = 0; t < nq; ++t) {
-                double d = poly_d(P, c, kx, ky, xc, yc, qx[t], qy[t]);
+                double d = poly_d(P, c, kx, ky, qr[t], qs[t]);
                 integral += qw[t] * d * d;
             }
             s += pow(h, 2.0 * K - P->dim) * integral;
@@ -407,22 +415,21 @@ static double seminorm2(const orc_problem* P, long e, const double* c)
     return s;
 }
 
-/* Hermite candidate from neighbour polynomial cn (centre sx,sy): its continuation into
- * K_e projected onto V_p(K_e) (exact: the integrand is a polynomial), then the mode-0
- * coefficient (the mean over K_e) replaced by that of U_h^e. */
+/* Hermite candidate from neighbour polynomial cn (frame offset sx,sy): its continuation
+ * into K_e projected onto V_p(K_e) (exact: the integrand is a polynomial), then the
+ * mode-0 coefficient (the mean over K_e) replaced by that of U_h^e. */
 static void candidate(const orc_problem* P, long e, const double* ce, const double* cn,
                       double sx, double sy, double* cl)
 {
     double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-    double xc, yc;
-    elem_center(P, e, &xc, &yc);
-    int nq = elem_quad(P, e, P->p + 2, qx, qy, qw);
+    double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+    int nq = elem_quad(P, e, P->p + 2, qx, qy, qr, qs, qw);
     double val[ORC_MAXNQ * ORC_MAXNQ];
-    for (int t = 0; t < nq; ++t) val[t] = poly_d(P, cn, 0, 0, sx, sy, qx[t], qy[t]);
+    for (int t = 0; t < nq; ++t) val[t] = poly_d(P, cn, 0, 0, qr[t] + sx, qs[t] + sy);
     for (int k = 0; k < nmodes(P); ++k) {
         double num = 0.0, den = 0.0;
         for (int t = 0; t < nq; ++t) {
-            double ph = phi_d(P, k, 0, 0, xc, yc, qx[t], qy[t]);
+            double ph = phi_d(P, k, 0, 0, qr[t], qs[t]);
             num += qw[t] * ph * val[t];
             den += qw[t] * ph * ph;
         }
@@ -487,20 +494,20 @@ static double lambda_elem(const orc_problem* P, long e, const double* ce)
 {
     if (P->lambda_nu > 0.0) return P->lambda_nu;
     double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-    double xc, yc, v[2], n[2];
-    elem_center(P, e, &xc, &yc);
+    double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+    double v[2], n[2];
     int nq = P->p + 2;
     double lam = 0.0;
-    int nv = elem_quad(P, e, nq, qx, qy, qw);
+    int nv = elem_quad(P, e, nq, qx, qy, qr, qs, qw);
     for (int t = 0; t < nv; ++t) {
-        flux_dF(P, poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]), qx[t], qy[t], v);
+        flux_dF(P, poly_d(P, ce, 0, 0, qr[t], qs[t]), qx[t], qy[t], v);
         double s = sqrt(v[0] * v[0] + v[1] * v[1]);
         if (s > lam) lam = s;
     }
     for (int f = 0; f < nfaces(P); ++f) {
-        int nf = face_quad(P, e, f, nq, qx, qy, qw, n);
+        int nf = face_quad(P, e, f, nq, qx, qy, qr, qs, qw, n);
         for (int t = 0; t < nf; ++t) {
-            flux_dF(P, poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]), qx[t], qy[t], v);
+            flux_dF(P, poly_d(P, ce, 0, 0, qr[t], qs[t]), qx[t], qy[t], v);
             double s = sqrt(v[0] * v[0] + v[1] * v[1]);
             if (s > lam) lam = s;
         }
@@ -515,19 +522,19 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
     int nq = P->p + 2;
     double ce[ORC_MAXK], cn[ORC_MAXK], R[ORC_MAXK] = {0};
     double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-    double fx[ORC_MAXNQ], fy[ORC_MAXNQ], fw[ORC_MAXNQ];
-    double xc, yc, F[2], n[2];
+    double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+    double fx[ORC_MAXNQ], fy[ORC_MAXNQ], fr[ORC_MAXNQ], fs[ORC_MAXNQ], fw[ORC_MAXNQ];
+    double F[2], n[2];
     load_elem(P, U, e, ce);
-    elem_center(P, e, &xc, &yc);
 
     /* volume: + int grad(phi_k) . F(U_h) dx */
-    int nv = elem_quad(P, e, nq, qx, qy, qw);
+    int nv = elem_quad(P, e, nq, qx, qy, qr, qs, qw);
     for (int t = 0; t < nv; ++t) {
-        double u = poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]);
+        double u = poly_d(P, ce, 0, 0, qr[t], qs[t]);
         flux_F(P, u, qx[t], qy[t], F);
         for (int k = 0; k < K; ++k) {
-            double g = phi_d(P, k, 1, 0, xc, yc, qx[t], qy[t]) * F[0];
-            if (P->dim == 2) g += phi_d(P, k, 0, 1, xc, yc, qx[t], qy[t]) * F[1];
+            double g = phi_d(P, k, 1, 0, qr[t], qs[t]) * F[0];
+            if (P->dim == 2) g += phi_d(P, k, 0, 1, qr[t], qs[t]) * F[1];
             R[k] += qw[t] * g;
         }
     }
@@ -537,12 +544,12 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
         double sx = 0.0, sy = 0.0;
         long nb = neighbour(P, e, f, &sx, &sy);
         if (nb >= 0) load_elem(P, U, nb, cn);
-        int nf = face_quad(P, e, f, nq, fx, fy, fw, n);
+        int nf = face_quad(P, e, f, nq, fx, fy, fr, fs, fw, n);
         for (int t = 0; t < nf; ++t) {
-            double um = poly_d(P, ce, 0, 0, xc, yc, fx[t], fy[t]);
+            double um = poly_d(P, ce, 0, 0, fr[t], fs[t]);
             double up;
             if (nb >= 0) {
-                up = poly_d(P, cn, 0, 0, sx, sy, fx[t], fy[t]);
+                up = poly_d(P, cn, 0, 0, fr[t] + sx, fs[t] + sy);
             } else if (P->bc[f] == ORC_BC_INFLOW_ZERO) {
                 double v[2];
                 flux_dF(P, um, fx[t], fy[t], v);
@@ -552,7 +559,7 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
             }
             double H = orc_llf(P, um, up, fx[t], fy[t], n[0], n[1]);
             for (int k = 0; k < K; ++k)
-                R[k] -= fw[t] * phi_d(P, k, 0, 0, xc, yc, fx[t], fy[t]) * H;
+                R[k] -= fw[t] * phi_d(P, k, 0, 0, fr[t], fs[t]) * H;
         }
     }
 
@@ -562,11 +569,11 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
         gamma = (P->stab == ORC_STAB_LO) ? 1.0 : sensor_elem(P, U, e, NULL, NULL);
         double nu = lambda_elem(P, e, ce) * hx_of(P) / (2.0 * P->p);
         for (int t = 0; t < nv; ++t) {
-            double ux = poly_d(P, ce, 1, 0, xc, yc, qx[t], qy[t]);
-            double uy = P->dim == 2 ? poly_d(P, ce, 0, 1, xc, yc, qx[t], qy[t]) : 0.0;
+            double ux = poly_d(P, ce, 1, 0, qr[t], qs[t]);
+            double uy = P->dim == 2 ? poly_d(P, ce, 0, 1, qr[t], qs[t]) : 0.0;
             for (int k = 0; k < K; ++k) {
-                double g = phi_d(P, k, 1, 0, xc, yc, qx[t], qy[t]) * ux;
-                if (P->dim == 2) g += phi_d(P, k, 0, 1, xc, yc, qx[t], qy[t]) * uy;
+                double g = phi_d(P, k, 1, 0, qr[t], qs[t]) * ux;
+                if (P->dim == 2) g += phi_d(P, k, 0, 1, qr[t], qs[t]) * uy;
                 R[k] -= gamma * nu * qw[t] * g;
             }
         }
@@ -577,7 +584,7 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
     for (int k = 0; k < K; ++k) {
         double m = 0.0;
         for (int t = 0; t < nv; ++t) {
-            double ph = phi_d(P, k, 0, 0, xc, yc, qx[t], qy[t]);
+            double ph = phi_d(P, k, 0, 0, qr[t], qs[t]);
             m += qw[t] * ph * ph;
         }
         Le[k] = R[k] / m;
@@ -587,8 +594,6 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
 /* ------------------------------------------------------------------------- */
 /* Public entry points (ctypes)                                               */
 /* ------------------------------------------------------------------------- */
-
-static int g_threads = 1;
 
 void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
 
@@ -677,14 +682,17 @@ void orc_project(const orc_problem* P, int nq, const double* f, double* U)
     long E = nelem(P);
     int K = nmodes(P);
     int npt = P->dim == 1 ? nq : nq * nq;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
     for (long e = 0; e < E; ++e) {
-        double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ], xc, yc;
-        elem_center(P, e, &xc, &yc);
-        elem_quad(P, e, nq, qx, qy, qw);
+        double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
+        double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+        elem_quad(P, e, nq, qx, qy, qr, qs, qw);
         for (int k = 0; k < K; ++k) {
             double num = 0.0, den = 0.0;
             for (int t = 0; t < npt; ++t) {
-                double ph = phi_d(P, k, 0, 0, xc, yc, qx[t], qy[t]);
+                double ph = phi_d(P, k, 0, 0, qr[t], qs[t]);
                 num += qw[t] * ph * f[e * npt + t];
                 den += qw[t] * ph * ph;
             }
@@ -702,12 +710,12 @@ double orc_l1_error(const orc_problem* P, const double* U, int nq, const double*
     double s = 0.0;
     for (long e = 0; e < E; ++e) {
         double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-        double ce[ORC_MAXK], xc, yc;
+        double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+        double ce[ORC_MAXK];
         load_elem(P, U, e, ce);
-        elem_center(P, e, &xc, &yc);
-        elem_quad(P, e, nq, qx, qy, qw);
+        elem_quad(P, e, nq, qx, qy, qr, qs, qw);
         for (int t = 0; t < npt; ++t)
-            s += qw[t] * fabs(poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]) - f[e * npt + t]);
+            s += qw[t] * fabs(poly_d(P, ce, 0, 0, qr[t], qs[t]) - f[e * npt + t]);
     }
     return s;
 }
@@ -720,11 +728,11 @@ void orc_eval(const orc_problem* P, const double* U, int nq, double* out)
     int npt = P->dim == 1 ? nq : nq * nq;
     for (long e = 0; e < E; ++e) {
         double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-        double ce[ORC_MAXK], xc, yc;
+        double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+        double ce[ORC_MAXK];
         load_elem(P, U, e, ce);
-        elem_center(P, e, &xc, &yc);
-        elem_quad(P, e, nq, qx, qy, qw);
-        for (int t = 0; t < npt; ++t) out[e * npt + t] = poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]);
+        elem_quad(P, e, nq, qx, qy, qr, qs, qw);
+        for (int t = 0; t < npt; ++t) out[e * npt + t] = poly_d(P, ce, 0, 0, qr[t], qs[t]);
     }
 }
 
@@ -736,11 +744,11 @@ double orc_mass(const orc_problem* P, const double* U)
     double s = 0.0;
     for (long e = 0; e < E; ++e) {
         double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
-        double ce[ORC_MAXK], xc, yc;
+        double qr[ORC_MAXNQ * ORC_MAXNQ], qs[ORC_MAXNQ * ORC_MAXNQ];
+        double ce[ORC_MAXK];
         load_elem(P, U, e, ce);
-        elem_center(P, e, &xc, &yc);
-        int n = elem_quad(P, e, P->p + 2, qx, qy, qw);
-        for (int t = 0; t < n; ++t) s += qw[t] * poly_d(P, ce, 0, 0, xc, yc, qx[t], qy[t]);
+        int n = elem_quad(P, e, P->p + 2, qx, qy, qr, qs, qw);
+        for (int t = 0; t < n; ++t) s += qw[t] * poly_d(P, ce, 0, 0, qr[t], qs[t]);
     }
     return s;
 }
@@ -766,3 +774,28 @@ int orc_candidate(const orc_problem* P, const double* U, long e, int f, double* 
 /* Legendre values for tests. */
 double orc_legendre(int n, int a, double x) {
     orc_init(); return leg_d(n, a, x); }
+
+/* Residual and sensor of selected elements only (for sampled checks on large meshes).
+ * out[k*n + t] = L_k of element idx[t]; gamma[t] = gamma of element idx[t]. */
+void orc_residual_at(const orc_problem* P, const double* U, const long* idx, long n, double* out)
+{
+    orc_init();
+    int K = nmodes(P);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
+    for (long t = 0; t < n; ++t) {
+        double Le[ORC_MAXK];
+        residual_elem(P, U, idx[t], Le, NULL);
+        for (int k = 0; k < K; ++k) out[k * n + t] = Le[k];
+    }
+}
+
+void orc_sensor_at(const orc_problem* P, const double* U, const long* idx, long n, double* gamma)
+{
+    orc_init();
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
+    for (long t = 0; t < n; ++t) gamma[t] = sensor_elem(P, U, idx[t], NULL, NULL);
+}

@@ -141,6 +141,9 @@ def lib():
             L.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
             L.orc_legendre.restype = ctypes.c_double
             L.orc_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
+            lp = ctypes.POINTER(ctypes.c_long)
+            L.orc_residual_at.argtypes = [pp, dp, lp, ctypes.c_long, dp]
+            L.orc_sensor_at.argtypes = [pp, dp, lp, ctypes.c_long, dp]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_get_threads.restype = ctypes.c_int
             _lib = L
@@ -180,6 +183,25 @@ def residual(P: Problem, U) -> np.ndarray:
     L = np.zeros_like(U)
     lib().orc_residual(ctypes.byref(c), _ptr(U), _ptr(L))
     return L
+
+
+def residual_at(P: Problem, U, idx) -> np.ndarray:
+    """Residual of the elements listed in idx only: shape (K, len(idx))."""
+    c, U = _checked(P), _state(P, U)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    out = np.zeros((P.K, idx.size))
+    lib().orc_residual_at(ctypes.byref(c), _ptr(U), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                          idx.size, _ptr(out))
+    return out
+
+
+def sensor_at(P: Problem, U, idx) -> np.ndarray:
+    c, U = _checked(P), _state(P, U)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    out = np.zeros(idx.size)
+    lib().orc_sensor_at(ctypes.byref(c), _ptr(U), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                        idx.size, _ptr(out))
+    return out
 
 
 def sensor(P: Problem, U):
