@@ -1,0 +1,294 @@
+"""Throughput of the WENO-stabilized RKDG SSP-RK3 step on one GB300.
+
+Workload (default): the 2D KPP problem u_t + div(sin u, cos u) = 0 on
+[-2,2]x[-2.5,1.5], 1024x1024 square cells, Q3 (16 modes per cell, 16,777,216 DOFs),
+FP32 state and arithmetic, outflow boundaries, lambda_e = 2, WENO sensor with q = 1,
+SSP-RK3 at CFL 0.05 (dt = 9.765625e-5).  Initial data 7 pi/2 inside the unit disc,
+pi/4 outside, L2-projected by the library from 8x8 Gauss samples per cell.
+
+A "step" is one full SSP-RK3 step (three fused stage kernels).  The metric is
+DOF-updates per second per stage: 3 * N_dof * steps / time.  The three state arrays
+(67 MB each) together exceed the 129 MB L2, so no explicit L2 flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 (torchrun) every rank advances its own replica of the workload ("replicas
+only": the single-mesh path is not sharded) and value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2309_12019_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    "kpp_1024x1024_q3": dict(dim=2, nx=1024, ny=1024, p=3, box=(-2.0, 2.0, -2.5, 1.5),
+                             bc=("outflow",) * 4, flux="kpp", lambda_nu=2.0, stab="weno",
+                             cfl=0.05, speeds=(1.0, 1.0), u0="kpp"),
+    "rotation_256x256_q2": dict(dim=2, nx=256, ny=256, p=2, box=(0.0, 1.0, 0.0, 1.0),
+                                bc=("inflow_zero",) * 4, flux="rotation", center=(0.5, 0.5), omega=1.0,
+                                stab="weno", cfl=0.1, speeds=(0.5, 0.5), u0="rotation"),
+}
+
+SPEC_KEYS = ("dim", "nx", "ny", "p", "box", "bc", "flux", "lambda_nu", "stab", "center", "omega")
+
+
+def spec_of(w):
+    return {k: w[k] for k in SPEC_KEYS if k in w}
+
+
+def initial_samples(w):
+    X, Y = I.sample_points(w["dim"], w["nx"], w["ny"], w["box"], 8)
+    f = I.u0_kpp(X, Y) if w["u0"] == "kpp" else I.u0_rotation(X, Y)
+    return np.ascontiguousarray(f.reshape(-1))
+
+
+def dt_of(w):
+    h = (w["box"][1] - w["box"][0]) / w["nx"]
+    return I.cfl_dt(w["cfl"], w["speeds"], [h, h])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu(w, prec, steps, warmup, world, local, measure_e2e):
+    import torch
+
+    from paper_2309_12019_gb300 import dgw
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = dgw.Context(dgw.Problem(**spec_of(w), prec=prec))
+    N = ctx.K * ctx.E
+    stream = torch.cuda.Stream(device=dev)
+    samples = torch.tensor(initial_samples(w), device=dev)
+    U = torch.empty((ctx.K, ctx.E), dtype=ctx.dtype, device=dev)
+    dt = dt_of(w)
+    with torch.cuda.stream(stream):
+        ctx.project(samples, U)
+        U0 = U.clone()
+        ctx.rk_step(U, dt, warmup)
+    stream.synchronize()
+    del samples
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            ctx.rk_step(U, dt, steps)
+            ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    ctx.sync_status(stream)
+    res = dict(N=N, t=t_dev, clocks=clk.summary(), launches=3 * steps, mass=ctx.mass(U, stream))
+    if measure_e2e:
+        # end to end through the host-buffer entry point: H2D + step + D2H every step
+        Uh = U0.cpu().pin_memory()
+        Uo = torch.empty_like(Uh).pin_memory()
+        for _ in range(2):
+            ctx.rk_step_host(Uh, Uo, dt, 1, stream=stream)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.rk_step_host(Uh, Uo, dt, 1, stream=stream)
+        t_e2e = time.perf_counter() - t0
+        res["t_e2e"] = t_e2e
+        res["bytes"] = Uh.numel() * Uh.element_size()
+    ctx.close()
+    return res
+
+
+def run_reference(w, steps, warmup, budget_s=12.0):
+    """The FP64 CPU oracle on this host's cores, each step a bounded sample: the
+    residual (per-stage work) of a contiguous block of elements."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    P = O.Problem(**spec_of(w))
+    U = O.project(P, initial_samples(w))
+    E, K = P.E, P.K
+    block = 4096
+    # calibrate the sample so that all steps fit in the budget
+    t0 = time.perf_counter()
+    O.residual_at(P, U, np.arange(block))
+    per_elem = (time.perf_counter() - t0) / block
+    n_el = int(max(block, min(E, budget_s / max(steps + warmup, 1) / per_elem)))
+    idx = np.arange(n_el) + (E - n_el) // 2
+    for _ in range(warmup):
+        O.residual_at(P, U, idx)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.residual_at(P, U, idx)
+    t = time.perf_counter() - t0
+    value = n_el * K * steps / t
+    return value, cores, n_el
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kpp_1024x1024_q3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_setup(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    metric = "DOF-updates/sec per SSP-RK3 stage"
+    config = {"workload": args.workload, "mesh": f"{w['nx']}x{w['ny']}", "p": w["p"], "flux": w["flux"],
+              "stab": w["stab"], "dofs": w["nx"] * w["ny"] * (w["p"] + 1) ** 2,
+              "l2": "inputs larger than L2 (three 67 MB FP32 state arrays per stage)",
+              "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, cores, n_el = run_reference(w, args.steps, args.warmup)
+        sample = f"oracle residual (per-stage work) of {n_el} contiguous cells of the {w['nx']}x{w['ny']} mesh per step"
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": "DOF-updates/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    r32 = run_gpu(w, "fp32", args.steps, args.warmup, world, local, measure_e2e=not args.no_e2e)
+    t = max_over_ranks(r32["t"], world)
+    t_e2e = max_over_ranks(r32["t_e2e"], world) if "t_e2e" in r32 else float("nan")
+    N = r32["N"]
+    value = world * 3 * N * args.steps / t
+    e2e_value = world * 3 * N * args.steps / t_e2e
+    r64 = None
+    if not args.no_fp64:
+        st64 = max(3, args.steps // 10)
+        r64 = run_gpu(w, "fp64", st64, args.warmup, world, local, measure_e2e=False)
+        r64["steps"] = st64
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    per_launch_s = t / (3 * args.steps)
+    alg_bytes = 8.0 / 3.0 * N * 4          # per stage: 8 state-array passes per step / 3 stages
+    achieved = alg_bytes / per_launch_s / 1e9
+    line = {"metric": metric, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                         "kernel": "stage_kernel (3 launches per step)"},
+            "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": r32.get("bytes"),
+                    "d2h_bytes_per_step": r32.get("bytes")} if "t_e2e" in r32 else None,
+            "gpu_launches": r32["launches"], "clocks": r32["clocks"], "mass_after": r32["mass"]}
+    if r64 is not None:
+        line["fp64"] = {"value": 3 * N * r64["steps"] / r64["t"], "unit": "DOF-updates/s",
+                        "ms_per_step": 1e3 * r64["t"] / r64["steps"], "steps": r64["steps"]}
+    if not args.no_cpu and world == 1:
+        v, cores, n_el = run_reference(w, 3, 1, budget_s=12.0)
+        line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                                "sample": f"oracle residual (per-stage work) of {n_el} contiguous cells, 3 repeats"}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * dgw.h -- C ABI of the GB300 library for the WENO-stabilized RKDG method of
+ * Vedral, "Dissipative WENO stabilization of high-order discontinuous Galerkin methods
+ * for hyperbolic problems" (arXiv 2309.12019).
+ *
+ * Problem (Sec. 2, Eq. pde/ivp): a scalar conservation law u_t + div F(u) = 0 on a
+ * Cartesian box in 1D or 2D, discretized by modal tensor-Legendre DG of degree p
+ * (Eq. fesol; Q_p on quadrilaterals), the local Lax-Friedrichs flux (Sec. 2), the
+ * dissipative stabilization gamma_e nu_e int grad(phi).grad(U_h) (Sec. 3, Eq. astab,
+ * with Eq. visc for nu_e) driven by the WENO sensor of Sec. 4 (Eq. sensor / gensensor),
+ * and advanced by the optimal SSP-RK3 scheme (Eq. ssp).
+ *
+ * Conventions shared by every entry point
+ *  - State arrays ("U") are device arrays owned by the caller, mode-major
+ *    (structure of arrays): U[k*E + e] with element e = iy*nx + ix and mode
+ *    k = i + (p+1)*j (i: Legendre degree in x, j: in y; 1D: k = i).  K = (p+1)^dim
+ *    modes, E = nx (1D) or nx*ny (2D) elements.  The element type is double for
+ *    DGW_FP64 contexts and float for DGW_FP32 contexts.  Base addresses must be
+ *    aligned to 16 bytes.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream) unless stated otherwise.  Argument
+ *    errors are returned synchronously and nothing is enqueued.  Device-side
+ *    conditions (non-finite results) set a flag in the context that
+ *    dgw_sync_status() reads.
+ *  - Return values are dgw_status codes; dgw_last_error() gives a thread-local
+ *    message for the last failing call of the calling thread.
+ *  - A context is bound to the CUDA device that was current at dgw_create; call
+ *    it with that device current.  A context may be used from one thread at a
+ *    time; calls on different streams that touch the same U race.
+ */
+#ifndef DGW_H
+#define DGW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DGW_OK = 0,
+    DGW_EINVAL = -1,        /* bad argument (null pointer, size, alignment, range) */
+    DGW_ENOMEM = -2,        /* device or host allocation failed */
+    DGW_ECUDA = -3,         /* a CUDA runtime call failed (message has the CUDA error) */
+    DGW_EUNSUPPORTED = -4,  /* valid but not built (e.g. p > 3, non-square 2D cells) */
+    DGW_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+    DGW_ENONFINITE = -6     /* a kernel produced a NaN or Inf */
+} dgw_status;
+
+/* Boundary treatment of one side of the box (Sec. 2: weak inflow conditions). */
+typedef enum {
+    DGW_BC_PERIODIC = 0,
+    DGW_BC_INFLOW_ZERO = 1, /* ghost U+ = 0 where F'(U-).n < 0, U+ = U- elsewhere */
+    DGW_BC_OUTFLOW = 2      /* ghost U+ = U- */
+} dgw_bc;
+
+/* Cartesian mesh of [x0,x1] (1D) or [x0,x1]x[y0,y1] (2D) with nx (x ny) equal cells.
+ * 2D cells must be square (the scaled seminorm of Sec. 4 uses one h_e per cell).
+ * bc: sides -x, +x, -y, +y; periodic sides must come in pairs. */
+typedef struct {
+    int dim;
+    int nx, ny;
+    double x0, x1, y0, y1;
+    int bc[4];
+} dgw_mesh;
+
+/* Flux functions of the paper's scalar examples (Sec. 5). */
+typedef enum {
+    DGW_FLUX_ADVECT = 0,    /* F = (a0, a1) u                                  */
+    DGW_FLUX_ROTATION = 1,  /* F = omega (cy - y, x - cx) u   (solid body)      */
+    DGW_FLUX_BURGERS = 2,   /* F = (a0, a1) u^2 / 2                            */
+    DGW_FLUX_KPP = 3        /* F = (sin u, cos u)                              */
+} dgw_flux_kind;
+
+typedef struct {
+    int kind;               /* dgw_flux_kind */
+    double a[2];
+    double center[2];
+    double omega;
+    double lambda_nu;       /* > 0: fixed lambda_e in nu_e = lambda_e h / (2p) (the paper
+                               uses 2.0 for KPP); 0: max |F'(U_h)|_2 over the element's
+                               volume and face Gauss points */
+} dgw_flux;
+
+typedef enum { DGW_STAB_DG = 0, DGW_STAB_LO = 1, DGW_STAB_WENO = 2 } dgw_stab;
+
+/* DGW_FP64: every operation in double.  DGW_FP32: state, residual and RK update in
+ * float with float accumulation; operator tables are built in double and rounded. */
+typedef enum { DGW_FP64 = 0, DGW_FP32 = 1 } dgw_prec;
+
+/* Stabilization and sensor parameters (Sec. 3-5). */
+typedef struct {
+    int stab;               /* dgw_stab: DG (none), LO (gamma = 1), WENO (Eq. sensor) */
+    double q;               /* sensor exponent, Eq. (sensor); the paper uses 1 */
+    double b;               /* threshold of Eq. (gensensor); 0 recovers Eq. (sensor) */
+    double w_nbr;           /* linear weight of each neighbour candidate (paper: 1e-2);
+                               the cell's own candidate gets 1 - m_e * w_nbr */
+    double eps_w;           /* nonlinear weights w_l ~ lin_l / (eps_w + beta_l)^2 (1e-6) */
+    double eps_s;           /* ||U - U*||_e <= eps_s gives gamma = 0 (1e-12) */
+    int prec;               /* dgw_prec */
+} dgw_params;
+
+typedef struct dgw_ctx dgw_ctx;
+
+/* Fills *m, *f, *s with the defaults above (periodic unit interval, advection with
+ * a = (1, 0), WENO with q = 1, b = 0, w_nbr = 1e-2, eps_w = 1e-6, eps_s = 1e-12, FP64).
+ * Any argument may be NULL. */
+void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s);
+
+/* Creates a context for degree p (1..3) on the current device: checks the arguments,
+ * builds the operator tables (Gauss rule of p+2 points, Legendre values, Hermite
+ * shift matrices, seminorm Gram matrix, stiffness) in double, uploads them, and
+ * allocates the two RK stage buffers (2*K*E elements) plus small scratch.
+ * *out receives the context; release it with dgw_destroy. */
+dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* flux,
+                      const dgw_params* params, dgw_ctx** out);
+
+/* Frees the context and its device memory (synchronizes the device first). NULL is
+ * accepted. */
+dgw_status dgw_destroy(dgw_ctx* ctx);
+
+/* Sizes: *E elements, *K modes per element, *elem_bytes bytes per coefficient.  Any
+ * pointer may be NULL. */
+dgw_status dgw_sizes(const dgw_ctx* ctx, int64_t* E, int* K, int* elem_bytes);
+
+/* Replaces the stabilization parameters (same precision).  Synchronous, cheap. */
+dgw_status dgw_set_params(dgw_ctx* ctx, const dgw_params* params);
+
+/* L2 projection of initial data onto V_p (Sec. 2, Eq. fesol).  samples (device,
+ * double, E * nq^dim values): f at the nq-point Gauss-Legendre points of each
+ * element, sample t = a + nq*b at x = xc + h/2 g_a, y = yc + h/2 g_b.  nq in 1..8.
+ * U (device, context precision, K*E) receives c_k = int f phi_k / int phi_k^2. */
+dgw_status dgw_project(dgw_ctx* ctx, int nq, const double* samples, void* U, void* stream);
+
+/* Semi-discrete right-hand side L = M^{-1} R_stab(U) (Eq. weak2 with s_h^e of Sec. 3):
+ * volume term, LLF face term, and -gamma_e nu_e times the element stiffness applied to
+ * U_h (gamma_e = 0 for DG, 1 for LO, Eq. sensor for WENO).  U and L: device, K*E,
+ * context precision, must not overlap. */
+dgw_status dgw_residual(dgw_ctx* ctx, const void* U, void* L, void* stream);
+
+/* WENO sensor gamma_e (Sec. 4, Eq. sensor / gensensor) of every element.
+ * gamma: device double[E].  Computed in the context precision, stored as double. */
+dgw_status dgw_sensor(dgw_ctx* ctx, const void* U, double* gamma, void* stream);
+
+/* nsteps steps of the optimal SSP-RK3 scheme (Eq. ssp) with step dt, in place on U
+ * (device, K*E).  Each stage recomputes the sensor from the stage state.  The stage
+ * states live in the context's buffers.  Launch sequence is replayed from a CUDA graph
+ * cached per (U, dt, nsteps, stream) unless the stream is being captured. */
+dgw_status dgw_rk_step(dgw_ctx* ctx, void* U, double dt, int nsteps, void* stream);
+
+/* As dgw_rk_step for a state held in HOST memory: copies U_in (host, K*E elements,
+ * pinned for asynchronous copies) to the device, runs nsteps steps and copies the
+ * result to U_out (host; may equal U_in).  Returns after the stream has finished. */
+dgw_status dgw_rk_step_host(dgw_ctx* ctx, const void* U_in, void* U_out, double dt,
+                            int nsteps, void* stream);
+
+/* Total mass sum_e int_{K_e} U_h dx = sum_e |K_e| c_0^e in double, by a fixed-order
+ * tree (bitwise reproducible).  Blocks until the result is on the host. */
+dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream);
+
+/* Reads and clears the context's device-side error flag (non-finite stage output).
+ * Synchronizes the stream.  DGW_OK or DGW_ENONFINITE. */
+dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* dgw_last_error(void);
+
+/* Library version string. */
+const char* dgw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGW_H */

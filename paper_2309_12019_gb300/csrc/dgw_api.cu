@@ -1,0 +1,510 @@
+// C ABI of libdgw: contexts, argument checks, launch sequences, CUDA-graph replay of
+// the SSP-RK3 loop, projection and the mass diagnostic.  See include/dgw.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dgw.h"
+#include "dgw_internal.h"
+
+using namespace dgw;
+
+static thread_local std::string g_err;
+
+static dgw_status fail(dgw_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static dgw_status fail(dgw_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define DGW_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(DGW_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+using GraphKey = std::tuple<void*, double, int, cudaStream_t>;
+
+struct dgw_ctx {
+    int device = 0;
+    dgw_mesh mesh{};
+    int p = 0;
+    dgw_flux flux{};
+    dgw_params params{};
+    int K = 0;
+    int64_t E = 0;
+    int eb = 8;
+    double h = 0.0;
+    void* S1 = nullptr;
+    void* S2 = nullptr;
+    void* Uhost_dev = nullptr;   // device copy for dgw_rk_step_host
+    double* partial = nullptr;   // mass partial sums
+    double* mass_dev = nullptr;
+    unsigned* flag = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+static const int kMassBlocks = 1024;
+static const int kMassThreads = 256;
+
+extern "C" void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s)
+{
+    if (m) {
+        std::memset(m, 0, sizeof *m);
+        m->dim = 1; m->nx = 16; m->ny = 1;
+        m->x0 = 0.0; m->x1 = 1.0; m->y0 = 0.0; m->y1 = 1.0;
+        for (int i = 0; i < 4; ++i) m->bc[i] = DGW_BC_PERIODIC;
+    }
+    if (f) {
+        std::memset(f, 0, sizeof *f);
+        f->kind = DGW_FLUX_ADVECT; f->a[0] = 1.0; f->a[1] = 0.0;
+        f->center[0] = f->center[1] = 0.5; f->omega = 1.0; f->lambda_nu = 0.0;
+    }
+    if (s) {
+        std::memset(s, 0, sizeof *s);
+        s->stab = DGW_STAB_WENO; s->q = 1.0; s->b = 0.0; s->w_nbr = 1e-2;
+        s->eps_w = 1e-6; s->eps_s = 1e-12; s->prec = DGW_FP64;
+    }
+}
+
+static dgw_status check_params(const dgw_params* s, int dim)
+{
+    if (!s) return fail(DGW_EINVAL, "params is NULL");
+    if (s->stab < DGW_STAB_DG || s->stab > DGW_STAB_WENO) return fail(DGW_EINVAL, "bad stab %d", s->stab);
+    if (s->prec != DGW_FP64 && s->prec != DGW_FP32) return fail(DGW_EINVAL, "bad prec %d", s->prec);
+    if (!(s->q > 0.0) || !std::isfinite(s->q)) return fail(DGW_EINVAL, "q must be > 0");
+    if (!(s->b >= 0.0 && s->b <= 1.0)) return fail(DGW_EINVAL, "b must lie in [0, 1]");
+    if (!(s->w_nbr >= 0.0 && s->w_nbr * 2 * dim < 1.0))
+        return fail(DGW_EINVAL, "w_nbr must lie in [0, 1/(2 dim))");
+    if (!(s->eps_w > 0.0) || !(s->eps_s >= 0.0)) return fail(DGW_EINVAL, "eps_w > 0 and eps_s >= 0 required");
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* flux,
+                                 const dgw_params* params, dgw_ctx** out)
+{
+    if (!mesh || !flux || !params || !out) return fail(DGW_EINVAL, "NULL argument to dgw_create");
+    *out = nullptr;
+    const dgw_mesh& m = *mesh;
+    if (m.dim != 1 && m.dim != 2) return fail(DGW_EINVAL, "dim must be 1 or 2");
+    if (m.nx < 1 || (m.dim == 2 && m.ny < 1)) return fail(DGW_EINVAL, "nx, ny must be >= 1");
+    if (!(m.x1 > m.x0) || (m.dim == 2 && !(m.y1 > m.y0))) return fail(DGW_EINVAL, "empty box");
+    for (int f = 0; f < 2 * m.dim; ++f)
+        if (m.bc[f] < DGW_BC_PERIODIC || m.bc[f] > DGW_BC_OUTFLOW) return fail(DGW_EINVAL, "bad bc[%d]", f);
+    for (int a = 0; a < m.dim; ++a)
+        if ((m.bc[2 * a] == DGW_BC_PERIODIC) != (m.bc[2 * a + 1] == DGW_BC_PERIODIC))
+            return fail(DGW_EINVAL, "periodic sides must come in pairs");
+    const double hx = (m.x1 - m.x0) / m.nx;
+    if (m.dim == 2) {
+        const double hy = (m.y1 - m.y0) / m.ny;
+        if (std::fabs(hx - hy) > 1e-12 * hx) return fail(DGW_EUNSUPPORTED, "2D cells must be square");
+    }
+    if (p < 1 || p > kMaxP) return fail(DGW_EUNSUPPORTED, "degree p=%d not built (1..3)", p);
+    if (flux->kind < DGW_FLUX_ADVECT || flux->kind > DGW_FLUX_KPP) return fail(DGW_EINVAL, "bad flux kind");
+    if (!(flux->lambda_nu >= 0.0)) return fail(DGW_EINVAL, "lambda_nu must be >= 0");
+    dgw_status st = check_params(params, m.dim);
+    if (st != DGW_OK) return st;
+    const int64_t E = m.dim == 1 ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
+    if (E > ((int64_t)1 << 36)) return fail(DGW_EINVAL, "mesh too large");
+
+    dgw_ctx* c = new dgw_ctx();
+    c->mesh = m;
+    if (m.dim == 1) { c->mesh.ny = 1; }
+    c->p = p;
+    c->flux = *flux;
+    c->params = *params;
+    c->K = m.dim == 1 ? p + 1 : (p + 1) * (p + 1);
+    c->E = E;
+    c->eb = params->prec == DGW_FP64 ? 8 : 4;
+    c->h = hx;
+    cudaError_t ce = cudaGetDevice(&c->device);
+    HostTables t;
+    build_tables(p, &t);
+    if (ce == cudaSuccess) {
+        if (params->prec == DGW_FP64) ce = m.dim == 1 ? upload_tables_f64_d1(t) : upload_tables_f64_d2(t);
+        else ce = m.dim == 1 ? upload_tables_f32_d1(t) : upload_tables_f32_d2(t);
+    }
+    const size_t bytes = (size_t)c->K * E * c->eb;
+    if (ce == cudaSuccess) ce = cudaMalloc(&c->S1, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&c->S2, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&c->partial, sizeof(double) * (kMassBlocks + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc(&c->flag, sizeof(unsigned));
+    if (ce == cudaSuccess) ce = cudaMemset(c->flag, 0, sizeof(unsigned));
+    if (ce != cudaSuccess) {
+        dgw_status s = fail(ce == cudaErrorMemoryAllocation ? DGW_ENOMEM : DGW_ECUDA,
+                            "dgw_create: %s", cudaGetErrorString(ce));
+        dgw_destroy(c);
+        return s;
+    }
+    c->mass_dev = c->partial + kMassBlocks;
+    *out = c;
+    return DGW_OK;
+}
+
+static void drop_graphs(dgw_ctx* c)
+{
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+extern "C" dgw_status dgw_destroy(dgw_ctx* c)
+{
+    if (!c) return DGW_OK;
+    cudaDeviceSynchronize();
+    drop_graphs(c);
+    cudaFree(c->S1);
+    cudaFree(c->S2);
+    cudaFree(c->Uhost_dev);
+    cudaFree(c->partial);
+    cudaFree(c->flag);
+    delete c;
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_sizes(const dgw_ctx* c, int64_t* E, int* K, int* eb)
+{
+    if (!c) return fail(DGW_EINVAL, "NULL context");
+    if (E) *E = c->E;
+    if (K) *K = c->K;
+    if (eb) *eb = c->eb;
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_set_params(dgw_ctx* c, const dgw_params* s)
+{
+    if (!c) return fail(DGW_EINVAL, "NULL context");
+    dgw_status st = check_params(s, c->mesh.dim);
+    if (st != DGW_OK) return st;
+    if (s->prec != c->params.prec) return fail(DGW_EINVAL, "precision is fixed at dgw_create");
+    c->params = *s;
+    drop_graphs(c);
+    return DGW_OK;
+}
+
+static StageArgs base_args(const dgw_ctx* c)
+{
+    StageArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.E = c->E;
+    a.nx = c->mesh.nx;
+    a.ny = c->mesh.dim == 2 ? c->mesh.ny : 1;
+    a.x0 = c->mesh.x0;
+    a.y0 = c->mesh.y0;
+    a.h = c->h;
+    for (int f = 0; f < 4; ++f) a.bc[f] = c->mesh.bc[f];
+    a.a0 = c->flux.a[0];
+    a.a1 = c->flux.a[1];
+    a.cx = c->flux.center[0];
+    a.cy = c->flux.center[1];
+    a.omega = c->flux.omega;
+    a.lambda_nu = c->flux.lambda_nu;
+    a.stab = c->params.stab;
+    a.q = c->params.q;
+    a.b = c->params.b;
+    a.w_nbr = c->params.w_nbr;
+    a.eps_w = c->params.eps_w;
+    a.eps_s = c->params.eps_s;
+    a.flag = c->flag;
+    return a;
+}
+
+static cudaError_t launch(const dgw_ctx* c, const StageArgs& a, int mode, cudaStream_t s)
+{
+    const bool f64 = c->params.prec == DGW_FP64;
+    if (c->mesh.dim == 1)
+        return f64 ? launch_stage_f64_d1(a, c->p, c->flux.kind, mode, s)
+                   : launch_stage_f32_d1(a, c->p, c->flux.kind, mode, s);
+    return f64 ? launch_stage_f64_d2(a, c->p, c->flux.kind, mode, s)
+               : launch_stage_f32_d2(a, c->p, c->flux.kind, mode, s);
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static dgw_status check_ctx(const dgw_ctx* c)
+{
+    if (!c) return fail(DGW_EINVAL, "NULL context");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+        return fail(DGW_EINVAL, "context belongs to device %d, current device is %d", c->device, dev);
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_residual(dgw_ctx* c, const void* U, void* L, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U || !L) return fail(DGW_EINVAL, "NULL array");
+    if (!aligned16(U) || !aligned16(L)) return fail(DGW_EINVAL, "arrays must be 16-byte aligned");
+    if (U == L) return fail(DGW_EINVAL, "U and L must not overlap");
+    StageArgs a = base_args(c);
+    a.Uk = U;
+    a.Uout = L;
+    a.cn = 0.0; a.ck = 0.0; a.cl = 1.0;
+    DGW_CUDA(launch(c, a, 0, (cudaStream_t)stream));
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_sensor(dgw_ctx* c, const void* U, double* gamma, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U || !gamma) return fail(DGW_EINVAL, "NULL array");
+    if (!aligned16(U)) return fail(DGW_EINVAL, "U must be 16-byte aligned");
+    StageArgs a = base_args(c);
+    a.Uk = U;
+    a.gamma_out = gamma;
+    DGW_CUDA(launch(c, a, 1, (cudaStream_t)stream));
+    return DGW_OK;
+}
+
+// One SSP-RK3 step (Eq. ssp): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+// U <- 1/3 U + 2/3 (U2 + dt L(U2)).  The third stage writes U in place: each thread
+// reads U only at its own element there.
+static cudaError_t enqueue_steps(const dgw_ctx* c, void* U, double dt, int nsteps, cudaStream_t s)
+{
+    StageArgs a = base_args(c);
+    for (int n = 0; n < nsteps; ++n) {
+        a.Uk = U; a.Un = nullptr; a.Uout = c->S1;
+        a.cn = 0.0; a.ck = 1.0; a.cl = dt;
+        cudaError_t e = launch(c, a, 0, s);
+        if (e != cudaSuccess) return e;
+        a.Uk = c->S1; a.Un = U; a.Uout = c->S2;
+        a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt;
+        e = launch(c, a, 0, s);
+        if (e != cudaSuccess) return e;
+        a.Uk = c->S2; a.Un = U; a.Uout = U;
+        a.cn = 1.0 / 3.0; a.ck = 2.0 / 3.0; a.cl = 2.0 / 3.0 * dt;
+        e = launch(c, a, 0, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static const int kGraphChunk = 16;
+
+static dgw_status run_graph(dgw_ctx* c, void* U, double dt, int n, cudaStream_t s)
+{
+    GraphKey key{U, dt, n, s};
+    auto it = c->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it == c->graphs.end()) {
+        if (c->graphs.size() >= 8) drop_graphs(c);
+        cudaGraph_t g = nullptr;
+        DGW_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_steps(c, U, dt, n, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(DGW_ECUDA, "graph capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(DGW_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        c->graphs[key] = exec;
+    } else {
+        exec = it->second;
+    }
+    DGW_CUDA(cudaGraphLaunch(exec, s));
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_rk_step(dgw_ctx* c, void* U, double dt, int nsteps, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U) return fail(DGW_EINVAL, "NULL state");
+    if (!aligned16(U)) return fail(DGW_EINVAL, "U must be 16-byte aligned");
+    if (nsteps < 0) return fail(DGW_EINVAL, "nsteps < 0");
+    if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
+    if (nsteps == 0) return DGW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (s != nullptr) DGW_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (s == nullptr || cap != cudaStreamCaptureStatusNone) {
+        DGW_CUDA(enqueue_steps(c, U, dt, nsteps, s));
+        return DGW_OK;
+    }
+    const int full = nsteps / kGraphChunk, rest = nsteps % kGraphChunk;
+    for (int i = 0; i < full; ++i) {
+        st = run_graph(c, U, dt, kGraphChunk, s);
+        if (st != DGW_OK) return st;
+    }
+    if (rest) return run_graph(c, U, dt, rest, s);
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_rk_step_host(dgw_ctx* c, const void* U_in, void* U_out, double dt,
+                                       int nsteps, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U_in || !U_out) return fail(DGW_EINVAL, "NULL host array");
+    const size_t bytes = (size_t)c->K * c->E * c->eb;
+    if (!c->Uhost_dev) {
+        cudaError_t e = cudaMalloc(&c->Uhost_dev, bytes);
+        if (e != cudaSuccess) return fail(DGW_ENOMEM, "dgw_rk_step_host: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    DGW_CUDA(cudaMemcpyAsync(c->Uhost_dev, U_in, bytes, cudaMemcpyHostToDevice, s));
+    st = dgw_rk_step(c, c->Uhost_dev, dt, nsteps, stream);
+    if (st != DGW_OK) return st;
+    DGW_CUDA(cudaMemcpyAsync(U_out, c->Uhost_dev, bytes, cudaMemcpyDeviceToHost, s));
+    DGW_CUDA(cudaStreamSynchronize(s));
+    return DGW_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// projection
+// ------------------------------------------------------------------------------------
+struct ProjArgs {
+    const double* f;
+    void* U;
+    int64_t E;
+    int nq, n1, dim, f64;
+    double w[8];
+    double B[8][kMaxN1];
+    double minv[kMaxN1];
+};
+
+__global__ void project_kernel(const ProjArgs a)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.E) return;
+    const int npt = a.dim == 1 ? a.nq : a.nq * a.nq;
+    const double* f = a.f + e * npt;
+    const int K = a.dim == 1 ? a.n1 : a.n1 * a.n1;
+    for (int k = 0; k < K; ++k) {
+        const int i = k % a.n1, j = k / a.n1;
+        double s = 0.0;
+        if (a.dim == 1) {
+            for (int q = 0; q < a.nq; ++q) s += a.w[q] * a.B[q][i] * f[q];
+            s *= a.minv[i];
+        } else {
+            for (int qb = 0; qb < a.nq; ++qb) {
+                double r = 0.0;
+                for (int qa = 0; qa < a.nq; ++qa) r += a.w[qa] * a.B[qa][i] * f[qa + a.nq * qb];
+                s += a.w[qb] * a.B[qb][j] * r;
+            }
+            s *= a.minv[i] * a.minv[j];
+        }
+        if (a.f64) static_cast<double*>(a.U)[k * a.E + e] = s;
+        else static_cast<float*>(a.U)[k * a.E + e] = (float)s;
+    }
+}
+
+
+extern "C" dgw_status dgw_project(dgw_ctx* c, int nq, const double* samples, void* U, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!samples || !U) return fail(DGW_EINVAL, "NULL array");
+    if (nq < 1 || nq > 8) return fail(DGW_EINVAL, "nq must lie in 1..8");
+    ProjArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.f = samples; a.U = U; a.E = c->E; a.nq = nq; a.n1 = c->p + 1; a.dim = c->mesh.dim;
+    a.f64 = c->params.prec == DGW_FP64;
+    double x[8];
+    gauss_rule_public(nq, x, a.w);
+    for (int q = 0; q < nq; ++q) {
+        // P_0..P_p at x_q by the three-term recurrence
+        double pm = 1.0, pc = x[q];
+        a.B[q][0] = 1.0;
+        if (c->p >= 1) a.B[q][1] = x[q];
+        for (int k = 1; k < c->p; ++k) {
+            double pn = ((2 * k + 1) * x[q] * pc - k * pm) / (k + 1);
+            pm = pc; pc = pn;
+            a.B[q][k + 1] = pn;
+        }
+    }
+    for (int i = 0; i <= c->p; ++i) a.minv[i] = (2 * i + 1) / 2.0;
+    const int threads = 128;
+    const int64_t blocks = (c->E + threads - 1) / threads;
+    project_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(a);
+    DGW_CUDA(cudaGetLastError());
+    return DGW_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// mass: sum_e |K_e| c_0^e by a fixed-order two-level tree
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void mass_partial_kernel(const Real* U0, int64_t E, double* partial)
+{
+    __shared__ double sh[kMassThreads];
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x)
+        s += (double)U0[e];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void mass_final_kernel(const double* partial, int n, double vol, double* out)
+{
+    __shared__ double sh[kMassThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] * vol;
+}
+
+extern "C" dgw_status dgw_mass(dgw_ctx* c, const void* U, double* host_mass, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U || !host_mass) return fail(DGW_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double vol = c->mesh.dim == 1 ? c->h : c->h * c->h;
+    if (c->params.prec == DGW_FP64)
+        mass_partial_kernel<double><<<kMassBlocks, kMassThreads, 0, s>>>((const double*)U, c->E, c->partial);
+    else
+        mass_partial_kernel<float><<<kMassBlocks, kMassThreads, 0, s>>>((const float*)U, c->E, c->partial);
+    DGW_CUDA(cudaGetLastError());
+    mass_final_kernel<<<1, kMassThreads, 0, s>>>(c->partial, kMassBlocks, vol, c->mass_dev);
+    DGW_CUDA(cudaGetLastError());
+    DGW_CUDA(cudaMemcpyAsync(host_mass, c->mass_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DGW_CUDA(cudaStreamSynchronize(s));
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_sync_status(dgw_ctx* c, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    unsigned v = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    DGW_CUDA(cudaMemcpyAsync(&v, c->flag, sizeof v, cudaMemcpyDeviceToHost, s));
+    DGW_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(unsigned), s));
+    DGW_CUDA(cudaStreamSynchronize(s));
+    if (v & 1u) return fail(DGW_ENONFINITE, "a stage produced a non-finite value");
+    return DGW_OK;
+}
+
+extern "C" const char* dgw_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* dgw_version(void) { return "dgw 0.1 (sm_103a)"; }

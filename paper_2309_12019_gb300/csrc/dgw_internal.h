@@ -1,0 +1,69 @@
+// Internal declarations shared by the translation units of libdgw (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dgw {
+
+constexpr int kMaxP = 3;
+constexpr int kMaxN1 = kMaxP + 1;          // modes per direction
+constexpr int kMaxNQ = kMaxP + 2;          // Gauss points per direction (p + 2)
+constexpr int kMaxK = kMaxN1 * kMaxN1;     // modes per element (2D)
+
+enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2 };
+enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3 };
+enum : int { STAB_DG = 0, STAB_LO = 1, STAB_WENO = 2 };
+
+// Operator tables of degree p, built once in double on the host (dgw_tables.cu) and
+// rounded to the kernel precision when uploaded.  Reference element [-1, 1]^d.
+struct HostTables {
+    int p;
+    double g[kMaxNQ];               // Gauss-Legendre nodes, p + 2 points
+    double w[kMaxNQ];               // and weights
+    double B[kMaxNQ][kMaxN1];       // P_i(g_q)
+    double D[kMaxNQ][kMaxN1];       // P_i'(g_q)
+    double T[2][kMaxN1][kMaxN1];    // T[s][i][m]: coefficient of P_i in P_m(xi + 2) (s = 0:
+                                    // neighbour on the minus side) or P_m(xi - 2) (s = 1)
+    double G1[kMaxN1][kMaxN1];      // seminorm Gram matrix, 1D
+    double G2[kMaxK][kMaxK];        // seminorm Gram matrix, 2D (mode k = i + (p+1) j)
+    double A1[kMaxN1][kMaxN1];      // int P_i' P_m'
+    double A0[kMaxN1];              // int P_i^2 = 2 / (2i + 1)
+    double minv[kMaxN1];            // (2i + 1) / 2
+};
+
+void build_tables(int p, HostTables* t);
+void gauss_rule_public(int n, double* x, double* w);
+
+// Arguments of one stage launch: Uout = cn*Un + ck*Uk + cl*L(Uk), where L is the
+// stabilized DG right-hand side of Uk.  Pointers are of the kernel precision.
+struct StageArgs {
+    const void* Uk;
+    const void* Un;        // may be null when cn == 0
+    void* Uout;            // may be null in sensor-only launches
+    double cn, ck, cl;
+    int64_t E;
+    int nx, ny;
+    double x0, y0, h;
+    int bc[4];
+    double a0, a1, cx, cy, omega, lambda_nu;
+    int stab;
+    double q, b, w_nbr, eps_w, eps_s;
+    double* gamma_out;     // optional per-element gamma (double)
+    unsigned* flag;        // bit 0: non-finite output
+};
+
+// Launchers, one per (precision, dimension) translation unit.  mode 0: stage or
+// residual; mode 1: sensor only (writes gamma_out).
+cudaError_t launch_stage_f32_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
+cudaError_t launch_stage_f32_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
+cudaError_t launch_stage_f64_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
+cudaError_t launch_stage_f64_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
+
+cudaError_t upload_tables_f32_d1(const HostTables& t);
+cudaError_t upload_tables_f32_d2(const HostTables& t);
+cudaError_t upload_tables_f64_d1(const HostTables& t);
+cudaError_t upload_tables_f64_d2(const HostTables& t);
+
+}  // namespace dgw

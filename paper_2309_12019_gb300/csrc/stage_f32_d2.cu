@@ -1,0 +1,13 @@
+// Stage kernels, float precision, 2D.
+#define DGW_REAL float
+#define DGW_DIM 2
+#define DGW_NS f32_d2
+#include "dgw_stage_impl.cuh"
+
+namespace dgw {
+cudaError_t launch_stage_f32_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s)
+{
+    return f32_d2::launch(a, p, flux, mode, s);
+}
+cudaError_t upload_tables_f32_d2(const HostTables& t) { return f32_d2::upload_tables(t); }
+}  // namespace dgw

@@ -1,0 +1,13 @@
+// Stage kernels, double precision, 1D.
+#define DGW_REAL double
+#define DGW_DIM 1
+#define DGW_NS f64_d1
+#include "dgw_stage_impl.cuh"
+
+namespace dgw {
+cudaError_t launch_stage_f64_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s)
+{
+    return f64_d1::launch(a, p, flux, mode, s);
+}
+cudaError_t upload_tables_f64_d1(const HostTables& t) { return f64_d1::upload_tables(t); }
+}  // namespace dgw

@@ -1,0 +1,231 @@
+"""Thin Python binding of libdgw (include/dgw.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts torch tensors
+to device pointers and the current torch stream to a ``cudaStream_t``, and raises
+``DGWError`` on any non-zero status.  There is no CPU fallback: if the library cannot be
+loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2}
+FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3}
+STAB = {"dg": 0, "lo": 1, "weno": 2}
+PREC = {"fp64": 0, "fp32": 1}
+
+STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ECUDA", -4: "DGW_EUNSUPPORTED",
+          -5: "DGW_ETIMEOUT", -6: "DGW_ENONFINITE"}
+
+
+class DGWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("bc", ctypes.c_int * 4)]
+
+
+class Flux(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double * 2), ("center", ctypes.c_double * 2),
+                ("omega", ctypes.c_double), ("lambda_nu", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("stab", ctypes.c_int), ("q", ctypes.c_double), ("b", ctypes.c_double),
+                ("w_nbr", ctypes.c_double), ("eps_w", ctypes.c_double), ("eps_s", ctypes.c_double),
+                ("prec", ctypes.c_int)]
+
+
+# every symbol declared in include/dgw.h
+EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
+           "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
+           "dgw_sync_status", "dgw_last_error", "dgw_version")
+
+
+def load(build: bool = True):
+    """Loads (building first if needed) the in-tree libdgw.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        L = ctypes.CDLL(path)
+        vp, i64p, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int), \
+            ctypes.POINTER(ctypes.c_double)
+        L.dgw_defaults.argtypes = [ctypes.POINTER(Mesh), ctypes.POINTER(Flux), ctypes.POINTER(Params)]
+        L.dgw_defaults.restype = None
+        L.dgw_create.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.POINTER(Flux),
+                                 ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.dgw_destroy.argtypes = [vp]
+        L.dgw_sizes.argtypes = [vp, i64p, ip, ip]
+        L.dgw_set_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.dgw_project.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.dgw_residual.argtypes = [vp, vp, vp, vp]
+        L.dgw_sensor.argtypes = [vp, vp, vp, vp]
+        L.dgw_rk_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp]
+        L.dgw_rk_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
+        L.dgw_mass.argtypes = [vp, vp, dp, vp]
+        L.dgw_sync_status.argtypes = [vp, vp]
+        L.dgw_last_error.restype = ctypes.c_char_p
+        L.dgw_version.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            getattr(L, name)
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise DGWError(status, load().dgw_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass
+class Problem:
+    """Mesh, degree, flux and stabilization of one scalar conservation law (host side)."""
+    dim: int
+    nx: int
+    p: int
+    ny: int = 1
+    box: tuple = (0.0, 1.0, 0.0, 1.0)
+    bc: tuple = ("periodic",) * 4
+    flux: str = "advect"
+    a: tuple = (1.0, 0.0)
+    center: tuple = (0.5, 0.5)
+    omega: float = 1.0
+    lambda_nu: float = 0.0
+    stab: str = "weno"
+    q: float = 1.0
+    b: float = 0.0
+    w_nbr: float = 1e-2
+    eps_w: float = 1e-6
+    eps_s: float = 1e-12
+    prec: str = "fp64"
+
+    @property
+    def E(self) -> int:
+        return self.nx * (self.ny if self.dim == 2 else 1)
+
+    @property
+    def K(self) -> int:
+        return (self.p + 1) ** self.dim
+
+    def c_structs(self):
+        m = Mesh()
+        m.dim, m.nx, m.ny = self.dim, self.nx, self.ny if self.dim == 2 else 1
+        m.x0, m.x1, m.y0, m.y1 = [float(v) for v in self.box]
+        for i, b in enumerate(self.bc):
+            m.bc[i] = BC[b]
+        f = Flux()
+        f.kind = FLUX[self.flux]
+        f.a[0], f.a[1] = self.a
+        f.center[0], f.center[1] = self.center
+        f.omega, f.lambda_nu = self.omega, self.lambda_nu
+        s = Params()
+        s.stab, s.q, s.b, s.w_nbr = STAB[self.stab], self.q, self.b, self.w_nbr
+        s.eps_w, s.eps_s, s.prec = self.eps_w, self.eps_s, PREC[self.prec]
+        return m, f, s
+
+
+class Context:
+    """Owns one dgw_ctx.  Methods mirror the C entry points of include/dgw.h."""
+
+    def __init__(self, problem: Problem):
+        L = load()
+        self.problem = problem
+        m, f, s = problem.c_structs()
+        h = ctypes.c_void_p()
+        _check(L.dgw_create(ctypes.byref(m), problem.p, ctypes.byref(f), ctypes.byref(s), ctypes.byref(h)))
+        self._h = h
+        E, K, eb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(L.dgw_sizes(h, ctypes.byref(E), ctypes.byref(K), ctypes.byref(eb)))
+        self.E, self.K, self.elem_bytes = E.value, K.value, eb.value
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.elem_bytes == 8 else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dgw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _state(self, U):
+        if not U.is_cuda or U.dtype != self.dtype or not U.is_contiguous() or U.numel() != self.K * self.E:
+            raise ValueError(f"state must be a contiguous CUDA {self.dtype} tensor of {self.K}x{self.E}")
+        return _ptr(U)
+
+    def set_params(self, **kw):
+        self.problem = dataclasses.replace(self.problem, **kw)
+        _, _, s = self.problem.c_structs()
+        _check(load().dgw_set_params(self._h, ctypes.byref(s)))
+
+    def project(self, samples, U, nq: int = 8, stream=None):
+        import torch
+        if samples.dtype != torch.float64 or not samples.is_cuda or not samples.is_contiguous():
+            raise ValueError("samples must be a contiguous CUDA float64 tensor")
+        _check(load().dgw_project(self._h, nq, _ptr(samples), self._state(U), _stream(stream)))
+
+    def residual(self, U, L, stream=None):
+        _check(load().dgw_residual(self._h, self._state(U), self._state(L), _stream(stream)))
+
+    def sensor(self, U, gamma, stream=None):
+        import torch
+        if gamma.dtype != torch.float64 or not gamma.is_cuda or gamma.numel() != self.E:
+            raise ValueError("gamma must be a CUDA float64 tensor of E entries")
+        _check(load().dgw_sensor(self._h, self._state(U), _ptr(gamma), _stream(stream)))
+
+    def rk_step(self, U, dt: float, nsteps: int = 1, stream=None):
+        _check(load().dgw_rk_step(self._h, self._state(U), float(dt), int(nsteps), _stream(stream)))
+
+    def rk_step_host(self, U_in, U_out, dt: float, nsteps: int = 1, stream=None):
+        for t in (U_in, U_out):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.K * self.E:
+                raise ValueError("host state must be a contiguous CPU tensor of the context dtype")
+        _check(load().dgw_rk_step_host(self._h, _ptr(U_in), _ptr(U_out), float(dt), int(nsteps),
+                                       _stream(stream)))
+
+    def mass(self, U, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(load().dgw_mass(self._h, self._state(U), ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def sync_status(self, stream=None):
+        _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+
+def version() -> str:
+    return load().dgw_version().decode()

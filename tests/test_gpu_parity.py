@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (the tolerances are written in each test):
+* FP64 path: relative L2 error <= 1e-12 for residuals and RK steps, |d gamma| <= 1e-12;
+* FP32 path (float state, float arithmetic, double sensor ratio): the oracle runs on the
+  same float-rounded input.  Residuals on random states agree to 1e-5 relative L2 (a few
+  hundred float roundings of O(1) terms, no cancellation), RK3 states on smooth data to
+  2e-5 relative L2;
+* sampled elements of the full-size workloads against the oracle element by element.
+Meshes are chosen so the element count is not a multiple of the 128-thread block and
+several blocks run.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import helpers as H
+from paper_2309_12019_gb300 import dgw
+from paper_2309_12019_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dgw.load()
+
+
+def gpu(s, prec="fp64"):
+    return dgw.Context(dgw.Problem(**s, prec=prec))
+
+
+def to_dev(U, prec):
+    return torch.tensor(U, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda").contiguous()
+
+
+def gpu_residual(ctx, U):
+    Ud = to_dev(U, ctx.problem.prec)
+    L = torch.empty_like(Ud)
+    ctx.residual(Ud, L)
+    torch.cuda.synchronize()
+    return L.double().cpu().numpy()
+
+
+def gpu_sensor(ctx, U):
+    Ud = to_dev(U, ctx.problem.prec)
+    g = torch.empty(ctx.E, dtype=torch.float64, device="cuda")
+    ctx.sensor(Ud, g)
+    torch.cuda.synchronize()
+    return g.cpu().numpy()
+
+
+CASES_1D = [(p, fl, st, bc) for p in (1, 2, 3)
+            for fl, bc in (("advect", "periodic"), ("burgers", "periodic"), ("burgers", "outflow"),
+                           ("advect", "inflow_zero"), ("kpp", "outflow"))
+            for st in ("dg", "lo", "weno")]
+CASES_2D = [(p, fl, st, bc) for p in (1, 2, 3)
+            for fl, bc in (("advect", "periodic"), ("rotation", "inflow_zero"), ("burgers", "periodic"),
+                           ("kpp", "outflow"), ("advect", "outflow"))
+            for st in ("lo", "weno")] + [(2, "rotation", "dg", "inflow_zero"), (3, "kpp", "dg", "outflow")]
+
+
+@pytest.mark.parametrize("p,flux,stab,bc", CASES_1D)
+def test_residual_fp64_1d(oracle_mod, p, flux, stab, bc):
+    s = H.spec(1, p, 300, flux=flux, stab=stab, bc=bc)
+    U = H.state_for(s, seed=100 + p)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    got = gpu_residual(gpu(s), U)
+    assert H.rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("p,flux,stab,bc", CASES_2D)
+def test_residual_fp64_2d(oracle_mod, p, flux, stab, bc):
+    s = H.spec(2, p, 19, ny=13, flux=flux, stab=stab, bc=bc)
+    U = H.state_for(s, seed=200 + p)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    got = gpu_residual(gpu(s), U)
+    assert H.rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dim,p,bc", [(1, 1, "periodic"), (1, 3, "outflow"), (2, 1, "periodic"),
+                                      (2, 2, "outflow"), (2, 3, "periodic"), (2, 3, "inflow_zero")])
+def test_sensor_fp64(oracle_mod, dim, p, bc):
+    s = H.spec(dim, p, 300 if dim == 1 else 17, ny=11, bc=bc)
+    U = H.state_for(s, seed=300 + p)
+    g_ref, _, _ = oracle_mod.sensor(oracle_mod.Problem(**s), U)
+    g = gpu_sensor(gpu(s), U)
+    assert np.max(np.abs(g - g_ref)) <= 1e-12
+    assert 0.05 < np.mean(g > 1e-3)     # the random state does trigger the sensor
+
+
+@pytest.mark.parametrize("dim,p,flux,bc", [(1, 2, "burgers", "periodic"), (2, 2, "rotation", "inflow_zero"),
+                                           (2, 3, "kpp", "outflow"), (2, 1, "advect", "periodic")])
+def test_rk3_fp64(oracle_mod, dim, p, flux, bc):
+    s = H.spec(dim, p, 200 if dim == 1 else 12, ny=9, flux=flux, bc=bc)
+    U = H.state_for(s, seed=400 + p)
+    dt, n = 0.02 / s["nx"], 7
+    ref = oracle_mod.rk3(oracle_mod.Problem(**s), U, dt, n)
+    ctx = gpu(s)
+    Ud = to_dev(U, "fp64")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        ctx.rk_step(Ud, dt, n)
+    st.synchronize()
+    assert H.rel_l2(Ud.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dim,p,flux,stab", [(1, 2, "burgers", "weno"), (2, 1, "advect", "weno"),
+                                             (2, 2, "rotation", "weno"), (2, 3, "kpp", "weno"),
+                                             (2, 3, "burgers", "lo")])
+def test_residual_fp32_random(oracle_mod, dim, p, flux, stab):
+    s = H.spec(dim, p, 300 if dim == 1 else 19, ny=13, flux=flux, stab=stab,
+               bc="inflow_zero" if flux == "rotation" else "periodic")
+    U = H.state_for(s, seed=500 + p).astype(np.float32).astype(np.float64)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    got = gpu_residual(gpu(s, "fp32"), U)
+    assert H.rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dim,p,flux", [(1, 3, "advect"), (2, 2, "advect"), (2, 3, "burgers")])
+def test_rk3_fp32_smooth(oracle_mod, dim, p, flux):
+    """FP32 SSP-RK3 on smooth projected data: relative L2 <= 2e-5 after 20 steps."""
+    n = 64 if dim == 1 else 24
+    s = H.spec(dim, p, n, flux=flux)
+    X, Y = I.sample_points(dim, n, n, s["box"], 8)
+    f = np.sin(2 * np.pi * X) * (np.cos(2 * np.pi * Y) if dim == 2 else 1.0) + 0.5
+    # each side projects the same samples itself; CFL 0.05 keeps Q3 well inside the
+    # SSP-RK3 stability region (near the limit round-off is amplified, not the scheme)
+    U = oracle_mod.project(oracle_mod.Problem(**s), f).astype(np.float32).astype(np.float64)
+    vmax = 1.5 if flux == "burgers" else max(abs(s["a"][0]), abs(s["a"][1]))
+    dt = I.cfl_dt(0.05, [vmax] * dim, [1.0 / n] * dim)
+    ref = oracle_mod.rk3(oracle_mod.Problem(**s), U, dt, 20)
+    ctx = gpu(s, "fp32")
+    Ud = torch.empty((ctx.K, ctx.E), dtype=torch.float32, device="cuda")
+    ctx.project(torch.tensor(f.reshape(-1), device="cuda"), Ud)
+    ctx.rk_step(Ud, dt, 20)
+    torch.cuda.synchronize()
+    assert H.rel_l2(Ud.double().cpu().numpy(), ref) <= 2e-5
+
+
+@pytest.mark.parametrize("dim,p,prec", [(1, 2, "fp64"), (2, 3, "fp64"), (2, 2, "fp32")])
+def test_projection(oracle_mod, dim, p, prec):
+    n = 50 if dim == 1 else 21
+    s = H.spec(dim, p, n)
+    X, Y = I.sample_points(dim, n, n, s["box"], 8)
+    f = I.u0_rotation(X, Y) if dim == 2 else I.u0_mixed_1d(X)
+    ref = oracle_mod.project(oracle_mod.Problem(**s), f)
+    ctx = gpu(s, prec)
+    U = torch.empty((ctx.K, ctx.E), dtype=ctx.dtype, device="cuda")
+    ctx.project(torch.tensor(f.reshape(-1), device="cuda"), U)
+    torch.cuda.synchronize()
+    tol = 1e-13 if prec == "fp64" else 1e-7     # 64-term sums in both, different order
+    assert H.rel_l2(U.double().cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("dim,prec", [(1, "fp64"), (2, "fp64"), (2, "fp32")])
+def test_mass_conserved(oracle_mod, dim, prec):
+    s = H.spec(dim, 2, 40 if dim == 1 else 16, flux="burgers")
+    U = H.state_for(s, seed=7)
+    if prec == "fp32":
+        U = U.astype(np.float32).astype(np.float64)
+    ctx = gpu(s, prec)
+    Ud = to_dev(U, prec)
+    m0 = ctx.mass(Ud)
+    assert abs(m0 - oracle_mod.mass(oracle_mod.Problem(**s), U)) <= 1e-12 * max(1.0, abs(m0))
+    ctx.rk_step(Ud, 0.001, 10)
+    m1 = ctx.mass(Ud)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert abs(m1 - m0) <= tol * (1 + abs(m0))
+
+
+def test_edge_meshes(oracle_mod):
+    """Single-element periodic meshes (the element is its own neighbour), all-boundary
+    meshes, and element counts around the block size."""
+    for s in (H.spec(1, 2, 1), H.spec(2, 3, 1), H.spec(2, 2, 3, ny=2, bc="outflow"),
+              H.spec(1, 1, 127), H.spec(1, 1, 128), H.spec(1, 3, 129, bc="outflow"),
+              H.spec(2, 1, 1, ny=1, bc="inflow_zero", flux="rotation")):
+        U = H.state_for(s, seed=11)
+        ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+        got = gpu_residual(gpu(s), U)
+        assert H.rel_l2(got, ref) <= 1e-12, s
+
+
+def test_degenerate_states(oracle_mod):
+    """Constant states are steady (L = 0, gamma = 0).  A constant cell has beta_0 = 0,
+    so its own candidate dominates the weights: next to slope-1 neighbours
+    ||U - U*||_e ~ 1e-15 <= eps_s and gamma = 0; next to gentle slopes (1e-3) the
+    neighbours keep weight, ||U - U*||_e > eps_s while ||U||_e = 0, and gamma = 1."""
+    s = H.spec(2, 2, 8, flux="burgers")
+    ctx = gpu(s)
+    U = np.zeros((9, 64))
+    U[0] = 1.7
+    assert np.max(np.abs(gpu_residual(ctx, U))) <= 1e-12
+    assert np.all(gpu_sensor(ctx, U) == 0.0)
+    s1 = H.spec(1, 1, 3)
+    for slope, expect in ((1.0, 0.0), (1e-3, 1.0)):
+        U1 = np.array([[0.0, 0.0, 0.0], [slope, 0.0, slope]])
+        g = gpu_sensor(gpu(s1), U1)
+        g_ref, _, _ = oracle_mod.sensor(oracle_mod.Problem(**s1), U1)
+        assert g[1] == expect and g_ref[1] == expect and np.max(np.abs(g - g_ref)) <= 1e-12
+
+
+def test_graph_replay_matches_direct_launches():
+    """dgw_rk_step replays a cached CUDA graph on a non-default stream and launches
+    directly on the default stream: the results are bitwise identical, and repeat runs
+    are deterministic (no atomics in the arithmetic)."""
+    s = H.spec(2, 3, 33, ny=20, flux="kpp", bc="outflow")
+    U = H.state_for(s, seed=3)
+    outs = []
+    for mode in ("direct", "graph", "graph"):
+        ctx = gpu(s, "fp32")
+        Ud = to_dev(U, "fp32")
+        if mode == "direct":
+            ctx.rk_step(Ud, 1e-3, 37, stream=0)
+        else:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                ctx.rk_step(Ud, 1e-3, 37)
+            st.synchronize()
+        torch.cuda.synchronize()
+        outs.append(Ud.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_host_entry_matches_device_entry():
+    s = H.spec(2, 2, 16, flux="rotation", bc="inflow_zero")
+    U = H.state_for(s, seed=5)
+    ctx = gpu(s)
+    Ud = to_dev(U, "fp64")
+    ctx.rk_step(Ud, 1e-3, 5)
+    Uh = torch.tensor(U).pin_memory()
+    out = torch.empty_like(Uh).pin_memory()
+    ctx.rk_step_host(Uh, out, 1e-3, 5)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), Ud.cpu().numpy())
+
+
+def test_nonfinite_detected():
+    """An absurd time step overflows the update; the stage kernel flags it and
+    dgw_sync_status reports DGW_ENONFINITE (then clears the flag)."""
+    s = H.spec(1, 2, 64, flux="burgers")
+    ctx = gpu(s)
+    Ud = to_dev(H.state_for(s, seed=1), "fp64")
+    ctx.rk_step(Ud, 1e300, 2)
+    with pytest.raises(dgw.DGWError) as ei:
+        ctx.sync_status()
+    assert ei.value.status == -6
+    ctx.sync_status()   # cleared
+
+
+def _full_size_sampled(oracle_mod, s, prec, f, nsample, seed):
+    """Project f (samples at the 8-point Gauss points) on both sides; compare the
+    projections everywhere and the residuals on sampled elements."""
+    Po = oracle_mod.Problem(**s)
+    U_ref = oracle_mod.project(Po, f)
+    ctx = gpu(s, prec)
+    U = torch.empty((ctx.K, ctx.E), dtype=ctx.dtype, device="cuda")
+    ctx.project(torch.tensor(f.reshape(-1), device="cuda"), U)
+    L = torch.empty_like(U)
+    ctx.residual(U, L)
+    g = torch.empty(ctx.E, dtype=torch.float64, device="cuda")
+    ctx.sensor(U, g)
+    torch.cuda.synchronize()
+    U_gpu = U.double().cpu().numpy()
+    assert H.rel_l2(U_gpu, U_ref) <= (1e-13 if prec == "fp64" else 1e-7)
+    rng = np.random.default_rng(seed)
+    g_np = g.cpu().numpy()
+    active = np.flatnonzero(g_np > 1e-3)
+    idx = np.unique(np.concatenate([rng.choice(ctx.E, nsample // 2, replace=False),
+                                    rng.choice(active, min(nsample // 2, active.size), replace=False),
+                                    [0, ctx.E - 1, s["nx"] - 1, ctx.E - s["nx"]]]))
+    # the oracle evaluates its own projection, rounded to the kernel precision
+    U_in = U_ref.astype(np.float32).astype(np.float64) if prec == "fp32" else U_ref
+    L_ref = oracle_mod.residual_at(Po, U_in, idx)
+    g_ref = oracle_mod.sensor_at(Po, U_in, idx)
+    return L.double().cpu().numpy()[:, idx], L_ref, g_np[idx], g_ref
+
+
+def test_full_size_kpp_1024_q3_fp32_sampled(oracle_mod):
+    """KPP on [-2,2]x[-2.5,1.5], 1024^2 Q3, FP32, lambda_e = 2, outflow: sampled elements."""
+    n = 1024
+    s = dict(dim=2, nx=n, ny=n, p=3, box=(-2.0, 2.0, -2.5, 1.5), bc=("outflow",) * 4, flux="kpp",
+             lambda_nu=2.0, stab="weno")
+    X, Y = I.sample_points(2, n, n, s["box"], 8)
+    L, L_ref, g, g_ref = _full_size_sampled(oracle_mod, s, "fp32", I.u0_kpp(X, Y), 600, 1)
+    scale = np.max(np.abs(L_ref))
+    assert np.max(np.abs(L - L_ref)) <= 2e-5 * scale
+    assert np.max(np.abs(g - g_ref)) <= 1e-5
+
+
+def test_full_size_rotation_256_q2_fp64_sampled(oracle_mod):
+    n = 256
+    s = dict(dim=2, nx=n, ny=n, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("inflow_zero",) * 4, flux="rotation",
+             center=(0.5, 0.5), omega=1.0, stab="weno")
+    X, Y = I.sample_points(2, n, n, s["box"], 8)
+    L, L_ref, g, g_ref = _full_size_sampled(oracle_mod, s, "fp64", I.u0_rotation(X, Y), 600, 2)
+    assert H.rel_l2(L, L_ref) <= 1e-12
+    assert np.max(np.abs(g - g_ref)) <= 1e-12
