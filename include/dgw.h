@@ -162,6 +162,11 @@ dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream
  * Synchronizes the stream.  DGW_OK or DGW_ENONFINITE. */
 dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
 
+/* Diagnostic: the float sin/cos the FP32 kernels use for the KPP flux (Sec. 5 KPP
+ * problem, F = (sin u, cos u)), applied to n device floats x; results in s and c
+ * (device).  Exists so that tests can bound its error against double precision. */
+dgw_status dgw_selftest_sincos(const float* x, float* s, float* c, int64_t n, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* dgw_last_error(void);
 

@@ -12,6 +12,7 @@
 
 #include "../../include/dgw.h"
 #include "dgw_internal.h"
+#include "dgw_math.cuh"
 
 using namespace dgw;
 
@@ -502,6 +503,25 @@ extern "C" dgw_status dgw_sync_status(dgw_ctx* c, void* stream)
     DGW_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(unsigned), s));
     DGW_CUDA(cudaStreamSynchronize(s));
     if (v & 1u) return fail(DGW_ENONFINITE, "a stage produced a non-finite value");
+    return DGW_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// self-test of the float sin/cos used by the KPP flux
+// ------------------------------------------------------------------------------------
+__global__ void sincos_selftest_kernel(const float* x, float* s, float* c, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dgw::fast_sincos(x[i], &s[i], &c[i]);
+}
+
+extern "C" dgw_status dgw_selftest_sincos(const float* x, float* s, float* c, int64_t n, void* stream)
+{
+    if (!x || !s || !c || n < 0) return fail(DGW_EINVAL, "bad arguments");
+    if (n == 0) return DGW_OK;
+    const int threads = 256;
+    sincos_selftest_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(x, s, c, n);
+    DGW_CUDA(cudaGetLastError());
     return DGW_OK;
 }
 

@@ -53,7 +53,7 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_last_error", "dgw_version")
+           "dgw_sync_status", "dgw_selftest_sincos", "dgw_last_error", "dgw_version")
 
 
 def load(build: bool = True):
@@ -80,6 +80,7 @@ def load(build: bool = True):
         L.dgw_rk_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
+        L.dgw_selftest_sincos.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
         L.dgw_last_error.restype = ctypes.c_char_p
         L.dgw_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -225,6 +226,16 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+
+def selftest_sincos(x, stream=None):
+    """sin and cos of a CUDA float32 tensor by the kernels' reduced-argument path."""
+    import torch
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA float32 tensor")
+    s, c = torch.empty_like(x), torch.empty_like(x)
+    _check(load().dgw_selftest_sincos(_ptr(x), _ptr(s), _ptr(c), x.numel(), _stream(stream)))
+    return s, c
 
 
 def version() -> str:

@@ -299,3 +299,14 @@ def test_full_size_rotation_256_q2_fp64_sampled(oracle_mod):
     L, L_ref, g, g_ref = _full_size_sampled(oracle_mod, s, "fp64", I.u0_rotation(X, Y), 600, 2)
     assert H.rel_l2(L, L_ref) <= 1e-12
     assert np.max(np.abs(g - g_ref)) <= 1e-12
+
+
+def test_fast_sincos_error_bound():
+    """The float sin/cos of the KPP flux (2 pi Cody-Waite reduction + __sincosf) stays
+    within 1e-6 of double-precision sin/cos for |x| <= 64 (KPP states reach ~11)."""
+    x = torch.linspace(-64.0, 64.0, 2_000_001, dtype=torch.float32, device="cuda")
+    s, c = dgw.selftest_sincos(x)
+    torch.cuda.synchronize()
+    xd = x.double()
+    assert float((s.double() - torch.sin(xd)).abs().max()) <= 1e-6
+    assert float((c.double() - torch.cos(xd)).abs().max()) <= 1e-6
