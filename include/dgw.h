@@ -162,6 +162,26 @@ dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream
  * Synchronizes the stream.  DGW_OK or DGW_ENONFINITE. */
 dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
 
+/* SSP-RK3 steps for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment convenience).  Such callers include work recorded
+ * into a CUDA graph by stream capture, applications whose device memory belongs to
+ * another allocator, and real-time code that allows no allocation after start-up.
+ * The arguments combine those of dgw_create and dgw_rk_step, and the result equals
+ * theirs, but nothing is allocated: the two stage states live in one file-scope
+ * device array of 2 x 8 MiB (+256 bytes) that every GPU loading the library keeps
+ * until the process exits.  K*E*elem_bytes must not exceed 8,388,608 bytes
+ * (e.g. 256^2 cells of Q2 in FP64); larger states return DGW_EINVAL with a message.
+ * The first call on a device, and the first for each (precision, dimension, degree)
+ * there, looks up the array's device address and uploads the operator tables
+ * synchronously: make those calls before any stream capture.  Later calls only
+ * enqueue kernels on the stream.  All calls share the array, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race and corrupt each other:
+ * order them on one stream.  Non-finite results are not reported by this entry
+ * point (there is no context to hold the flag). */
+dgw_status dgw_rk_step_noalloc(const dgw_mesh* mesh, int p, const dgw_flux* flux,
+                               const dgw_params* params, void* U, double dt, int nsteps,
+                               void* stream);
+
 /* Diagnostic: the float sin/cos the FP32 kernels use for the KPP flux (Sec. 5 KPP
  * problem, F = (sin u, cos u)), applied to n device floats x; results in s and c
  * (device).  Exists so that tests can bound its error against double precision. */

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 
@@ -522,6 +524,106 @@ extern "C" dgw_status dgw_selftest_sincos(const float* x, float* s, float* c, in
     const int threads = 256;
     sincos_selftest_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(x, s, c, n);
     DGW_CUDA(cudaGetLastError());
+    return DGW_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// SSP-RK3 steps without any device allocation
+// ------------------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc: work being recorded into a CUDA graph by stream
+// capture (allocating there breaks or invalidates the capture), applications whose
+// device memory is owned by another allocator, and real-time code that allows no
+// allocation after start-up.  dgw_rk_step_noalloc serves them: instead of a context's
+// stage buffers it keeps the two SSP-RK3 stage states in this fixed array, which every
+// GPU that loads the library holds until the process exits.  Layout: stage 1, stage 2
+// (kNoAllocStageBytes each), then the kernels' error flag.  Nothing in it has to start
+// at zero: each stage buffer is written in full before it is read, and the flag is
+// only ever set.
+static const size_t kNoAllocStageBytes = (size_t)8 << 20;   // 8 MiB per stage state
+static __device__ __align__(256) unsigned char g_noalloc_scratch[2 * kNoAllocStageBytes + 256];
+
+static std::mutex g_noalloc_mu;
+static std::map<int, unsigned char*> g_noalloc_addr;        // device -> array address
+static std::set<std::tuple<int, int, int, int>> g_noalloc_tables;   // device, prec, dim, p
+
+extern "C" dgw_status dgw_rk_step_noalloc(const dgw_mesh* mesh, int p, const dgw_flux* flux,
+                                          const dgw_params* params, void* U, double dt,
+                                          int nsteps, void* stream)
+{
+    if (!mesh || !flux || !params || !U) return fail(DGW_EINVAL, "NULL argument to dgw_rk_step_noalloc");
+    const dgw_mesh& m = *mesh;
+    if (m.dim != 1 && m.dim != 2) return fail(DGW_EINVAL, "dim must be 1 or 2");
+    if (m.nx < 1 || (m.dim == 2 && m.ny < 1)) return fail(DGW_EINVAL, "nx, ny must be >= 1");
+    if (!(m.x1 > m.x0) || (m.dim == 2 && !(m.y1 > m.y0))) return fail(DGW_EINVAL, "empty box");
+    for (int f = 0; f < 2 * m.dim; ++f)
+        if (m.bc[f] < DGW_BC_PERIODIC || m.bc[f] > DGW_BC_OUTFLOW) return fail(DGW_EINVAL, "bad bc[%d]", f);
+    for (int a = 0; a < m.dim; ++a)
+        if ((m.bc[2 * a] == DGW_BC_PERIODIC) != (m.bc[2 * a + 1] == DGW_BC_PERIODIC))
+            return fail(DGW_EINVAL, "periodic sides must come in pairs");
+    const double hx = (m.x1 - m.x0) / m.nx;
+    if (m.dim == 2 && std::fabs(hx - (m.y1 - m.y0) / m.ny) > 1e-12 * hx)
+        return fail(DGW_EUNSUPPORTED, "2D cells must be square");
+    if (p < 1 || p > kMaxP) return fail(DGW_EUNSUPPORTED, "degree p=%d not built (1..3)", p);
+    if (flux->kind < DGW_FLUX_ADVECT || flux->kind > DGW_FLUX_KPP) return fail(DGW_EINVAL, "bad flux kind");
+    if (!(flux->lambda_nu >= 0.0)) return fail(DGW_EINVAL, "lambda_nu must be >= 0");
+    dgw_status st = check_params(params, m.dim);
+    if (st != DGW_OK) return st;
+    if (!aligned16(U)) return fail(DGW_EINVAL, "U must be 16-byte aligned");
+    if (nsteps < 0) return fail(DGW_EINVAL, "nsteps < 0");
+    if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
+    const int64_t E = m.dim == 1 ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
+    const int K = m.dim == 1 ? p + 1 : (p + 1) * (p + 1);
+    const int eb = params->prec == DGW_FP64 ? 8 : 4;
+    const double bytes = (double)K * (double)E * eb;
+    if (bytes > (double)kNoAllocStageBytes)
+        return fail(DGW_EINVAL,
+                    "dgw_rk_step_noalloc: a state of %.0f bytes exceeds the fixed stage capacity of %zu "
+                    "bytes (K*E*elem_bytes); use dgw_create/dgw_rk_step for larger meshes",
+                    bytes, kNoAllocStageBytes);
+    if (nsteps == 0) return DGW_OK;
+
+    int dev = -1;
+    DGW_CUDA(cudaGetDevice(&dev));
+    unsigned char* base = nullptr;
+    {
+        // once per device (with that device current): the array's device address, and
+        // the operator tables of this precision, dimension and degree
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        auto it = g_noalloc_addr.find(dev);
+        if (it == g_noalloc_addr.end()) {
+            void* ptr = nullptr;
+            DGW_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            it = g_noalloc_addr.emplace(dev, static_cast<unsigned char*>(ptr)).first;
+        }
+        base = it->second;
+        const auto key = std::make_tuple(dev, params->prec, m.dim, p);
+        if (!g_noalloc_tables.count(key)) {
+            HostTables t;
+            build_tables(p, &t);
+            cudaError_t ce;
+            if (params->prec == DGW_FP64) ce = m.dim == 1 ? upload_tables_f64_d1(t) : upload_tables_f64_d2(t);
+            else ce = m.dim == 1 ? upload_tables_f32_d1(t) : upload_tables_f32_d2(t);
+            if (ce != cudaSuccess) return fail(DGW_ECUDA, "table upload: %s", cudaGetErrorString(ce));
+            g_noalloc_tables.insert(key);
+        }
+    }
+
+    // A context that lives on the host stack and points into the fixed array.
+    dgw_ctx c;
+    c.device = dev;
+    c.mesh = m;
+    if (m.dim == 1) c.mesh.ny = 1;
+    c.p = p;
+    c.flux = *flux;
+    c.params = *params;
+    c.K = K;
+    c.E = E;
+    c.eb = eb;
+    c.h = hx;
+    c.S1 = base;
+    c.S2 = base + kNoAllocStageBytes;
+    c.flag = reinterpret_cast<unsigned*>(base + 2 * kNoAllocStageBytes);
+    DGW_CUDA(enqueue_steps(&c, U, dt, nsteps, (cudaStream_t)stream));
     return DGW_OK;
 }
 

@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_selftest_sincos", "dgw_last_error", "dgw_version")
+           "dgw_sync_status", "dgw_rk_step_noalloc", "dgw_selftest_sincos", "dgw_last_error",
+           "dgw_version")
 
 
 def load(build: bool = True):
@@ -80,6 +81,8 @@ def load(build: bool = True):
         L.dgw_rk_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
+        L.dgw_rk_step_noalloc.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.POINTER(Flux),
+                                          ctypes.POINTER(Params), vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_selftest_sincos.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
         L.dgw_last_error.restype = ctypes.c_char_p
         L.dgw_version.restype = ctypes.c_char_p
@@ -226,6 +229,18 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+
+def rk_step_noalloc(problem: Problem, U, dt: float, nsteps: int = 1, stream=None):
+    """dgw_rk_step_noalloc: SSP-RK3 steps with the stage states in the library's fixed
+    device array (no allocation; see include/dgw.h for the size limit and the rules)."""
+    import torch
+    want = torch.float64 if problem.prec == "fp64" else torch.float32
+    if not U.is_cuda or U.dtype != want or not U.is_contiguous() or U.numel() != problem.K * problem.E:
+        raise ValueError(f"state must be a contiguous CUDA {want} tensor of {problem.K}x{problem.E}")
+    m, f, s = problem.c_structs()
+    _check(load().dgw_rk_step_noalloc(ctypes.byref(m), problem.p, ctypes.byref(f), ctypes.byref(s), _ptr(U),
+                                      float(dt), int(nsteps), _stream(stream)))
 
 
 def selftest_sincos(x, stream=None):
