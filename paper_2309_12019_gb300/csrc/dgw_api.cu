@@ -10,6 +10,8 @@
 #include <string>
 #include <tuple>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/dgw.h"
@@ -59,6 +61,8 @@ struct dgw_ctx {
     double* mass_dev = nullptr;
     unsigned* flag = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<const void*, CUtensorMap> tmaps;   // TMA descriptors per state array (2D)
+    std::map<const void*, bool> no_tmap;
 };
 
 static const int kMassBlocks = 1024;
@@ -198,6 +202,56 @@ extern "C" dgw_status dgw_set_params(dgw_ctx* c, const dgw_params* s)
     return DGW_OK;
 }
 
+// TMA descriptor of a state array viewed as a 3D tensor (x: nx, y: ny, k: K) with the
+// stage-tile box (kBoxX2 x kBoxY2 x K).  Null when TMA does not apply: 1D meshes, or
+// row / plane strides that are not multiples of 16 bytes.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U)
+{
+    dgw_ctx* c = const_cast<dgw_ctx*>(cc);
+    if (c->mesh.dim != 2) return nullptr;
+    auto it = c->tmaps.find(U);
+    if (it != c->tmaps.end()) return &it->second;
+    if (c->no_tmap.count(U)) return nullptr;
+    const uint64_t eb = (uint64_t)c->eb, nx = (uint64_t)c->mesh.nx, ny = (uint64_t)c->mesh.ny;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (nx * eb) % 16 || (nx * ny * eb) % 16 || ((uintptr_t)U & 15u)) {
+        c->no_tmap[U] = true;
+        return nullptr;
+    }
+    cuuint64_t dims[3] = {nx, ny, (cuuint64_t)c->K};
+    cuuint64_t strides[2] = {nx * eb, nx * ny * eb};
+    cuuint32_t box[3] = {(cuuint32_t)kBoxX2, (cuuint32_t)kBoxY2, (cuuint32_t)c->K};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    CUresult r = enc(&m, eb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                     const_cast<void*>(U), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->no_tmap[U] = true;
+        return nullptr;
+    }
+    if (c->tmaps.size() > 64) c->tmaps.clear();
+    return &(c->tmaps[U] = m);
+}
+
 static StageArgs base_args(const dgw_ctx* c)
 {
     StageArgs a;
@@ -225,8 +279,10 @@ static StageArgs base_args(const dgw_ctx* c)
     return a;
 }
 
-static cudaError_t launch(const dgw_ctx* c, const StageArgs& a, int mode, cudaStream_t s)
+static cudaError_t launch(const dgw_ctx* c, const StageArgs& a0, int mode, cudaStream_t s)
 {
+    StageArgs a = a0;
+    a.tmap = tensor_map(c, a.Uk);
     const bool f64 = c->params.prec == DGW_FP64;
     if (c->mesh.dim == 1)
         return f64 ? launch_stage_f64_d1(a, c->p, c->flux.kind, mode, s)

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace dgw {
@@ -11,6 +12,14 @@ constexpr int kMaxP = 3;
 constexpr int kMaxN1 = kMaxP + 1;          // modes per direction
 constexpr int kMaxNQ = kMaxP + 2;          // Gauss points per direction (p + 2)
 constexpr int kMaxK = kMaxN1 * kMaxN1;     // modes per element (2D)
+
+// 2D stage tile: TX x TY cells, one thread each.  Its TMA box spans TX + 8 columns
+// (the halo column on each side, widened so the box starts on a 16-byte boundary)
+// and TY + 2 rows, for all K modes.
+constexpr int kTileX2 = 32;
+constexpr int kTileY2 = 4;
+constexpr int kBoxX2 = kTileX2 + 8;
+constexpr int kBoxY2 = kTileY2 + 2;
 
 enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2 };
 enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3 };
@@ -51,7 +60,8 @@ struct StageArgs {
     int stab;
     double q, b, w_nbr, eps_w, eps_s;
     double* gamma_out;     // optional per-element gamma (double)
-    unsigned* flag;        // bit 0: non-finite output
+    unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
+    const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x kBoxY2 x K), or null
 };
 
 // Launchers, one per (precision, dimension) translation unit.  mode 0: stage or

@@ -3,19 +3,23 @@
 // Included by one translation unit per (precision, dimension) with DGW_REAL, DGW_DIM
 // and DGW_NS defined.  Each unit owns its copy of the constant-memory operator tables.
 //
-// One CTA owns a TX x TY tile of cells (one thread per cell).  It stages the tile's
-// modal coefficients plus a one-cell face halo in shared memory, then
-//   A. evaluates every face of the tile once: traces from both sides, the local
-//      Lax-Friedrichs flux (Sec. 2) at the p+2 Gauss points, lifted onto the face
-//      Legendre modes, into shared memory;
-//   B. per cell: the WENO sensor from the four face neighbours in shared memory
-//      (Sec. 4), the volume term (Eq. weak2) by sum factorisation, the face
-//      contributions, the stabilization gamma nu K c (Sec. 3), M^{-1} and the
-//      SSP-RK3 combination Uout = cn Un + ck Uk + cl L(Uk) (Eq. ssp).
+// One CTA owns a TX x TY tile of cells (one thread per cell).
+//   0. It stages the modal coefficients of the tile plus a one-cell face halo in shared
+//      memory: one TMA box load (2D, 16-byte aligned strides) waited on through an
+//      mbarrier with a bounded spin, else cooperative coalesced loads; periodic halo
+//      cells of boundary tiles are then filled from the wrapped side.
+//   1. Per cell: the traces of its polynomial on its faces (shared memory), the WENO
+//      sensor from the four face neighbours (Sec. 4), the volume term (Eq. weak2) by
+//      sum factorisation, kept in registers.
+//   2. Every face of the tile once: both traces at the p+2 Gauss points, the local
+//      Lax-Friedrichs flux (Sec. 2), lifted onto the face Legendre modes.
+//   3. Per cell: face contributions, the stabilization gamma nu K c (Sec. 3), M^{-1}
+//      and the SSP-RK3 combination Uout = cn Un + ck Uk + cl L(Uk) (Eq. ssp).
 // Constant factors are folded so that, in the reference element,
 //   L_k = (2/h) minv(k) [acc_k - gamma lambda / p (K_ref c)_k].
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "dgw_internal.h"
 #include "dgw_math.cuh"
@@ -28,12 +32,14 @@ constexpr int DIM = DGW_DIM;
 constexpr bool kF32 = sizeof(Real) == 4;
 
 // tile: 128 threads, one cell each
-constexpr int TX = DIM == 1 ? 128 : 32;
-constexpr int TY = DIM == 1 ? 1 : 4;
+constexpr int TX = DIM == 1 ? 128 : kTileX2;
+constexpr int TY = DIM == 1 ? 1 : kTileY2;
 constexpr int NT = TX * TY;
-constexpr int HX = TX + 2;                 // staged columns (one halo cell each side)
+constexpr int HX = TX + 8;                 // staged columns: tile at [OX, OX+TX), halo OX-1, OX+TX
+constexpr int OX = 4;
 constexpr int HY = DIM == 1 ? 1 : TY + 2;  // staged rows
 constexpr int OY = DIM == 1 ? 0 : 1;       // row offset of the tile inside the stage
+static_assert(DIM == 1 || (HX == kBoxX2 && HY == kBoxY2), "TMA box and stage layout disagree");
 
 template <int P>
 struct Tab {
@@ -86,7 +92,9 @@ static cudaError_t upload(const HostTables& h)
 }
 
 // Scalars of one launch, converted once on the host to the kernel precision.
-struct KParams {
+struct alignas(64) KParams {
+    CUtensorMap tmap;    // TMA descriptor of Uk (valid when use_tma)
+    int use_tma;
     const Real* Uk;
     const Real* Un;
     Real* Uout;
@@ -241,141 +249,171 @@ __device__ __forceinline__ int wrap_y(const KParams& A, int gy)
     return -1;
 }
 
+// Bounded wait on phase 0 of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait0(uint32_t bar)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok) : "r"(bar) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // MODE 0: stage / residual; MODE 1: sensor only.
 template <int P, int FLUX, int MODE>
-__global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
+__global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_constant__ KParams A)
 {
     constexpr int N1 = P + 1, NQ = P + 2;
     constexpr int K = Tab<P>::K;
     constexpr int NFX = (TX + 1) * TY;                 // x-faces of the tile
     constexpr int NFY = DIM == 2 ? TX * (TY + 1) : 0;  // y-faces
+    constexpr int TN = DIM == 1 ? 1 : N1;              // trace / face coefficients
     const Tab<P>& T = tab<P>();
 
-    __shared__ Real su[K][HY][HX];
-    __shared__ Real hfx[TY][TX + 1][DIM == 1 ? 1 : N1];
-    __shared__ Real hfy[DIM == 2 ? TY + 1 : 1][TX][DIM == 2 ? N1 : 1];
+    __shared__ alignas(128) Real su[K][HY][HX];
+    // cell index innermost: a warp touches consecutive words (no bank conflicts)
+    __shared__ Real trx[TY][2][TN][TX + 2];                          // x-traces, col = lx + 1
+    __shared__ Real trys[DIM == 2 ? TY + 2 : 1][2][TN][TX];          // y-traces, row = ly + 1
+    __shared__ Real hfx[TY][TN][TX + 1];
+    __shared__ Real hfy[DIM == 2 ? TY + 1 : 1][TN][TX];
     __shared__ Real lam_s[TY][TX];
+    __shared__ alignas(8) uint64_t mbar;
+    __shared__ int fail_s;
 
     const int tid = threadIdx.x;
     const int tx0 = blockIdx.x * TX;
     const int ty0 = DIM == 2 ? blockIdx.y * TY : 0;
     const int64_t E = A.E;
     const bool need_lam = (MODE == 0) && (A.stab != STAB_DG) && !A.lam_fixed;
+    const bool periodic_x = A.bc[0] == BC_PERIODIC;
+    const bool periodic_y = DIM == 2 && A.bc[2] == BC_PERIODIC;
 
-    // ---- stage the tile and its face halo (corners are not needed) ----
-    for (int idx = tid; idx < K * HY * HX; idx += NT) {
-        const int k = idx / (HY * HX);
-        const int rem = idx - k * (HY * HX);
-        const int r = rem / HX, cc = rem - r * HX;
-        const bool corner = DIM == 2 && (r == 0 || r == HY - 1) && (cc == 0 || cc == HX - 1);
-        if (corner) continue;
-        const int gx = wrap_x(A, tx0 - 1 + cc);
-        const int gy = DIM == 2 ? wrap_y(A, ty0 - OY + r) : 0;
-        if (gx < 0 || gy < 0) continue;
-        su[k][r][cc] = A.Uk[k * E + (int64_t)gy * A.nx + gx];
-    }
-    if (need_lam) lam_s[tid / TX][tid % TX] = Real(0);
-    __syncthreads();
-
-    // ---- A. faces: each face of the tile once ----
-    if (MODE == 0) {
-        for (int f = tid; f < NFX + NFY; f += NT) {
-            const bool xf = f < NFX;
-            int lx, ly;              // tile position of the cell on the plus side of the face
-            if (xf) { ly = f / (TX + 1); lx = f - ly * (TX + 1); }
-            else { const int g = f - NFX; ly = g / TX; lx = g - ly * TX; }
-            const int gx = tx0 + lx, gy = ty0 + ly;   // plus-side cell (global, unwrapped)
-            // the face lies at x = x0 + gx h (x-face) or y = y0 + gy h (y-face)
-            if (xf) { if (gx > A.nx || gy >= A.ny) continue; }
-            else { if (gy > A.ny || gx >= A.nx) continue; }
-            const int axis = xf ? 0 : 1;
-            const bool minus_in = xf ? (gx - 1 >= 0 || A.bc[0] == BC_PERIODIC)
-                                     : (gy - 1 >= 0 || A.bc[2] == BC_PERIODIC);
-            const bool plus_in = xf ? (gx < A.nx || A.bc[1] == BC_PERIODIC)
-                                    : (gy < A.ny || A.bc[3] == BC_PERIODIC);
-            // stage coordinates of the two cells
-            const int pr = ly + OY, pc = lx + 1;
-            const int mr = xf ? pr : pr - 1, mc = xf ? pc - 1 : pc;
-            // trace coefficients along the face: minus cell at xi = +1, plus cell at xi = -1
-            Real tm[N1], tp[N1];
-#pragma unroll
-            for (int t = 0; t < N1; ++t) {
-                Real sm = Real(0), sp = Real(0);
-#pragma unroll
-                for (int n = 0; n < N1; ++n) {
-                    const int k = DIM == 1 ? n : (xf ? n + N1 * t : t + N1 * n);
-                    if (DIM == 1 && t > 0) break;
-                    if (minus_in) sm += su[k][mr][mc];
-                    if (plus_in) sp += ((n & 1) ? Real(-1) : Real(1)) * su[k][pr][pc];
-                }
-                tm[t] = sm;
-                tp[t] = sp;
+    // ---- 0. stage the tile and its face halo ----
+    if (DIM == 2 && A.use_tma) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+        if (tid == 0) {
+            fail_s = 0;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(sizeof(Real) * K * HY * HX);
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(bar), "r"(bytes) : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];"
+                :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&A.tmap)), "r"(tx0 - OX), "r"(ty0 - OY),
+                   "r"(0), "r"(bar)
+                : "memory");
+        }
+        if (!mbar_wait0(bar)) fail_s = 1;
+        __syncthreads();
+        if (fail_s) {
+            if (tid == 0) atomicOr(A.flag, 2u);
+            return;
+        }
+        // periodic images of halo cells that lie outside the box's wrap-free view
+        const bool edge = (periodic_x && (tx0 == 0 || tx0 + TX >= A.nx)) ||
+                          (periodic_y && (ty0 == 0 || ty0 + TY >= A.ny));
+        if (edge) {
+            for (int idx = tid; idx < K * HY * HX; idx += NT) {
+                const int k = idx / (HY * HX);
+                const int rem = idx - k * (HY * HX);
+                const int r = rem / HX, cc = rem - r * HX;
+                const int ux = tx0 - OX + cc, uy = ty0 - OY + r;     // unwrapped
+                if (ux < -1 || ux > A.nx || uy < -1 || uy > A.ny) continue;
+                const bool inx = ux >= 0 && ux < A.nx, iny = uy >= 0 && uy < A.ny;
+                if (inx && iny) continue;          // delivered by the box
+                if (!inx && !iny) continue;        // corner: not needed
+                const int gx = wrap_x(A, ux), gy = wrap_y(A, uy);
+                if (gx < 0 || gy < 0) continue;
+                su[k][r][cc] = A.Uk[k * E + (int64_t)gy * A.nx + gx];
             }
-            Real hq[N1];
+            __syncthreads();
+        }
+    } else {
+        for (int idx = tid; idx < HY * HX; idx += NT) {
+            const int r = idx / HX, cc = idx - r * HX;
+            if (cc < OX - 1 || cc > OX + TX) continue;
+            const bool corner = DIM == 2 && (r == 0 || r == HY - 1) && (cc == OX - 1 || cc == OX + TX);
+            if (corner) continue;
+            const int gx = wrap_x(A, tx0 - OX + cc);
+            const int gy = DIM == 2 ? wrap_y(A, ty0 - OY + r) : 0;
+            if (gx < 0 || gy < 0) continue;
+            const Real* src = A.Uk + (int64_t)gy * A.nx + gx;
 #pragma unroll
-            for (int t = 0; t < N1; ++t) hq[t] = Real(0);
-            Real lm = Real(0), lp = Real(0);
-            constexpr int NFQ = DIM == 1 ? 1 : NQ;
-#pragma unroll
-            for (int q = 0; q < NFQ; ++q) {
-                Real uL = Real(0), uR = Real(0);
-                if (DIM == 1) { uL = tm[0]; uR = tp[0]; }
-                else {
-#pragma unroll
-                    for (int t = 0; t < N1; ++t) { uL = fma(tm[t], T.B[q][t], uL); uR = fma(tp[t], T.B[q][t], uR); }
-                }
-                Real x, y;
-                if (xf) { x = A.x0 + Real(gx) * A.h; y = DIM == 2 ? A.y0 + (Real(gy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
-                else { x = A.x0 + (Real(gx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(gy) * A.h; }
-                if (!minus_in) {
-                    // ghost for the plus cell, whose outward normal is -e_axis
-                    const int side = xf ? 0 : 2;
-                    uL = (A.bc[side] == BC_INFLOW_ZERO && -dflux_axis<FLUX>(A, axis, uR, x, y) < Real(0)) ? Real(0) : uR;
-                } else if (!plus_in) {
-                    const int side = xf ? 1 : 3;
-                    uR = (A.bc[side] == BC_INFLOW_ZERO && dflux_axis<FLUX>(A, axis, uL, x, y) < Real(0)) ? Real(0) : uL;
-                }
-                if (need_lam) {
-                    lm = fmax(lm, speed_norm<FLUX>(A, uL, x, y));
-                    lp = fmax(lp, speed_norm<FLUX>(A, uR, x, y));
-                }
-                const Real H = llf<FLUX>(A, axis, uL, uR, x, y) * (DIM == 1 ? Real(1) : T.w[q]);
-#pragma unroll
-                for (int t = 0; t < N1; ++t) hq[t] = fma(DIM == 1 ? Real(1) : T.B[q][t], H, hq[t]);
-            }
-            if (xf) {
-#pragma unroll
-                for (int t = 0; t < (DIM == 1 ? 1 : N1); ++t) hfx[ly][lx][t] = hq[t];
-            } else {
-#pragma unroll
-                for (int t = 0; t < N1; ++t) hfy[DIM == 2 ? ly : 0][lx][t] = hq[t];
-            }
-            if (need_lam) {
-                // only the traces of cells of this tile that lie in the domain count
-                const int mlx = xf ? lx - 1 : lx, mly = xf ? ly : ly - 1;
-                if (minus_in && mlx >= 0 && mly >= 0 && (xf ? gx - 1 < A.nx : gy - 1 < A.ny))
-                    atomic_max_nonneg(&lam_s[mly][mlx], lm);
-                if (plus_in && lx < TX && ly < TY && gx < A.nx && gy < A.ny)
-                    atomic_max_nonneg(&lam_s[ly][lx], lp);
-            }
+            for (int k = 0; k < K; ++k) su[k][r][cc] = src[k * E];
         }
         __syncthreads();
     }
 
-    // ---- B. per cell ----
     const int lx = tid % TX, ly = tid / TX;
     const int gx = tx0 + lx, gy = ty0 + ly;
-    if (gx >= A.nx || (DIM == 2 && gy >= A.ny)) return;
-    const int64_t e = (int64_t)gy * A.nx + gx;
-    const int sr = ly + OY, sc = lx + 1;
+    const bool in_domain = gx < A.nx && (DIM == 1 || gy < A.ny);
+    const int sr = ly + OY, sc = lx + OX;
 
     Real c[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) c[k] = su[k][sr][sc];
 
-    // sensor (Sec. 4): Hermite candidates of the face neighbours, nonlinear weights
+    // ---- 1a. traces of this cell's slot (also for slots that hold periodic images) ----
+    if (MODE == 0) {
+#pragma unroll
+        for (int t = 0; t < TN; ++t) {
+            Real xm = Real(0), xp = Real(0), ym = Real(0), yp = Real(0);
+#pragma unroll
+            for (int n = 0; n < N1; ++n) {
+                const Real kx = DIM == 1 ? c[n] : c[n + N1 * t];
+                xp += kx;
+                xm += (n & 1) ? -kx : kx;
+                if (DIM == 2) {
+                    const Real ky = c[t + N1 * n];
+                    yp += ky;
+                    ym += (n & 1) ? -ky : ky;
+                }
+            }
+            trx[ly][0][t][lx + 1] = xm;
+            trx[ly][1][t][lx + 1] = xp;
+            if (DIM == 2) {
+                trys[ly + 1][0][t][lx] = ym;
+                trys[ly + 1][1][t][lx] = yp;
+            }
+        }
+        // halo cells: the one trace that faces the tile
+        constexpr int NH = 2 * TY + (DIM == 2 ? 2 * TX : 0);
+        for (int hidx = tid; hidx < NH; hidx += NT) {
+            int r, cc, side, axis;
+            if (hidx < TY) { r = hidx + OY; cc = OX - 1; axis = 0; side = 1; }
+            else if (hidx < 2 * TY) { r = hidx - TY + OY; cc = OX + TX; axis = 0; side = 0; }
+            else if (hidx < 2 * TY + TX) { r = 0; cc = OX + hidx - 2 * TY; axis = 1; side = 1; }
+            else { r = HY - 1; cc = OX + hidx - 2 * TY - TX; axis = 1; side = 0; }
+#pragma unroll
+            for (int t = 0; t < TN; ++t) {
+                Real v = Real(0);
+#pragma unroll
+                for (int n = 0; n < N1; ++n) {
+                    const int k = DIM == 1 ? n : (axis == 0 ? n + N1 * t : t + N1 * n);
+                    const Real ck = su[k][r][cc];
+                    v += (side == 0 && (n & 1)) ? -ck : ck;
+                }
+                if (axis == 0) trx[r - OY][side][t][cc == OX - 1 ? 0 : TX + 1] = v;
+                else trys[r == 0 ? 0 : TY + 1][side][t][cc - OX] = v;
+            }
+        }
+        if (need_lam) lam_s[ly][lx] = Real(0);
+    }
+
+    // ---- 1b. sensor (Sec. 4): Hermite candidates of the face neighbours ----
     Real gamma = (MODE == 0 && A.stab == STAB_LO) ? Real(1) : Real(0);
-    if (MODE == 1 || A.stab == STAB_WENO) {
+    if ((MODE == 1 || A.stab == STAB_WENO) && in_domain) {
         bool has[2 * DIM];
         int me = 0;
 #pragma unroll
@@ -397,19 +435,22 @@ __global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
             const int axis = f >> 1, side = f & 1;
             const int nr = sr + (f == 2 ? -1 : (f == 3 ? 1 : 0));
             const int nc = sc + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+            Real cn[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) cn[k] = su[k][nr][nc];
             Real cl[K];
 #pragma unroll
             for (int k = 1; k < K; ++k) {
                 const int i = k % N1, j = k / N1;
                 const int a = axis == 0 ? i : j;
-                Real s = Real(0);
+                Real sacc = Real(0);
 #pragma unroll
                 for (int m = 0; m < N1; ++m) {
                     if (m < a) continue;   // P_m(xi +- 2) has degree m
                     const int km = axis == 0 ? m + N1 * j : i + N1 * m;
-                    s = fma(T.T[side][a][m], su[km][nr][nc], s);
+                    sacc = fma(T.T[side][a][m], cn[km], sacc);
                 }
-                cl[k] = s;
+                cl[k] = sacc;
             }
             cl[0] = Real(0);
             const Real dl = A.eps_w + qform<P>(T, cl);
@@ -434,18 +475,15 @@ __global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
             if (!A.q_one) gamma = pow(gamma, A.q);
             if (r < A.b) gamma = Real(0);
         }
-        if (MODE == 1) {
-            A.gamma_out[e] = (double)gamma;
-            return;
-        }
+        if (MODE == 1) A.gamma_out[(int64_t)gy * A.nx + gx] = (double)gamma;
     }
     if (MODE == 1) return;
 
-    // volume term (Eq. weak2), sum-factorised: acc_ij = sum_q W_q [D_i B_j Fx + B_i D_j Fy]
+    // ---- 1c. volume term (Eq. weak2): acc_ij = sum_q W_q [D_i B_j Fx + B_i D_j Fy] ----
     Real acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = Real(0);
-    Real lam = need_lam ? lam_s[ly][lx] : Real(0);
+    Real lam = Real(0);
     const Real xc = A.x0 + (Real(gx) + Real(0.5)) * A.h;
     const Real yc = DIM == 2 ? A.y0 + (Real(gy) + Real(0.5)) * A.h : Real(0);
     if (DIM == 1) {
@@ -467,10 +505,10 @@ __global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
         for (int j = 0; j < N1; ++j)
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
-                Real s = Real(0);
+                Real sacc = Real(0);
 #pragma unroll
-                for (int i = 0; i < N1; ++i) s = fma(c[i + N1 * j], T.B[qx][i], s);
-                tmp[j][qx] = s;
+                for (int i = 0; i < N1; ++i) sacc = fma(c[i + N1 * j], T.B[qx][i], sacc);
+                tmp[j][qx] = sacc;
             }
 #pragma unroll
         for (int qy = 0; qy < NQ; ++qy) {
@@ -501,17 +539,90 @@ __global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
             }
         }
     }
+    __syncthreads();
 
-    // faces: -phi_k(+1) H on the plus faces, +phi_k(-1) H on the minus faces
+    // ---- 2. faces: each face of the tile once, from the traces ----
+    for (int f = tid; f < NFX + NFY; f += NT) {
+        const bool xf = f < NFX;
+        int flx, fly;              // tile position of the cell on the plus side of the face
+        if (xf) { fly = f / (TX + 1); flx = f - fly * (TX + 1); }
+        else { const int g = f - NFX; fly = g / TX; flx = g - fly * TX; }
+        const int fgx = tx0 + flx, fgy = ty0 + fly;   // plus-side cell (global, unwrapped)
+        if (xf) { if (fgx > A.nx || fgy >= A.ny) continue; }
+        else { if (fgy > A.ny || fgx >= A.nx) continue; }
+        const int axis = xf ? 0 : 1;
+        const bool minus_in = xf ? (fgx - 1 >= 0 || periodic_x) : (fgy - 1 >= 0 || periodic_y);
+        const bool plus_in = xf ? (fgx < A.nx || periodic_x) : (fgy < A.ny || periodic_y);
+        Real tm[TN], tp[TN];
+#pragma unroll
+        for (int t = 0; t < TN; ++t) {
+            if (xf) { tm[t] = trx[fly][1][t][flx]; tp[t] = trx[fly][0][t][flx + 1]; }
+            else { tm[t] = trys[DIM == 2 ? fly : 0][1][t][flx]; tp[t] = trys[DIM == 2 ? fly + 1 : 0][0][t][flx]; }
+        }
+        Real hq[TN];
+#pragma unroll
+        for (int t = 0; t < TN; ++t) hq[t] = Real(0);
+        Real lm = Real(0), lp = Real(0);
+        constexpr int NFQ = DIM == 1 ? 1 : NQ;
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) {
+            Real uL = Real(0), uR = Real(0);
+            if (DIM == 1) { uL = tm[0]; uR = tp[0]; }
+            else {
+#pragma unroll
+                for (int t = 0; t < TN; ++t) { uL = fma(tm[t], T.B[q][t], uL); uR = fma(tp[t], T.B[q][t], uR); }
+            }
+            Real x = Real(0), y = Real(0);
+            if (FLUX == FLUX_ROTATION || need_lam || !minus_in || !plus_in) {
+                if (xf) { x = A.x0 + Real(fgx) * A.h; y = DIM == 2 ? A.y0 + (Real(fgy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
+                else { x = A.x0 + (Real(fgx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(fgy) * A.h; }
+            }
+            if (!minus_in) {
+                // ghost for the plus cell, whose outward normal is -e_axis
+                const int bside = xf ? 0 : 2;
+                uL = (A.bc[bside] == BC_INFLOW_ZERO && -dflux_axis<FLUX>(A, axis, uR, x, y) < Real(0)) ? Real(0) : uR;
+            } else if (!plus_in) {
+                const int bside = xf ? 1 : 3;
+                uR = (A.bc[bside] == BC_INFLOW_ZERO && dflux_axis<FLUX>(A, axis, uL, x, y) < Real(0)) ? Real(0) : uL;
+            }
+            if (need_lam) {
+                lm = fmax(lm, speed_norm<FLUX>(A, uL, x, y));
+                lp = fmax(lp, speed_norm<FLUX>(A, uR, x, y));
+            }
+            const Real H = llf<FLUX>(A, axis, uL, uR, x, y) * (DIM == 1 ? Real(1) : T.w[q]);
+#pragma unroll
+            for (int t = 0; t < TN; ++t) hq[t] = fma(DIM == 1 ? Real(1) : T.B[q][t], H, hq[t]);
+        }
+        if (xf) {
+#pragma unroll
+            for (int t = 0; t < TN; ++t) hfx[fly][t][flx] = hq[t];
+        } else {
+#pragma unroll
+            for (int t = 0; t < TN; ++t) hfy[DIM == 2 ? fly : 0][t][flx] = hq[t];
+        }
+        if (need_lam) {
+            // only traces of this tile's cells that lie in the domain count
+            const int mlx = xf ? flx - 1 : flx, mly = xf ? fly : fly - 1;
+            if (minus_in && mlx >= 0 && mly >= 0 && (xf ? fgx - 1 < A.nx : fgy - 1 < A.ny))
+                atomic_max_nonneg(&lam_s[mly][mlx], lm);
+            if (plus_in && flx < TX && fly < TY && fgx < A.nx && fgy < A.ny)
+                atomic_max_nonneg(&lam_s[fly][flx], lp);
+        }
+    }
+    __syncthreads();
+    if (!in_domain) return;
+    const int64_t e = (int64_t)gy * A.nx + gx;
+
+    // ---- 3. faces: -phi_k(+1) H on the plus faces, +phi_k(-1) H on the minus faces ----
     if (DIM == 1) {
-        const Real hm = hfx[0][lx][0], hp = hfx[0][lx + 1][0];
+        const Real hm = hfx[0][0][lx], hp = hfx[0][0][lx + 1];
 #pragma unroll
         for (int n = 0; n < N1; ++n) acc[n] += ((n & 1) ? -hm : hm) - hp;
     } else {
 #pragma unroll
         for (int t = 0; t < N1; ++t) {
-            const Real xm = hfx[ly][lx][t], xp = hfx[ly][lx + 1][t];
-            const Real ym = hfy[ly][lx][t], yp = hfy[ly + 1][lx][t];
+            const Real xm = hfx[ly][t][lx], xp = hfx[ly][t][lx + 1];
+            const Real ym = hfy[DIM == 2 ? ly : 0][t][lx], yp = hfy[DIM == 2 ? ly + 1 : 0][t][lx];
 #pragma unroll
             for (int n = 0; n < N1; ++n) {
                 acc[n + N1 * t] += ((n & 1) ? -xm : xm) - xp;
@@ -519,11 +630,14 @@ __global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
             }
         }
     }
+    if (need_lam) lam = fmax(lam, lam_s[ly][lx]);
 
     // stabilization (Sec. 3), M^{-1}, RK combination (Eq. ssp)
     const Real lamv = A.lam_fixed ? A.lambda_nu : lam;
     const Real gs = gamma * lamv / Real(P);   // gamma nu (2/h)
-    bool bad = false;
+    Real chk = Real(0);                        // becomes NaN if any output is not finite
+    const Real* __restrict__ un = A.Un + e;
+    Real* __restrict__ uo = A.Uout + e;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int i = k % N1, j = k / N1;
@@ -549,16 +663,22 @@ __global__ void __launch_bounds__(NT) stage_kernel(const KParams A)
         if (DIM == 2) mi *= T.minv[j];
         const Real L = A.two_h * mi * r;
         Real out = A.cl * L + A.ck * c[k];
-        if (A.has_un) out += A.cn * A.Un[k * E + e];
-        bad |= !isfinite(out);
-        A.Uout[k * E + e] = out;
+        if (A.has_un) out += A.cn * un[k * E];
+        chk = fma(out, Real(0), chk);
+        uo[k * E] = out;
     }
-    if (bad) atomicOr(A.flag, 1u);
+    if (chk != chk) atomicOr(A.flag, 1u);
 }
 
 static KParams make_params(const StageArgs& s)
 {
     KParams a;
+    memset(&a, 0, sizeof a);
+    a.use_tma = 0;
+    if (s.tmap) {
+        a.tmap = *s.tmap;
+        a.use_tma = 1;
+    }
     a.Uk = static_cast<const Real*>(s.Uk);
     a.Un = static_cast<const Real*>(s.Un);
     a.Uout = static_cast<Real*>(s.Uout);
