@@ -40,9 +40,11 @@ WORKLOADS = {
     "rotation_256x256_q2": dict(dim=2, nx=256, ny=256, p=2, box=(0.0, 1.0, 0.0, 1.0),
                                 bc=("inflow_zero",) * 4, flux="rotation", center=(0.5, 0.5), omega=1.0,
                                 stab="weno", cfl=0.1, speeds=(0.5, 0.5), u0="rotation"),
+    "advect1d_128_p2": dict(dim=1, nx=128, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4,
+                            flux="advect", a=(1.0, 0.0), stab="weno", cfl=0.1, speeds=(1.0,), u0="mixed1d"),
 }
 
-SPEC_KEYS = ("dim", "nx", "ny", "p", "box", "bc", "flux", "lambda_nu", "stab", "center", "omega")
+SPEC_KEYS = ("dim", "nx", "ny", "p", "box", "bc", "flux", "lambda_nu", "stab", "center", "omega", "a")
 
 
 def spec_of(w):
@@ -51,13 +53,18 @@ def spec_of(w):
 
 def initial_samples(w):
     X, Y = I.sample_points(w["dim"], w["nx"], w["ny"], w["box"], 8)
-    f = I.u0_kpp(X, Y) if w["u0"] == "kpp" else I.u0_rotation(X, Y)
+    if w["u0"] == "kpp":
+        f = I.u0_kpp(X, Y)
+    elif w["u0"] == "rotation":
+        f = I.u0_rotation(X, Y)
+    else:
+        f = I.u0_mixed_1d(X)
     return np.ascontiguousarray(f.reshape(-1))
 
 
 def dt_of(w):
     h = (w["box"][1] - w["box"][0]) / w["nx"]
-    return I.cfl_dt(w["cfl"], w["speeds"], [h, h])
+    return I.cfl_dt(w["cfl"], w["speeds"], [h] * w["dim"])
 
 
 def peaks():
@@ -192,6 +199,65 @@ def run_gpu(w, prec, steps, warmup, world, local, measure_e2e):
     return res
 
 
+def run_ensemble(steps, warmup, local, n=512):
+    """The batched ensemble: n independent 1D Burgers / 2D advection instances of uneven
+    size and degree (inputs.ensemble_instances), one persistent kernel per dimension."""
+    import torch
+
+    from paper_2309_12019_gb300 import dgw
+    dev = torch.device("cuda", local)
+    insts = I.ensemble_instances(n)
+    probs = [dgw.Problem(dim=d["dim"], nx=d["nx"], ny=d["ny"], p=d["p"], flux=d["flux"], a=d["a"],
+                         stab="weno", bc=("periodic",) * 4) for d in insts]
+    b = dgw.Batch(probs, prec="fp32")
+    U = torch.zeros(b.total, dtype=torch.float32, device=dev)
+    nq, cap, i = 4, 1 << 25, 0
+    while i < n:      # project in chunks of instances (initial data sampled on the GPU)
+        parts, tot, j = [], 0, i
+        while j < n:
+            d = insts[j]
+            cnt = d["nx"] * d["ny"] * nq ** d["dim"]
+            if parts and tot + cnt > cap:
+                break
+            X, Y = I.sample_points_xp(d["dim"], d["nx"], d["ny"], (0.0, 1.0, 0.0, 1.0), nq, torch,
+                                      dtype=torch.float64, device=dev)
+            parts.append(I.u0_fourier_steps(d["init"], X, Y if d["dim"] == 2 else None, xp=torch).reshape(-1))
+            tot += cnt
+            j += 1
+        b.project(torch.cat(parts).contiguous(), U, first=i, count=j - i, nq=nq)
+        del parts
+        i = j
+    b.set_dt([d["dt"] for d in insts])
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        chunk = b.autotune(U, steps=2)
+        b.rk_step(U, warmup)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        b.rk_step(U, steps)
+        ev1.record(stream)
+    ev1.synchronize()
+    b.sync_status(stream)
+    t = ev0.elapsed_time(ev1) / 1e3
+    N = sum(pr.K * pr.E for pr in probs)
+    out = {"workload": f"ensemble_{n}", "value": 3 * N * steps / t, "unit": "DOF-updates/s", "dofs": N,
+           "instances": n, "instances_1d": sum(d["dim"] == 1 for d in insts), "steps": steps,
+           "ms_per_step": 1e3 * t / steps, "work_item_tiles": chunk, "dtype": "f32",
+           "finite": bool(torch.isfinite(U).all().item())}
+    b.close()
+    return out
+
+
+def run_small(name, prec, steps, warmup, local):
+    """Throughput of one of the smaller configurations through dgw_rk_step."""
+    w = WORKLOADS[name]
+    r = run_gpu(w, prec, steps, warmup, 1, local, measure_e2e=False)
+    return {"workload": name, "dtype": "f64" if prec == "fp64" else "f32", "value": 3 * r["N"] * steps / r["t"],
+            "unit": "DOF-updates/s", "steps": steps, "ms_per_step": 1e3 * r["t"] / steps}
+
+
 def run_reference(w, steps, warmup, budget_s=12.0):
     """The FP64 CPU oracle on this host's cores, each step a bounded sample: the
     residual (per-stage work) of a contiguous block of elements."""
@@ -229,6 +295,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble and the smaller configurations")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world, rank, local = dist_setup(args)
@@ -265,6 +333,12 @@ def main():
         st64 = max(3, args.steps // 10)
         r64 = run_gpu(w, "fp64", st64, args.warmup, world, local, measure_e2e=False)
         r64["steps"] = st64
+    extras = {}
+    if not args.no_extras:
+        extras["ensemble"] = run_ensemble(100, 3, local)
+        extras["others"] = [run_small("rotation_256x256_q2", "fp64", 100, 5, local),
+                            run_small("rotation_256x256_q2", "fp32", 100, 5, local),
+                            run_small("advect1d_128_p2", "fp64", 1280, 10, local)]
     if rank != 0:
         return
     hbm, src = peaks()
@@ -283,6 +357,7 @@ def main():
     if r64 is not None:
         line["fp64"] = {"value": 3 * N * r64["steps"] / r64["t"], "unit": "DOF-updates/s",
                         "ms_per_step": 1e3 * r64["t"] / r64["steps"], "steps": r64["steps"]}
+    line.update(extras)
     if not args.no_cpu and world == 1:
         v, cores, n_el = run_reference(w, 3, 1, budget_s=12.0)
         line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",

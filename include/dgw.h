@@ -162,6 +162,52 @@ dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream
  * Synchronizes the stream.  DGW_OK or DGW_ENONFINITE. */
 dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Batched ensemble: many independent meshes (their own size, degree, flux, time step)
+ * advanced together.  The paper has no counterpart; each instance is the scalar problem
+ * above.  One persistent kernel per dimension (cooperative launch) takes work items
+ * (stage, instance, chunk of tiles) in order; an item waits, with a bounded spin, only
+ * for its own instance's previous stage, so instances of different sizes overlap.
+ * Fluxes: advection and Burgers.  Stabilization parameters and precision are common.
+ * ---------------------------------------------------------------------------------- */
+typedef struct dgw_batch dgw_batch;
+
+/* Creates a batch of n instances (meshes[i], ps[i], fluxes[i]); allocates two stage
+ * buffers of the packed state and small counters.  Time steps: dgw_batch_set_dt. */
+dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int* ps, const dgw_flux* fluxes,
+                            const dgw_params* params, dgw_batch** out);
+dgw_status dgw_batch_destroy(dgw_batch* b);
+
+/* Packed state: one device array of *total coefficients; instance i occupies
+ * [offsets[i], offsets[i] + K_i E_i) in the layout of a single context (mode-major).
+ * Offsets are multiples of 4 elements. */
+dgw_status dgw_batch_sizes(const dgw_batch* b, int64_t* total, int64_t* offsets);
+
+/* Time step of every instance (host array of n doubles).  Synchronous. */
+dgw_status dgw_batch_set_dt(dgw_batch* b, const double* dt);
+
+/* L2 projection of instances first .. first+count-1 from samples at the nq-point Gauss
+ * points (dgw_project layout, nq in 1..8), concatenated in instance order (device,
+ * double, sum of E_i nq^dim_i values). */
+dgw_status dgw_batch_project(dgw_batch* b, int nq, int first, int count, const double* samples,
+                             void* U, void* stream);
+
+/* nsteps SSP-RK3 steps (Eq. ssp) of every instance, in place on the packed state U. */
+dgw_status dgw_batch_rk_step(dgw_batch* b, void* U, int nsteps, void* stream);
+
+/* Times `steps` steps for each work-item size (1, 2, 4, 8, 16 tiles) on a copy of U and
+ * keeps the fastest; *chosen_chunk receives it.  Allocates a temporary copy of U. */
+dgw_status dgw_batch_autotune(dgw_batch* b, void* U, int steps, int* chosen_chunk, void* stream);
+
+/* Reads and clears the batch's error flag: DGW_ETIMEOUT if a wait gave up,
+ * DGW_ENONFINITE for a non-finite result.  Synchronizes the stream. */
+dgw_status dgw_batch_sync_status(dgw_batch* b, void* stream);
+
+/* Diagnostic: spin limit of the waits, and (unreachable != 0) make every dependent
+ * wait ask for one tile more than exists, so that it gives up: tests the bounded-wait
+ * path without a hang. */
+dgw_status dgw_batch_debug(dgw_batch* b, long long wait_limit, int unreachable);
+
 /* SSP-RK3 steps for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a deployment convenience).  Such callers include work recorded
  * into a CUDA graph by stream capture, applications whose device memory belongs to

@@ -9,6 +9,11 @@
 #include <set>
 #include <string>
 #include <tuple>
+#include <vector>
+#include <algorithm>
+#include <vector>
+#include <algorithm>
+#include <numeric>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -495,6 +500,339 @@ extern "C" dgw_status dgw_project(dgw_ctx* c, int nq, const double* samples, voi
     const int64_t blocks = (c->E + threads - 1) / threads;
     project_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(a);
     DGW_CUDA(cudaGetLastError());
+    return DGW_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// batched ensemble
+// ------------------------------------------------------------------------------------
+struct dgw_batch {
+    int device = 0;
+    int n = 0;
+    dgw_params params{};
+    int eb = 4;
+    std::vector<BatchInst> inst;
+    std::vector<int> dims;
+    int64_t total = 0;
+    BatchInst* d_inst = nullptr;
+    BatchItem* d_items[2] = {nullptr, nullptr};
+    int nitems[2] = {0, 0};
+    void* S1 = nullptr;
+    void* S2 = nullptr;
+    unsigned long long* counters = nullptr;   // queue[2] then done[n]
+    unsigned* flag = nullptr;
+    int* abort = nullptr;
+    int grid[2] = {0, 0};
+    int chunk = 4;
+    int blocks_per_sm[2] = {0, 0};
+    int sms = 0;
+    long long wait_limit = 1ll << 24;
+    int unreachable = 0;
+};
+
+static dgw_status batch_build_items(dgw_batch* b)
+{
+    for (int d = 0; d < 2; ++d) {
+        std::vector<int> order;
+        for (int i = 0; i < b->n; ++i)
+            if (b->dims[i] == d + 1) order.push_back(i);
+        // longest instances first, so the tail of each stage is made of small items
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return b->inst[x].ntiles > b->inst[y].ntiles; });
+        std::vector<BatchItem> items;
+        for (int i : order)
+            for (int t = 0; t < b->inst[i].ntiles; t += b->chunk)
+                items.push_back(BatchItem{i, t, std::min(b->chunk, b->inst[i].ntiles - t), 0});
+        cudaFree(b->d_items[d]);
+        b->d_items[d] = nullptr;
+        b->nitems[d] = (int)items.size();
+        if (!items.empty()) {
+            DGW_CUDA(cudaMalloc(&b->d_items[d], sizeof(BatchItem) * items.size()));
+            DGW_CUDA(cudaMemcpy(b->d_items[d], items.data(), sizeof(BatchItem) * items.size(),
+                                cudaMemcpyHostToDevice));
+        }
+    }
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_destroy(dgw_batch* b)
+{
+    if (!b) return DGW_OK;
+    cudaDeviceSynchronize();
+    cudaFree(b->d_inst);
+    cudaFree(b->d_items[0]);
+    cudaFree(b->d_items[1]);
+    cudaFree(b->S1);
+    cudaFree(b->S2);
+    cudaFree(b->counters);
+    cudaFree(b->flag);
+    cudaFree(b->abort);
+    delete b;
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int* ps, const dgw_flux* fluxes,
+                                       const dgw_params* params, dgw_batch** out)
+{
+    if (!out || !meshes || !ps || !fluxes || !params || n < 1) return fail(DGW_EINVAL, "bad arguments to dgw_batch_create");
+    *out = nullptr;
+    dgw_status st = check_params(params, 2);
+    if (st != DGW_OK) return st;
+    std::vector<BatchInst> insts;
+    std::vector<int> dims;
+    int64_t off = 0;
+    bool need_tab[2][2][kMaxP + 1] = {};
+    const int eb = params->prec == DGW_FP64 ? 8 : 4;
+    for (int i = 0; i < n; ++i) {
+        const dgw_mesh& m = meshes[i];
+        const int p = ps[i];
+        const dgw_flux& f = fluxes[i];
+        if (m.dim != 1 && m.dim != 2) return fail(DGW_EINVAL, "instance %d: dim must be 1 or 2", i);
+        if (m.nx < 1 || (m.dim == 2 && m.ny < 1) || !(m.x1 > m.x0) || (m.dim == 2 && !(m.y1 > m.y0)))
+            return fail(DGW_EINVAL, "instance %d: bad mesh", i);
+        const double hx = (m.x1 - m.x0) / m.nx;
+        if (m.dim == 2 && std::fabs(hx - (m.y1 - m.y0) / m.ny) > 1e-12 * hx)
+            return fail(DGW_EUNSUPPORTED, "instance %d: 2D cells must be square", i);
+        if (p < 1 || p > kMaxP) return fail(DGW_EUNSUPPORTED, "instance %d: degree %d not built", i, p);
+        if (f.kind != DGW_FLUX_ADVECT && f.kind != DGW_FLUX_BURGERS)
+            return fail(DGW_EUNSUPPORTED, "instance %d: the batched kernel is built for advection and Burgers", i);
+        if (!(f.lambda_nu >= 0.0)) return fail(DGW_EINVAL, "instance %d: lambda_nu must be >= 0", i);
+        for (int s = 0; s < 2 * m.dim; ++s)
+            if (m.bc[s] < DGW_BC_PERIODIC || m.bc[s] > DGW_BC_OUTFLOW) return fail(DGW_EINVAL, "instance %d: bad bc", i);
+        for (int a = 0; a < m.dim; ++a)
+            if ((m.bc[2 * a] == DGW_BC_PERIODIC) != (m.bc[2 * a + 1] == DGW_BC_PERIODIC))
+                return fail(DGW_EINVAL, "instance %d: periodic sides must come in pairs", i);
+        BatchInst I;
+        std::memset(&I, 0, sizeof I);
+        I.nx = m.nx;
+        I.ny = m.dim == 2 ? m.ny : 1;
+        I.E = (int64_t)I.nx * I.ny;
+        I.p = p;
+        I.flux = f.kind;
+        const int K = m.dim == 1 ? p + 1 : (p + 1) * (p + 1);
+        I.ntx = m.dim == 1 ? (m.nx + 127) / 128 : (m.nx + kTileX2 - 1) / kTileX2;
+        I.ntiles = m.dim == 1 ? I.ntx : I.ntx * ((m.ny + kTileY2 - 1) / kTileY2);
+        for (int s = 0; s < 4; ++s) I.bc[s] = s < 2 * m.dim ? m.bc[s] : DGW_BC_PERIODIC;
+        I.x0 = m.x0; I.y0 = m.y0; I.h = hx;
+        I.a0 = f.a[0]; I.a1 = f.a[1]; I.cx = f.center[0]; I.cy = f.center[1];
+        I.omega = f.omega; I.lambda_nu = f.lambda_nu; I.dt = 0.0;
+        I.off = off;
+        off += ((int64_t)K * I.E + 3) / 4 * 4;     // keep every instance 16-byte aligned
+        insts.push_back(I);
+        dims.push_back(m.dim);
+        need_tab[eb == 8][m.dim - 1][p] = true;
+    }
+    dgw_batch* b = new dgw_batch();
+    b->n = n;
+    b->params = *params;
+    b->eb = eb;
+    b->inst = insts;
+    b->dims = dims;
+    b->total = off;
+    cudaError_t ce = cudaGetDevice(&b->device);
+    for (int f64 = 0; f64 < 2 && ce == cudaSuccess; ++f64)
+        for (int d = 0; d < 2 && ce == cudaSuccess; ++d)
+            for (int p = 1; p <= kMaxP && ce == cudaSuccess; ++p) {
+                if (!need_tab[f64][d][p]) continue;
+                HostTables t;
+                build_tables(p, &t);
+                ce = f64 ? (d == 0 ? upload_tables_f64_d1(t) : upload_tables_f64_d2(t))
+                         : (d == 0 ? upload_tables_f32_d1(t) : upload_tables_f32_d2(t));
+            }
+    const size_t bytes = (size_t)b->total * b->eb;
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->S1, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->S2, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->counters, sizeof(unsigned long long) * (2 + n));
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->flag, sizeof(unsigned));
+    if (ce == cudaSuccess) ce = cudaMemset(b->flag, 0, sizeof(unsigned));
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->abort, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->d_inst, sizeof(BatchInst) * n);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (ce != cudaSuccess) {
+        dgw_status s2 = fail(ce == cudaErrorMemoryAllocation ? DGW_ENOMEM : DGW_ECUDA, "dgw_batch_create: %s",
+                             cudaGetErrorString(ce));
+        dgw_batch_destroy(b);
+        return s2;
+    }
+    const bool f64 = b->eb == 8;
+    b->blocks_per_sm[0] = f64 ? batch_blocks_per_sm_f64_d1() : batch_blocks_per_sm_f32_d1();
+    b->blocks_per_sm[1] = f64 ? batch_blocks_per_sm_f64_d2() : batch_blocks_per_sm_f32_d2();
+    for (int d = 0; d < 2; ++d) b->grid[d] = b->blocks_per_sm[d] * b->sms;
+    if (b->grid[0] <= 0 || b->grid[1] <= 0) {
+        dgw_batch_destroy(b);
+        return fail(DGW_ECUDA, "dgw_batch_create: occupancy query failed");
+    }
+    st = batch_build_items(b);
+    if (st == DGW_OK && cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(DGW_ECUDA, "dgw_batch_create: upload failed");
+    if (st != DGW_OK) {
+        dgw_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_sizes(const dgw_batch* b, int64_t* total, int64_t* offsets)
+{
+    if (!b) return fail(DGW_EINVAL, "NULL batch");
+    if (total) *total = b->total;
+    if (offsets)
+        for (int i = 0; i < b->n; ++i) offsets[i] = b->inst[i].off;
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_set_dt(dgw_batch* b, const double* dt)
+{
+    if (!b || !dt) return fail(DGW_EINVAL, "NULL argument");
+    for (int i = 0; i < b->n; ++i)
+        if (!std::isfinite(dt[i]) || dt[i] == 0.0) return fail(DGW_EINVAL, "dt[%d] must be finite and nonzero", i);
+    for (int i = 0; i < b->n; ++i) b->inst[i].dt = dt[i];
+    DGW_CUDA(cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice));
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_project(dgw_batch* b, int nq, int first, int count, const double* samples,
+                                        void* U, void* stream)
+{
+    if (!b || !samples || !U) return fail(DGW_EINVAL, "NULL argument");
+    if (nq < 1 || nq > 8) return fail(DGW_EINVAL, "nq must lie in 1..8");
+    if (first < 0 || count < 0 || first + count > b->n) return fail(DGW_EINVAL, "instance range out of bounds");
+    double x[8], w[8];
+    gauss_rule_public(nq, x, w);
+    int64_t so = 0;
+    for (int i = first; i < first + count; ++i) {
+        const BatchInst& I = b->inst[i];
+        ProjArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.f = samples + so;
+        so += I.E * (b->dims[i] == 1 ? nq : nq * nq);
+        a.U = static_cast<char*>(U) + (size_t)I.off * b->eb;
+        a.E = I.E; a.nq = nq; a.n1 = I.p + 1; a.dim = b->dims[i]; a.f64 = b->eb == 8;
+        for (int q = 0; q < nq; ++q) {
+            a.w[q] = w[q];
+            double pm = 1.0, pc = x[q];
+            a.B[q][0] = 1.0;
+            a.B[q][1] = x[q];
+            for (int k = 1; k < I.p; ++k) {
+                double pn = ((2 * k + 1) * x[q] * pc - k * pm) / (k + 1);
+                pm = pc; pc = pn;
+                a.B[q][k + 1] = pn;
+            }
+        }
+        for (int k = 0; k <= I.p; ++k) a.minv[k] = (2 * k + 1) / 2.0;
+        project_kernel<<<(unsigned)((I.E + 127) / 128), 128, 0, (cudaStream_t)stream>>>(a);
+        DGW_CUDA(cudaGetLastError());
+    }
+    return DGW_OK;
+}
+
+static dgw_status batch_enqueue(dgw_batch* b, void* U, int nsteps, cudaStream_t s)
+{
+    DGW_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (2 + b->n), s));
+    DGW_CUDA(cudaMemsetAsync(b->abort, 0, sizeof(int), s));
+    for (int d = 0; d < 2; ++d) {
+        if (b->nitems[d] == 0) continue;
+        BatchArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.inst = b->d_inst;
+        a.items = b->d_items[d];
+        a.nitems = b->nitems[d];
+        a.nstages = 3 * nsteps;
+        a.U = U;
+        a.S1 = b->S1;
+        a.S2 = b->S2;
+        a.queue = b->counters + d;
+        a.done = b->counters + 2;
+        a.flag = b->flag;
+        a.abort = b->abort;
+        a.stab = b->params.stab;
+        a.q = b->params.q; a.b = b->params.b; a.w_nbr = b->params.w_nbr;
+        a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s;
+        a.wait_limit = b->wait_limit;
+        a.unreachable = b->unreachable;
+        const bool f64 = b->eb == 8;
+        cudaError_t e = d == 0 ? (f64 ? launch_batch_f64_d1(a, b->grid[0], s) : launch_batch_f32_d1(a, b->grid[0], s))
+                               : (f64 ? launch_batch_f64_d2(a, b->grid[1], s) : launch_batch_f32_d2(a, b->grid[1], s));
+        if (e != cudaSuccess) return fail(DGW_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    }
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_rk_step(dgw_batch* b, void* U, int nsteps, void* stream)
+{
+    if (!b || !U) return fail(DGW_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(DGW_EINVAL, "nsteps < 0");
+    if (((uintptr_t)U & 15u) != 0) return fail(DGW_EINVAL, "U must be 16-byte aligned");
+    if (nsteps == 0) return DGW_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return fail(DGW_EINVAL, "wrong device");
+    for (int i = 0; i < b->n; ++i)
+        if (b->inst[i].dt == 0.0) return fail(DGW_EINVAL, "dt not set (dgw_batch_set_dt)");
+    return batch_enqueue(b, U, nsteps, (cudaStream_t)stream);
+}
+
+extern "C" dgw_status dgw_batch_autotune(dgw_batch* b, void* U, int steps, int* chosen_chunk, void* stream)
+{
+    if (!b || !U || steps < 1) return fail(DGW_EINVAL, "bad arguments");
+    for (int i = 0; i < b->n; ++i)
+        if (b->inst[i].dt == 0.0) return fail(DGW_EINVAL, "dt not set (dgw_batch_set_dt)");
+    cudaStream_t s = (cudaStream_t)stream;
+    void* tmp = nullptr;
+    const size_t bytes = (size_t)b->total * b->eb;
+    DGW_CUDA(cudaMalloc(&tmp, bytes));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int chunks[] = {1, 2, 4, 8, 16};
+    int best = b->chunk;
+    float best_ms = 1e30f;
+    dgw_status st = DGW_OK;
+    for (int c : chunks) {
+        b->chunk = c;
+        st = batch_build_items(b);
+        if (st != DGW_OK) break;
+        if (cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { st = fail(DGW_ECUDA, "copy"); break; }
+        st = batch_enqueue(b, tmp, 1, s);    // warm-up
+        if (st != DGW_OK) break;
+        cudaEventRecord(e0, s);
+        st = batch_enqueue(b, tmp, steps, s);
+        if (st != DGW_OK) break;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (st != DGW_OK) return st;
+    b->chunk = best;
+    st = batch_build_items(b);
+    if (chosen_chunk) *chosen_chunk = best;
+    return st;
+}
+
+extern "C" dgw_status dgw_batch_sync_status(dgw_batch* b, void* stream)
+{
+    if (!b) return fail(DGW_EINVAL, "NULL batch");
+    unsigned v = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    DGW_CUDA(cudaMemcpyAsync(&v, b->flag, sizeof v, cudaMemcpyDeviceToHost, s));
+    DGW_CUDA(cudaMemsetAsync(b->flag, 0, sizeof(unsigned), s));
+    DGW_CUDA(cudaStreamSynchronize(s));
+    if (v & 2u) return fail(DGW_ETIMEOUT, "a work item waited too long for its instance's previous stage");
+    if (v & 1u) return fail(DGW_ENONFINITE, "a stage produced a non-finite value");
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_debug(dgw_batch* b, long long wait_limit, int unreachable)
+{
+    if (!b || wait_limit < 1) return fail(DGW_EINVAL, "bad arguments");
+    b->wait_limit = wait_limit;
+    b->unreachable = unreachable ? 1 : 0;
     return DGW_OK;
 }
 

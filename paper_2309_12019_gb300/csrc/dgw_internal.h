@@ -64,12 +64,57 @@ struct StageArgs {
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x kBoxY2 x K), or null
 };
 
+// ------------------------------------------------------------------------------------
+// Batched ensemble: many independent meshes advanced by one persistent kernel per
+// dimension.  Work item = (stage, instance, chunk of tiles); an item waits only for its
+// own instance's previous stage (per-instance counters, bounded spin).
+// ------------------------------------------------------------------------------------
+struct BatchInst {
+    int64_t off;           // first coefficient of the instance in the packed state
+    int64_t E;
+    int nx, ny, p, flux;
+    int ntx, ntiles;       // tiles per row, tiles per stage
+    int bc[4];
+    double x0, y0, h, a0, a1, cx, cy, omega, lambda_nu, dt;
+};
+
+struct BatchItem {
+    int inst, tile0, ntile, pad;
+};
+
+struct BatchArgs {
+    const BatchInst* inst;
+    const BatchItem* items;
+    int nitems;
+    int nstages;                   // 3 * steps
+    void* U;
+    void* S1;
+    void* S2;
+    unsigned long long* queue;     // dequeue counter, zero at launch
+    unsigned long long* done;      // per instance: tiles finished, zero at launch
+    unsigned* flag;                // bit 0: non-finite; bit 1: a bounded wait gave up
+    int* abort;                    // set when a wait gave up: every CTA stops
+    int stab;
+    double q, b, w_nbr, eps_w, eps_s;
+    long long wait_limit;          // spin iterations before a wait gives up
+    int unreachable;               // diagnostic: ask one tile more than exists (wait must give up)
+};
+
 // Launchers, one per (precision, dimension) translation unit.  mode 0: stage or
 // residual; mode 1: sensor only (writes gamma_out).
 cudaError_t launch_stage_f32_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 cudaError_t launch_stage_f32_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 cudaError_t launch_stage_f64_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 cudaError_t launch_stage_f64_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
+
+cudaError_t launch_batch_f32_d1(const BatchArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f32_d2(const BatchArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64_d1(const BatchArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64_d2(const BatchArgs& a, int grid, cudaStream_t s);
+int batch_blocks_per_sm_f32_d1();
+int batch_blocks_per_sm_f32_d2();
+int batch_blocks_per_sm_f64_d1();
+int batch_blocks_per_sm_f64_d2();
 
 cudaError_t upload_tables_f32_d1(const HostTables& t);
 cudaError_t upload_tables_f32_d2(const HostTables& t);

@@ -95,6 +95,7 @@ static cudaError_t upload(const HostTables& h)
 struct alignas(64) KParams {
     CUtensorMap tmap;    // TMA descriptor of Uk (valid when use_tma)
     int use_tma;
+    int cg_loads;        // load Uk / Un through L2 only (data written earlier in the same launch)
     const Real* Uk;
     const Real* Un;
     Real* Uout;
@@ -264,9 +265,26 @@ __device__ __forceinline__ bool mbar_wait0(uint32_t bar)
     return false;
 }
 
-// MODE 0: stage / residual; MODE 1: sensor only.
+// Shared memory of one tile (carved from dynamic shared memory).
+template <int P>
+struct TileSmem {
+    static constexpr int N1 = P + 1, K = Tab<P>::K, TN = DIM == 1 ? 1 : N1;
+    alignas(128) Real su[K][HY][HX];
+    // cell index innermost: a warp touches consecutive words (no bank conflicts)
+    Real trx[TY][2][TN][TX + 2];                          // x-traces, col = lx + 1
+    Real trys[DIM == 2 ? TY + 2 : 1][2][TN][TX];          // y-traces, row = ly + 1
+    Real hfx[TY][TN][TX + 1];
+    Real hfy[DIM == 2 ? TY + 1 : 1][TN][TX];
+    Real lam_s[TY][TX];
+    alignas(8) uint64_t mbar;
+    int fail_s;
+};
+
+// One tile of one stage.  Called by all NT threads of a CTA together (it contains
+// CTA barriers); tx0, ty0: first cell of the tile.  MODE 0: stage / residual;
+// MODE 1: sensor only.
 template <int P, int FLUX, int MODE>
-__global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_constant__ KParams A)
+__device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P>& S)
 {
     constexpr int N1 = P + 1, NQ = P + 2;
     constexpr int K = Tab<P>::K;
@@ -274,20 +292,16 @@ __global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_co
     constexpr int NFY = DIM == 2 ? TX * (TY + 1) : 0;  // y-faces
     constexpr int TN = DIM == 1 ? 1 : N1;              // trace / face coefficients
     const Tab<P>& T = tab<P>();
-
-    __shared__ alignas(128) Real su[K][HY][HX];
-    // cell index innermost: a warp touches consecutive words (no bank conflicts)
-    __shared__ Real trx[TY][2][TN][TX + 2];                          // x-traces, col = lx + 1
-    __shared__ Real trys[DIM == 2 ? TY + 2 : 1][2][TN][TX];          // y-traces, row = ly + 1
-    __shared__ Real hfx[TY][TN][TX + 1];
-    __shared__ Real hfy[DIM == 2 ? TY + 1 : 1][TN][TX];
-    __shared__ Real lam_s[TY][TX];
-    __shared__ alignas(8) uint64_t mbar;
-    __shared__ int fail_s;
+    auto& su = S.su;
+    auto& trx = S.trx;
+    auto& trys = S.trys;
+    auto& hfx = S.hfx;
+    auto& hfy = S.hfy;
+    auto& lam_s = S.lam_s;
+    auto& mbar = S.mbar;
+    auto& fail_s = S.fail_s;
 
     const int tid = threadIdx.x;
-    const int tx0 = blockIdx.x * TX;
-    const int ty0 = DIM == 2 ? blockIdx.y * TY : 0;
     const int64_t E = A.E;
     const bool need_lam = (MODE == 0) && (A.stab != STAB_DG) && !A.lam_fixed;
     const bool periodic_x = A.bc[0] == BC_PERIODIC;
@@ -349,8 +363,13 @@ __global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_co
             const int gy = DIM == 2 ? wrap_y(A, ty0 - OY + r) : 0;
             if (gx < 0 || gy < 0) continue;
             const Real* src = A.Uk + (int64_t)gy * A.nx + gx;
+            if (A.cg_loads) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) su[k][r][cc] = src[k * E];
+                for (int k = 0; k < K; ++k) su[k][r][cc] = __ldcg(src + k * E);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) su[k][r][cc] = src[k * E];
+            }
         }
         __syncthreads();
     }
@@ -663,11 +682,23 @@ __global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_co
         if (DIM == 2) mi *= T.minv[j];
         const Real L = A.two_h * mi * r;
         Real out = A.cl * L + A.ck * c[k];
-        if (A.has_un) out += A.cn * un[k * E];
+        if (A.has_un) out += A.cn * (A.cg_loads ? __ldcg(un + k * E) : un[k * E]);
         chk = fma(out, Real(0), chk);
         uo[k * E] = out;
     }
     if (chk != chk) atomicOr(A.flag, 1u);
+}
+
+template <int P, int FLUX, int MODE>
+__global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_constant__ KParams A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    if ((__cvta_generic_to_shared(smem_raw) & 127u) != 0) {   // TMA needs an aligned box
+        if (threadIdx.x == 0) atomicOr(A.flag, 2u);
+        return;
+    }
+    TileSmem<P>& S = *reinterpret_cast<TileSmem<P>*>(smem_raw);
+    process_tile<P, FLUX, MODE>(A, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, S);
 }
 
 static KParams make_params(const StageArgs& s)
@@ -675,6 +706,7 @@ static KParams make_params(const StageArgs& s)
     KParams a;
     memset(&a, 0, sizeof a);
     a.use_tma = 0;
+    a.cg_loads = 0;
     if (s.tmap) {
         a.tmap = *s.tmap;
         a.use_tma = 1;
@@ -702,14 +734,165 @@ static KParams make_params(const StageArgs& s)
     return a;
 }
 
+// ------------------------------------------------------------------------------------
+// batched ensemble: persistent kernel
+// ------------------------------------------------------------------------------------
+template <int P, int FLUX>
+__device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst& I, const int r,
+                                            const int tile0, const int ntile, unsigned char* smem)
+{
+    KParams A;
+    A.use_tma = 0;
+    A.cg_loads = 1;
+    const Real* U = static_cast<const Real*>(B.U) + I.off;
+    const Real* S1 = static_cast<const Real*>(B.S1) + I.off;
+    const Real* S2 = static_cast<const Real*>(B.S2) + I.off;
+    A.Uk = r == 0 ? U : (r == 1 ? S1 : S2);
+    A.Un = U;
+    A.Uout = const_cast<Real*>(r == 0 ? S1 : (r == 1 ? S2 : U));
+    A.gamma_out = nullptr;
+    A.flag = B.flag;
+    A.E = I.E;
+    A.nx = I.nx;
+    A.ny = I.ny;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) A.bc[f] = I.bc[f];
+    A.stab = B.stab;
+    A.lam_fixed = I.lambda_nu > 0.0;
+    A.q_one = B.q == 1.0;
+    A.has_un = r > 0;
+    A.x0 = (Real)I.x0; A.y0 = (Real)I.y0; A.h = (Real)I.h; A.hh = (Real)(0.5 * I.h);
+    A.two_h = (Real)(2.0 / I.h);
+    A.a0 = (Real)I.a0; A.a1 = (Real)I.a1; A.cx = (Real)I.cx; A.cy = (Real)I.cy;
+    A.omega = (Real)I.omega; A.lambda_nu = (Real)I.lambda_nu;
+    A.q = (Real)B.q; A.b = (Real)B.b; A.w_nbr = (Real)B.w_nbr; A.eps_w = (Real)B.eps_w;
+    A.eps_s = (Real)B.eps_s;
+    const double dt = I.dt;
+    A.cn = (Real)(r == 0 ? 0.0 : (r == 1 ? 0.75 : 1.0 / 3.0));
+    A.ck = (Real)(r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0));
+    A.cl = (Real)(r == 0 ? dt : (r == 1 ? 0.25 * dt : 2.0 / 3.0 * dt));
+    TileSmem<P>& S = *reinterpret_cast<TileSmem<P>*>(smem);
+    for (int t = tile0; t < tile0 + ntile; ++t) {
+        const int tx0 = (t % I.ntx) * TX;
+        const int ty0 = DIM == 2 ? (t / I.ntx) * TY : 0;
+        process_tile<P, FLUX, 0>(A, tx0, ty0, S);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent kernel over all work items of all stages: items are dequeued in order,
+// so every item an item waits for was dequeued earlier by a resident CTA (the launch is
+// cooperative, hence all CTAs are resident) and no wait can deadlock; each wait is
+// still bounded, and a wait that gives up stops the whole launch through B.abort.
+constexpr size_t kTileSmemMax = sizeof(TileSmem<3>) > sizeof(TileSmem<2>) ? sizeof(TileSmem<3>) : sizeof(TileSmem<2>);
+constexpr size_t kBatchSmem = (kTileSmemMax + 127) / 128 * 128 + 128;   // tile + scheduler words
+
+__global__ void __launch_bounds__(NT, kF32 ? 6 : 3) batch_kernel(const BatchArgs B)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    long long& s_w = *reinterpret_cast<long long*>(smem_raw + kBatchSmem - 128);
+    int& s_ok = *reinterpret_cast<int*>(smem_raw + kBatchSmem - 64);
+    const long long total = (long long)B.nitems * B.nstages;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long w = (long long)atomicAdd(B.queue, 1ULL);
+            if (w >= total || *((volatile int*)B.abort)) w = -1;
+            s_w = w;
+        }
+        __syncthreads();
+        const long long w = s_w;
+        if (w < 0) break;
+        const int g = (int)(w / B.nitems);
+        const BatchItem it = B.items[w - (long long)g * B.nitems];
+        const BatchInst& I = B.inst[it.inst];
+        if (threadIdx.x == 0) {
+            const unsigned long long need = (unsigned long long)g * (unsigned long long)I.ntiles + (B.unreachable ? 1ull : 0ull);
+            int ok = 1;
+            if (need > 0) {
+                ok = 0;
+                for (long long n = 0; n < B.wait_limit; ++n) {
+                    if (ld_acquire(&B.done[it.inst]) >= need) { ok = 1; break; }
+                    if (*((volatile int*)B.abort)) break;
+                    __nanosleep(64);
+                }
+            }
+            if (!ok) {
+                atomicOr(B.flag, 2u);
+                atomicExch(B.abort, 1);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        __threadfence();
+        const int r = g % 3;
+        switch (I.p * 8 + I.flux) {
+        case 1 * 8 + FLUX_ADVECT: batch_tiles<1, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw); break;
+        case 2 * 8 + FLUX_ADVECT: batch_tiles<2, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw); break;
+        case 3 * 8 + FLUX_ADVECT: batch_tiles<3, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw); break;
+        case 1 * 8 + FLUX_BURGERS: batch_tiles<1, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw); break;
+        case 2 * 8 + FLUX_BURGERS: batch_tiles<2, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw); break;
+        case 3 * 8 + FLUX_BURGERS: batch_tiles<3, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw); break;
+        default: break;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&B.done[it.inst], (unsigned long long)it.ntile);
+    }
+}
+
+static int batch_blocks_per_sm()
+{
+    if (kBatchSmem > 48 * 1024 &&
+        cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, NT, kBatchSmem) != cudaSuccess) return 0;
+    return n;
+}
+
+static cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = kBatchSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel, a);
+}
+
 template <int P, int FLUX>
 static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
 {
     const KParams a = make_params(s);
     dim3 grid((s.nx + TX - 1) / TX, DIM == 2 ? (s.ny + TY - 1) / TY : 1);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    if (mode == 0) stage_kernel<P, FLUX, 0><<<grid, NT, 0, st>>>(a);
-    else stage_kernel<P, FLUX, 1><<<grid, NT, 0, st>>>(a);
+    const size_t smem = sizeof(TileSmem<P>);
+    if (smem > 48 * 1024) {
+        // opt in once per instantiation to more than 48 KB of dynamic shared memory
+        static bool opted[2] = {false, false};
+        if (!opted[mode]) {
+            cudaError_t e = mode == 0
+                ? cudaFuncSetAttribute(stage_kernel<P, FLUX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                : cudaFuncSetAttribute(stage_kernel<P, FLUX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            opted[mode] = true;
+        }
+    }
+    if (mode == 0) stage_kernel<P, FLUX, 0><<<grid, NT, smem, st>>>(a);
+    else stage_kernel<P, FLUX, 1><<<grid, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 

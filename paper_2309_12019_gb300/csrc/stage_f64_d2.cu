@@ -9,5 +9,10 @@ cudaError_t launch_stage_f64_d2(const StageArgs& a, int p, int flux, int mode, c
 {
     return f64_d2::launch(a, p, flux, mode, s);
 }
+cudaError_t launch_batch_f64_d2(const BatchArgs& a, int grid, cudaStream_t s)
+{
+    return f64_d2::launch_batch(a, grid, s);
+}
+int batch_blocks_per_sm_f64_d2() { return f64_d2::batch_blocks_per_sm(); }
 cudaError_t upload_tables_f64_d2(const HostTables& t) { return f64_d2::upload_tables(t); }
 }  // namespace dgw

@@ -53,8 +53,10 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_rk_step_noalloc", "dgw_selftest_sincos", "dgw_last_error",
-           "dgw_version")
+           "dgw_sync_status", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
+           "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
+           "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
+           "dgw_last_error", "dgw_version")
 
 
 def load(build: bool = True):
@@ -81,6 +83,16 @@ def load(build: bool = True):
         L.dgw_rk_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
+        L.dgw_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Mesh), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(Flux), ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.dgw_batch_destroy.argtypes = [vp]
+        L.dgw_batch_sizes.argtypes = [vp, i64p, i64p]
+        L.dgw_batch_set_dt.argtypes = [vp, dp]
+        L.dgw_batch_project.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.dgw_batch_rk_step.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.dgw_batch_autotune.argtypes = [vp, vp, ctypes.c_int, ip, vp]
+        L.dgw_batch_sync_status.argtypes = [vp, vp]
+        L.dgw_batch_debug.argtypes = [vp, ctypes.c_longlong, ctypes.c_int]
         L.dgw_rk_step_noalloc.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.POINTER(Flux),
                                           ctypes.POINTER(Params), vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_selftest_sincos.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
@@ -229,6 +241,85 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+
+class Batch:
+    """Owns one dgw_batch: many independent problems advanced by one persistent kernel per
+    dimension.  Methods mirror the dgw_batch_* entry points of include/dgw.h."""
+
+    def __init__(self, problems, prec: str = "fp32"):
+        L = load()
+        n = len(problems)
+        meshes, fluxes, params = (Mesh * n)(), (Flux * n)(), None
+        ps = (ctypes.c_int * n)()
+        for i, pr in enumerate(problems):
+            pr = dataclasses.replace(pr, prec=prec)
+            m, f, s = pr.c_structs()
+            meshes[i], fluxes[i], ps[i] = m, f, pr.p
+            params = params or s
+        h = ctypes.c_void_p()
+        _check(L.dgw_batch_create(n, meshes, ps, fluxes, ctypes.byref(params), ctypes.byref(h)))
+        self._h = h
+        self.problems = list(problems)
+        self.prec = prec
+        total = ctypes.c_int64()
+        offs = (ctypes.c_int64 * n)()
+        _check(L.dgw_batch_sizes(h, ctypes.byref(total), offs))
+        self.total = total.value
+        self.offsets = list(offs)
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.prec == "fp64" else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dgw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _state(self, U):
+        if not U.is_cuda or U.dtype != self.dtype or not U.is_contiguous() or U.numel() < self.total:
+            raise ValueError(f"packed state must be a contiguous CUDA {self.dtype} tensor of {self.total}")
+        return _ptr(U)
+
+    def view(self, U, i):
+        """Instance i of the packed state as a (K, E) tensor view."""
+        pr = self.problems[i]
+        return U[self.offsets[i]:self.offsets[i] + pr.K * pr.E].view(pr.K, pr.E)
+
+    def set_dt(self, dts):
+        arr = (ctypes.c_double * len(dts))(*[float(d) for d in dts])
+        _check(load().dgw_batch_set_dt(self._h, arr))
+
+    def project(self, samples, U, first: int = 0, count=None, nq: int = 8, stream=None):
+        """Projects instances first .. first+count-1 from their concatenated samples."""
+        import torch
+        if samples.dtype != torch.float64 or not samples.is_cuda or not samples.is_contiguous():
+            raise ValueError("samples must be a contiguous CUDA float64 tensor")
+        count = len(self.problems) - first if count is None else count
+        _check(load().dgw_batch_project(self._h, int(nq), int(first), int(count), _ptr(samples),
+                                        self._state(U), _stream(stream)))
+
+    def rk_step(self, U, nsteps: int = 1, stream=None):
+        _check(load().dgw_batch_rk_step(self._h, self._state(U), int(nsteps), _stream(stream)))
+
+    def autotune(self, U, steps: int = 2, stream=None) -> int:
+        c = ctypes.c_int()
+        _check(load().dgw_batch_autotune(self._h, self._state(U), int(steps), ctypes.byref(c), _stream(stream)))
+        return c.value
+
+    def sync_status(self, stream=None):
+        _check(load().dgw_batch_sync_status(self._h, _stream(stream)))
+
+    def debug(self, wait_limit: int, unreachable: bool):
+        _check(load().dgw_batch_debug(self._h, int(wait_limit), 1 if unreachable else 0))
 
 
 def rk_step_noalloc(problem: Problem, U, dt: float, nsteps: int = 1, stream=None):

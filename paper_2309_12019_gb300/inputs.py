@@ -102,19 +102,85 @@ def fourier_steps_params(dim: int, rng: np.random.Generator, nmodes: int = 8, ma
     return dict(amp=amp, phase=phase, k=k, lo=lo, width=width)
 
 
-def u0_fourier_steps(params, x, y=None):
+def u0_fourier_steps(params, x, y=None, xp=np):
+    """sum_j a_j sin(2 pi k_j.x + phi_j) plus unit steps on periodic intervals/rectangles.
+    x, y: NumPy arrays (xp=np) or torch tensors (xp=torch)."""
     k = params["k"]
-    u = np.zeros_like(x, dtype=np.float64)
+    u = xp.zeros_like(x)
     for j in range(len(params["amp"])):
-        arg = k[j, 0] * x if k.shape[1] == 1 else k[j, 0] * x + k[j, 1] * y
-        u = u + params["amp"][j] * np.sin(2.0 * np.pi * arg + params["phase"][j])
+        arg = float(k[j, 0]) * x if k.shape[1] == 1 else float(k[j, 0]) * x + float(k[j, 1]) * y
+        u = u + float(params["amp"][j]) * xp.sin(2.0 * math.pi * arg + float(params["phase"][j]))
     for s in range(len(params["lo"])):
-        inside = np.ones_like(x, dtype=bool)
         coords = [x] if k.shape[1] == 1 else [x, y]
+        inside = None
         for c, lo, w in zip(coords, params["lo"][s], params["width"][s]):
-            inside &= np.mod(c - lo, 1.0) < w
-        u = u + inside.astype(np.float64)
+            t = xp.remainder(c - float(lo), 1.0) < float(w)
+            inside = t if inside is None else (inside & t)
+        u = u + xp.where(inside, 1.0, 0.0)
     return u
+
+
+def ensemble_instances(n: int = 512, seed: int = SEED):
+    """The batched-ensemble workload: n independent periodic instances on the unit
+    interval / square, each 1D Burgers or 2D linear advection with v = (cos t, sin t)
+    (coin flip), cells log-uniform in [64, 4096] (1D) or side log-uniform in [32, 512]
+    (2D), degree uniform in {1, 2, 3}, initial data u0_fourier_steps, and the time step
+    dt = CFL_p / sum_i(max|f_i'| / h) with max|f'| bounded by the sum of amplitudes plus
+    steps (Burgers) or |cos t|, |sin t| (advection).  CFL_p = 0.1, 0.05, 0.025 for
+    p = 1, 2, 3: the stabilization term gamma nu grad^2 has spectral radius 6, 15, 28.3
+    gamma lambda / h per direction for p = 1, 2, 3 (largest eigenvalue of the scaled
+    element stiffness), and SSP-RK3 is stable on the negative axis up to 2.51, so at
+    gamma = 1 in 2D lambda dt / h must stay below 0.21, 0.084, 0.044.  Instance i uses
+    the generator seeded with seed + i."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        dim = 1 if rng.uniform() < 0.5 else 2
+        if dim == 1:
+            cells = int(round(math.exp(rng.uniform(math.log(64), math.log(4096)))))
+        else:
+            cells = int(round(math.exp(rng.uniform(math.log(32), math.log(512)))))
+        p = int(rng.integers(1, 4))
+        theta = float(rng.uniform(0.0, 2.0 * math.pi))
+        params = fourier_steps_params(dim, rng)
+        h = 1.0 / cells
+        cfl = {1: 0.1, 2: 0.05, 3: 0.025}[p]
+        if dim == 1:
+            bound = float(np.sum(params["amp"])) + len(params["lo"])
+            dt = cfl_dt(cfl, [bound], [h])
+            a = (1.0, 0.0)
+            flux = "burgers"
+        else:
+            a = (math.cos(theta), math.sin(theta))
+            dt = cfl_dt(cfl, [abs(a[0]), abs(a[1])], [h, h])
+            flux = "advect"
+        out.append(dict(dim=dim, nx=cells, ny=cells if dim == 2 else 1, p=p, flux=flux, a=a, dt=dt,
+                        init=params))
+    return out
+
+
+def sample_points_xp(dim: int, nx: int, ny: int, box, nq: int, xp, **kw):
+    """sample_points for an array namespace xp (np or torch; kw go to xp.tensor/asarray)."""
+    g = gauss_nodes(nq)
+    x0, x1, y0, y1 = box
+    hx = (x1 - x0) / nx
+    if xp is np:
+        X, Y = sample_points(dim, nx, ny, box, nq)
+        return X, Y
+    gt = xp.tensor(g, **kw)
+    xc = x0 + (xp.arange(nx, **kw) + 0.5) * hx
+    if dim == 1:
+        X = xc[:, None] + 0.5 * hx * gt[None, :]
+        return X, xp.zeros_like(X)
+    hy = (y1 - y0) / ny
+    yc = y0 + (xp.arange(ny, **kw) + 0.5) * hy
+    Xe = xc[None, :].expand(ny, nx).reshape(-1)
+    Ye = yc[:, None].expand(ny, nx).reshape(-1)
+    ga = gt.repeat(nq)                 # a fastest
+    gb = gt.repeat_interleave(nq)
+    X = Xe[:, None] + 0.5 * hx * ga[None, :]
+    Y = Ye[:, None] + 0.5 * hy * gb[None, :]
+    return X, Y
 
 
 # --------------------------------------------------------------------------------------
