@@ -250,6 +250,44 @@ def run_ensemble(steps, warmup, local, n=512):
     return out
 
 
+def run_adjoint(local, n=512, steps=200, every=20):
+    """The adjoint workload: 2D Burgers (u^2/2, u^2/2), periodic unit square, n^2 Q2,
+    FP32, misfit after `steps` SSP-RK3 steps against a target grown from another seeded
+    field; gradient by the checkpointed discrete adjoint (recompute every `every`)."""
+    import torch
+
+    from paper_2309_12019_gb300 import adjoint, dgw
+    dev = torch.device("cuda", local)
+    s = dict(dim=2, nx=n, ny=n, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4, flux="burgers",
+             a=(1.0, 1.0), stab="weno")
+    pc, pt = I.adjoint_field(I.SEED + 5001), I.adjoint_field(I.SEED + 5002)
+    dt = I.cfl_dt(0.1, [float(np.sum(pc["amp"])) + 1.0] * 2, [1.0 / n] * 2)
+    c = dgw.Context(dgw.Problem(**s, prec="fp32"))
+    X, Y = I.sample_points(2, n, n, s["box"], 8)
+    U0 = torch.empty((9, n * n), dtype=torch.float32, device=dev)
+    Ut = torch.empty_like(U0)
+    c.project(torch.tensor(I.u0_fourier_steps(pc, X, Y).reshape(-1), device=dev), U0)
+    c.project(torch.tensor(I.u0_fourier_steps(pt, X, Y).reshape(-1), device=dev), Ut)
+    c.rk_step(Ut, dt, steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    U0g = U0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    ev[0].record()
+    J = adjoint.misfit(c, adjoint.rollout(c, U0g, dt, steps, every=every), Ut)
+    ev[1].record()
+    J.backward()
+    ev[2].record()
+    ev[2].synchronize()
+    c.sync_status()
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    out = {"workload": f"adjoint_burgers_{n}x{n}_q2", "dtype": "f32", "steps": steps, "checkpoint_every": every,
+           "dofs": 9 * n * n, "forward_ms_per_step": fwd / steps, "backward_ms_per_step": bwd / steps,
+           "backward_over_forward": bwd / fwd, "misfit": float(J),
+           "grad_finite": bool(torch.isfinite(U0g.grad).all().item())}
+    c.close()
+    return out
+
+
 def run_small(name, prec, steps, warmup, local):
     """Throughput of one of the smaller configurations through dgw_rk_step."""
     w = WORKLOADS[name]
@@ -336,6 +374,7 @@ def main():
     extras = {}
     if not args.no_extras:
         extras["ensemble"] = run_ensemble(100, 3, local)
+        extras["adjoint"] = run_adjoint(local)
         extras["others"] = [run_small("rotation_256x256_q2", "fp64", 100, 5, local),
                             run_small("rotation_256x256_q2", "fp32", 100, 5, local),
                             run_small("advect1d_128_p2", "fp64", 1280, 10, local)]

@@ -163,6 +163,32 @@ dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream
 dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------------------------
+ * Discrete adjoint (the paper has no counterpart: it differentiates the discrete scheme
+ * of Sec. 2-4).  Built for periodic meshes with the advection and Burgers fluxes;
+ * other contexts return DGW_EUNSUPPORTED.  Non-smooth points use subgradients:
+ * d min(1, r)/dr = [r < 1], d|x| = sign(x) (sign(0) = 0), a maximum picks its first
+ * maximising argument, and the eps_s guard / b threshold are constant pieces.  The
+ * context allocates 4 + 2*dim state-sized buffers on first use.
+ * ---------------------------------------------------------------------------------- */
+
+/* out = J_L(U)^T lam, the transpose Jacobian of L = M^{-1} R_stab (Eq. weak2 with the
+ * stabilization of Sec. 3 and the sensor of Sec. 4) at U, applied to lam.  All three
+ * device arrays K*E; out must not overlap U or lam. */
+dgw_status dgw_residual_vjp(dgw_ctx* ctx, const void* U, const void* lam, void* out, void* stream);
+
+/* Reverse of one SSP-RK3 step (Eq. ssp) from the state U_n at the start of the step:
+ * lam_n = (dU^{n+1}/dU^n)^T lam_np1.  The two stage states are recomputed from U_n.
+ * lam_n may equal lam_np1. */
+dgw_status dgw_adjoint_step(dgw_ctx* ctx, const void* U_n, const void* lam_np1, void* lam_n, double dt,
+                            void* stream);
+
+/* Misfit J = 1/2 int (U_h - U_target,h)^2 dx (exact: mass-matrix weighted) in double,
+ * and optionally grad = dJ/dU = M (U - U_target) (device, K*E, may be NULL).  Blocks
+ * until *host_J is set. */
+dgw_status dgw_misfit(dgw_ctx* ctx, const void* U, const void* U_target, double* host_J, void* grad,
+                      void* stream);
+
+/* ------------------------------------------------------------------------------------
  * Batched ensemble: many independent meshes (their own size, degree, flux, time step)
  * advanced together.  The paper has no counterpart; each instance is the scalar problem
  * above.  One persistent kernel per dimension (cooperative launch) takes work items

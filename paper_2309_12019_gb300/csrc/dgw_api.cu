@@ -67,6 +67,10 @@ struct dgw_ctx {
     unsigned* flag = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<const void*, CUtensorMap> tmaps;   // TMA descriptors per state array (2D)
+    void* adj_ws = nullptr;      // adjoint: per-cell partials (own), K*E
+    void* adj_wn = nullptr;      // adjoint: per-cell partials (one block per face), 2*dim*K*E
+    void* adj_b1 = nullptr;      // adjoint: lambda of stage 2
+    void* adj_b2 = nullptr;      // adjoint: lambda of stage 1
     std::map<const void*, bool> no_tmap;
 };
 
@@ -181,6 +185,10 @@ extern "C" dgw_status dgw_destroy(dgw_ctx* c)
     cudaFree(c->S1);
     cudaFree(c->S2);
     cudaFree(c->Uhost_dev);
+    cudaFree(c->adj_ws);
+    cudaFree(c->adj_wn);
+    cudaFree(c->adj_b1);
+    cudaFree(c->adj_b2);
     cudaFree(c->partial);
     cudaFree(c->flag);
     delete c;
@@ -885,6 +893,142 @@ extern "C" dgw_status dgw_mass(dgw_ctx* c, const void* U, double* host_mass, voi
     mass_final_kernel<<<1, kMassThreads, 0, s>>>(c->partial, kMassBlocks, vol, c->mass_dev);
     DGW_CUDA(cudaGetLastError());
     DGW_CUDA(cudaMemcpyAsync(host_mass, c->mass_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DGW_CUDA(cudaStreamSynchronize(s));
+    return DGW_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// discrete adjoint
+// ------------------------------------------------------------------------------------
+static dgw_status adjoint_ready(dgw_ctx* c)
+{
+    for (int f = 0; f < 2 * c->mesh.dim; ++f)
+        if (c->mesh.bc[f] != DGW_BC_PERIODIC)
+            return fail(DGW_EUNSUPPORTED, "the adjoint is built for periodic meshes");
+    if (c->flux.kind != DGW_FLUX_ADVECT && c->flux.kind != DGW_FLUX_BURGERS)
+        return fail(DGW_EUNSUPPORTED, "the adjoint is built for the advection and Burgers fluxes");
+    const size_t bytes = (size_t)c->K * c->E * c->eb;
+    cudaError_t e = cudaSuccess;
+    if (!c->adj_ws) e = cudaMalloc(&c->adj_ws, bytes);
+    if (e == cudaSuccess && !c->adj_wn) e = cudaMalloc(&c->adj_wn, bytes * 2 * c->mesh.dim);
+    if (e == cudaSuccess && !c->adj_b1) e = cudaMalloc(&c->adj_b1, bytes);
+    if (e == cudaSuccess && !c->adj_b2) e = cudaMalloc(&c->adj_b2, bytes);
+    if (e != cudaSuccess) return fail(DGW_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+    return DGW_OK;
+}
+
+// out = c0 x0 + c1 x1 + c2 x2 + cv J_L(U)^T lam
+static cudaError_t vjp_combine(const dgw_ctx* c, const void* U, const void* lam, const void* x0, double c0,
+                               const void* x1, double c1, const void* x2, double c2, double cv, void* out,
+                               cudaStream_t s)
+{
+    StageArgs a = base_args(c);
+    a.Uk = U;
+    const bool f64 = c->params.prec == DGW_FP64;
+    const int d = c->mesh.dim;
+    cudaError_t e = f64 ? (d == 1 ? launch_vjp_f64_d1(a, c->p, c->flux.kind, lam, c->adj_ws, c->adj_wn, s)
+                                  : launch_vjp_f64_d2(a, c->p, c->flux.kind, lam, c->adj_ws, c->adj_wn, s))
+                        : (d == 1 ? launch_vjp_f32_d1(a, c->p, c->flux.kind, lam, c->adj_ws, c->adj_wn, s)
+                                  : launch_vjp_f32_d2(a, c->p, c->flux.kind, lam, c->adj_ws, c->adj_wn, s));
+    if (e != cudaSuccess) return e;
+    GatherArgs g;
+    std::memset(&g, 0, sizeof g);
+    g.E = c->E; g.nx = c->mesh.nx; g.ny = d == 2 ? c->mesh.ny : 1;
+    g.wself = c->adj_ws; g.wnb = c->adj_wn;
+    g.x[0] = x0; g.x[1] = x1; g.x[2] = x2;
+    g.coef[0] = c0; g.coef[1] = c1; g.coef[2] = c2;
+    g.cvjp = cv;
+    g.out = out;
+    return f64 ? (d == 1 ? launch_gather_f64_d1(g, c->p, s) : launch_gather_f64_d2(g, c->p, s))
+               : (d == 1 ? launch_gather_f32_d1(g, c->p, s) : launch_gather_f32_d2(g, c->p, s));
+}
+
+extern "C" dgw_status dgw_residual_vjp(dgw_ctx* c, const void* U, const void* lam, void* out, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U || !lam || !out) return fail(DGW_EINVAL, "NULL array");
+    if (out == U || out == lam) return fail(DGW_EINVAL, "out must not overlap U or lam");
+    st = adjoint_ready(c);
+    if (st != DGW_OK) return st;
+    DGW_CUDA(vjp_combine(c, U, lam, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, 1.0, out, (cudaStream_t)stream));
+    return DGW_OK;
+}
+
+// Reverse of one SSP-RK3 step (Eq. ssp).  With a = lam^{n+1}:
+//   lam_U2 = 2/3 a + 2/3 dt J_L(U2)^T a
+//   lam_U1 = 1/4 lam_U2 + 1/4 dt J_L(U1)^T lam_U2
+//   lam^n  = 1/3 a + 3/4 lam_U2 + lam_U1 + dt J_L(U^n)^T lam_U1
+// where U1, U2 are recomputed from U^n.
+extern "C" dgw_status dgw_adjoint_step(dgw_ctx* c, const void* U_n, const void* lam_np1, void* lam_n,
+                                       double dt, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U_n || !lam_np1 || !lam_n) return fail(DGW_EINVAL, "NULL array");
+    if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
+    st = adjoint_ready(c);
+    if (st != DGW_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    StageArgs a = base_args(c);
+    a.Uk = U_n; a.Un = nullptr; a.Uout = c->S1;
+    a.cn = 0.0; a.ck = 1.0; a.cl = dt;
+    DGW_CUDA(launch(c, a, 0, s));
+    a.Uk = c->S1; a.Un = U_n; a.Uout = c->S2;
+    a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt;
+    DGW_CUDA(launch(c, a, 0, s));
+    DGW_CUDA(vjp_combine(c, c->S2, lam_np1, lam_np1, 2.0 / 3.0, nullptr, 0.0, nullptr, 0.0, 2.0 / 3.0 * dt,
+                         c->adj_b1, s));
+    DGW_CUDA(vjp_combine(c, c->S1, c->adj_b1, c->adj_b1, 0.25, nullptr, 0.0, nullptr, 0.0, 0.25 * dt,
+                         c->adj_b2, s));
+    DGW_CUDA(vjp_combine(c, U_n, c->adj_b2, lam_np1, 1.0 / 3.0, c->adj_b1, 0.75, c->adj_b2, 1.0, dt, lam_n, s));
+    return DGW_OK;
+}
+
+template <typename Real>
+__global__ void misfit_kernel(const Real* U, const Real* Ut, Real* grad, int64_t E, int K, int n1, int dim,
+                              double h, double* partial)
+{
+    __shared__ double sh[kMassThreads];
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < K; ++k) {
+            const int i = k % n1, j = k / n1;
+            double m = 0.5 * h * 2.0 / (2 * i + 1);            // mass of P_i on a cell of width h
+            if (dim == 2) m *= 0.5 * h * 2.0 / (2 * j + 1);
+            const double d = (double)U[k * E + e] - (double)Ut[k * E + e];
+            s += 0.5 * m * d * d;
+            if (grad) grad[k * E + e] = (Real)(m * d);
+        }
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+extern "C" dgw_status dgw_misfit(dgw_ctx* c, const void* U, const void* U_target, double* host_J, void* grad,
+                                 void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U || !U_target || !host_J) return fail(DGW_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->params.prec == DGW_FP64)
+        misfit_kernel<double><<<kMassBlocks, kMassThreads, 0, s>>>((const double*)U, (const double*)U_target,
+                                                                   (double*)grad, c->E, c->K, c->p + 1, c->mesh.dim,
+                                                                   c->h, c->partial);
+    else
+        misfit_kernel<float><<<kMassBlocks, kMassThreads, 0, s>>>((const float*)U, (const float*)U_target,
+                                                                 (float*)grad, c->E, c->K, c->p + 1, c->mesh.dim,
+                                                                 c->h, c->partial);
+    DGW_CUDA(cudaGetLastError());
+    mass_final_kernel<<<1, kMassThreads, 0, s>>>(c->partial, kMassBlocks, 1.0, c->mass_dev);
+    DGW_CUDA(cudaGetLastError());
+    DGW_CUDA(cudaMemcpyAsync(host_J, c->mass_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     DGW_CUDA(cudaStreamSynchronize(s));
     return DGW_OK;
 }

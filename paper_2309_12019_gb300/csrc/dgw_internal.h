@@ -100,6 +100,19 @@ struct BatchArgs {
     int unreachable;               // diagnostic: ask one tile more than exists (wait must give up)
 };
 
+// Discrete adjoint: out = sum_i coef[i] x[i] + cvjp * J_L(U)^T lam, the transpose-Jacobian
+// product assembled from per-cell partials (wself: own, wnb: one block per face).
+struct GatherArgs {
+    int64_t E;
+    int nx, ny;
+    const void* wself;
+    const void* wnb;
+    const void* x[3];      // may be null
+    double coef[3];
+    double cvjp;
+    void* out;
+};
+
 // Launchers, one per (precision, dimension) translation unit.  mode 0: stage or
 // residual; mode 1: sensor only (writes gamma_out).
 cudaError_t launch_stage_f32_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
@@ -115,6 +128,15 @@ int batch_blocks_per_sm_f32_d1();
 int batch_blocks_per_sm_f32_d2();
 int batch_blocks_per_sm_f64_d1();
 int batch_blocks_per_sm_f64_d2();
+
+cudaError_t launch_vjp_f32_d1(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);
+cudaError_t launch_vjp_f32_d2(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);
+cudaError_t launch_vjp_f64_d1(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);
+cudaError_t launch_vjp_f64_d2(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);
+cudaError_t launch_gather_f32_d1(const GatherArgs& g, int p, cudaStream_t s);
+cudaError_t launch_gather_f32_d2(const GatherArgs& g, int p, cudaStream_t s);
+cudaError_t launch_gather_f64_d1(const GatherArgs& g, int p, cudaStream_t s);
+cudaError_t launch_gather_f64_d2(const GatherArgs& g, int p, cudaStream_t s);
 
 cudaError_t upload_tables_f32_d1(const HostTables& t);
 cudaError_t upload_tables_f32_d2(const HostTables& t);

@@ -873,6 +873,50 @@ static cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t st)
     return cudaLaunchKernelEx(&cfg, batch_kernel, a);
 }
 
+#include "dgw_adjoint_impl.cuh"
+
+template <int P>
+static cudaError_t launch_vjp_p(const StageArgs& s, int flux, const void* lam, void* wself, void* wnb,
+                                cudaStream_t st)
+{
+    const KParams a = make_params(s);
+    const unsigned blocks = (unsigned)((s.E + 127) / 128);
+    if (flux == FLUX_ADVECT)
+        vjp_kernel<P, FLUX_ADVECT><<<blocks, 128, 0, st>>>(a, (const Real*)lam, (Real*)wself, (Real*)wnb);
+    else if (flux == FLUX_BURGERS)
+        vjp_kernel<P, FLUX_BURGERS><<<blocks, 128, 0, st>>>(a, (const Real*)lam, (Real*)wself, (Real*)wnb);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_vjp(const StageArgs& s, int p, int flux, const void* lam, void* wself, void* wnb,
+                              cudaStream_t st)
+{
+    switch (p) {
+    case 1: return launch_vjp_p<1>(s, flux, lam, wself, wnb, st);
+    case 2: return launch_vjp_p<2>(s, flux, lam, wself, wnb, st);
+    case 3: return launch_vjp_p<3>(s, flux, lam, wself, wnb, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t launch_gather(const GatherArgs& g, int p, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((g.E + 127) / 128);
+    const Real* x0 = (const Real*)g.x[0];
+    const Real* x1 = (const Real*)g.x[1];
+    const Real* x2 = (const Real*)g.x[2];
+    const Real c0 = (Real)g.coef[0], c1 = (Real)g.coef[1], c2 = (Real)g.coef[2], cv = (Real)g.cvjp;
+    switch (p) {
+    case 1: gather_kernel<1><<<blocks, 128, 0, st>>>(g.E, g.nx, g.ny, (const Real*)g.wself, (const Real*)g.wnb, x0, x1, x2, c0, c1, c2, cv, (Real*)g.out); break;
+    case 2: gather_kernel<2><<<blocks, 128, 0, st>>>(g.E, g.nx, g.ny, (const Real*)g.wself, (const Real*)g.wnb, x0, x1, x2, c0, c1, c2, cv, (Real*)g.out); break;
+    case 3: gather_kernel<3><<<blocks, 128, 0, st>>>(g.E, g.nx, g.ny, (const Real*)g.wself, (const Real*)g.wnb, x0, x1, x2, c0, c1, c2, cv, (Real*)g.out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int P, int FLUX>
 static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
 {

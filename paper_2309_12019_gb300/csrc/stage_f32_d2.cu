@@ -14,5 +14,10 @@ cudaError_t launch_batch_f32_d2(const BatchArgs& a, int grid, cudaStream_t s)
     return f32_d2::launch_batch(a, grid, s);
 }
 int batch_blocks_per_sm_f32_d2() { return f32_d2::batch_blocks_per_sm(); }
+cudaError_t launch_vjp_f32_d2(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s)
+{
+    return f32_d2::launch_vjp(a, p, flux, lam, ws, wn, s);
+}
+cudaError_t launch_gather_f32_d2(const GatherArgs& g, int p, cudaStream_t s) { return f32_d2::launch_gather(g, p, s); }
 cudaError_t upload_tables_f32_d2(const HostTables& t) { return f32_d2::upload_tables(t); }
 }  // namespace dgw

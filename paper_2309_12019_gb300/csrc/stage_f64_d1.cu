@@ -14,5 +14,10 @@ cudaError_t launch_batch_f64_d1(const BatchArgs& a, int grid, cudaStream_t s)
     return f64_d1::launch_batch(a, grid, s);
 }
 int batch_blocks_per_sm_f64_d1() { return f64_d1::batch_blocks_per_sm(); }
+cudaError_t launch_vjp_f64_d1(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s)
+{
+    return f64_d1::launch_vjp(a, p, flux, lam, ws, wn, s);
+}
+cudaError_t launch_gather_f64_d1(const GatherArgs& g, int p, cudaStream_t s) { return f64_d1::launch_gather(g, p, s); }
 cudaError_t upload_tables_f64_d1(const HostTables& t) { return f64_d1::upload_tables(t); }
 }  // namespace dgw

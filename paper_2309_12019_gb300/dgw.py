@@ -53,7 +53,7 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
+           "dgw_sync_status", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
            "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
            "dgw_last_error", "dgw_version")
@@ -83,6 +83,9 @@ def load(build: bool = True):
         L.dgw_rk_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
+        L.dgw_residual_vjp.argtypes = [vp, vp, vp, vp, vp]
+        L.dgw_adjoint_step.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp]
+        L.dgw_misfit.argtypes = [vp, vp, vp, dp, vp, vp]
         L.dgw_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Mesh), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(Flux), ctypes.POINTER(Params), ctypes.POINTER(vp)]
         L.dgw_batch_destroy.argtypes = [vp]
@@ -241,6 +244,23 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+    def residual_vjp(self, U, lam, out, stream=None):
+        """out = J_L(U)^T lam (dgw_residual_vjp)."""
+        _check(load().dgw_residual_vjp(self._h, self._state(U), self._state(lam), self._state(out), _stream(stream)))
+
+    def adjoint_step(self, U_n, lam_np1, lam_n, dt: float, stream=None):
+        """lam_n = (dU^{n+1}/dU^n)^T lam_np1 for one SSP-RK3 step from U_n (dgw_adjoint_step)."""
+        _check(load().dgw_adjoint_step(self._h, self._state(U_n), self._state(lam_np1), self._state(lam_n),
+                                       float(dt), _stream(stream)))
+
+    def misfit(self, U, U_target, grad=None, stream=None) -> float:
+        """J = 1/2 int (U_h - U_target)^2, and grad = dJ/dU if given (dgw_misfit)."""
+        J = ctypes.c_double()
+        g = self._state(grad) if grad is not None else None
+        _check(load().dgw_misfit(self._h, self._state(U), self._state(U_target), ctypes.byref(J), g,
+                                 _stream(stream)))
+        return J.value
 
 
 class Batch:

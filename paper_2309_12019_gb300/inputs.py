@@ -85,9 +85,10 @@ def u0_kpp(x, y):
     return np.where(np.hypot(x, y) <= 1.0, 3.5 * np.pi, 0.25 * np.pi)
 
 
-def fourier_steps_params(dim: int, rng: np.random.Generator, nmodes: int = 8, max_steps: int = 3):
+def fourier_steps_params(dim: int, rng: np.random.Generator, nmodes: int = 8, max_steps: int = 3,
+                         min_steps: int = 0):
     """Random smooth-plus-steps datum: nmodes Fourier modes with amplitude ~U(0,1) plus
-    0..max_steps unit steps (indicators of random periodic intervals / rectangles)."""
+    min_steps..max_steps unit steps (indicators of random periodic intervals / rectangles)."""
     amp = rng.uniform(0.0, 1.0, nmodes)
     phase = rng.uniform(0.0, 2.0 * np.pi, nmodes)
     if dim == 1:
@@ -96,7 +97,7 @@ def fourier_steps_params(dim: int, rng: np.random.Generator, nmodes: int = 8, ma
         k = rng.integers(-4, 5, size=(nmodes, 2))
         zero = np.all(k == 0, axis=1)
         k[zero, 0] = 1
-    nsteps = int(rng.integers(0, max_steps + 1))
+    nsteps = int(rng.integers(min_steps, max_steps + 1))
     lo = rng.uniform(0.0, 1.0, size=(nsteps, dim))
     width = rng.uniform(0.05, 0.4, size=(nsteps, dim))
     return dict(amp=amp, phase=phase, k=k, lo=lo, width=width)
@@ -157,6 +158,12 @@ def ensemble_instances(n: int = 512, seed: int = SEED):
         out.append(dict(dim=dim, nx=cells, ny=cells if dim == 2 else 1, p=p, flux=flux, a=a, dt=dt,
                         init=params))
     return out
+
+
+def adjoint_field(seed: int):
+    """Datum of the adjoint workload: 4 Fourier modes plus exactly one unit step on the
+    periodic unit square (control: seed, target: another seed)."""
+    return fourier_steps_params(2, np.random.default_rng(seed), nmodes=4, max_steps=1, min_steps=1)
 
 
 def sample_points_xp(dim: int, nx: int, ny: int, box, nq: int, xp, **kw):
