@@ -66,12 +66,12 @@ struct dgw_ctx {
     double* mass_dev = nullptr;
     unsigned* flag = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
-    std::map<const void*, CUtensorMap> tmaps;   // TMA descriptors per state array (2D)
+    std::map<std::pair<const void*, int>, CUtensorMap> tmaps;   // TMA descriptors (2D): (array, box kind)
     void* adj_ws = nullptr;      // adjoint: per-cell partials (own), K*E
     void* adj_wn = nullptr;      // adjoint: per-cell partials (one block per face), 2*dim*K*E
     void* adj_b1 = nullptr;      // adjoint: lambda of stage 2
     void* adj_b2 = nullptr;      // adjoint: lambda of stage 1
-    std::map<const void*, bool> no_tmap;
+    std::map<std::pair<const void*, int>, bool> no_tmap;
 };
 
 static const int kMassBlocks = 1024;
@@ -235,22 +235,25 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U)
+// box kind 0: tile plus halo (kBoxX2 x kBoxY2 x K); 1: tile (kTileX2 x kTileY2 x K)
+static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U, int kind = 0)
 {
     dgw_ctx* c = const_cast<dgw_ctx*>(cc);
-    if (c->mesh.dim != 2) return nullptr;
-    auto it = c->tmaps.find(U);
+    if (c->mesh.dim != 2 || !U) return nullptr;
+    const auto key = std::make_pair(U, kind);
+    auto it = c->tmaps.find(key);
     if (it != c->tmaps.end()) return &it->second;
-    if (c->no_tmap.count(U)) return nullptr;
+    if (c->no_tmap.count(key)) return nullptr;
     const uint64_t eb = (uint64_t)c->eb, nx = (uint64_t)c->mesh.nx, ny = (uint64_t)c->mesh.ny;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || (nx * eb) % 16 || (nx * ny * eb) % 16 || ((uintptr_t)U & 15u)) {
-        c->no_tmap[U] = true;
+        c->no_tmap[key] = true;
         return nullptr;
     }
     cuuint64_t dims[3] = {nx, ny, (cuuint64_t)c->K};
     cuuint64_t strides[2] = {nx * eb, nx * ny * eb};
-    cuuint32_t box[3] = {(cuuint32_t)kBoxX2, (cuuint32_t)kBoxY2, (cuuint32_t)c->K};
+    cuuint32_t box[3] = {(cuuint32_t)(kind == 0 ? kBoxX2 : kTileX2), (cuuint32_t)(kind == 0 ? kBoxY2 : kTileY2),
+                         (cuuint32_t)c->K};
     cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
     CUresult r = enc(&m, eb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -258,11 +261,11 @@ static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U)
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
-        c->no_tmap[U] = true;
+        c->no_tmap[key] = true;
         return nullptr;
     }
     if (c->tmaps.size() > 64) c->tmaps.clear();
-    return &(c->tmaps[U] = m);
+    return &(c->tmaps[key] = m);
 }
 
 static StageArgs base_args(const dgw_ctx* c)
@@ -295,7 +298,8 @@ static StageArgs base_args(const dgw_ctx* c)
 static cudaError_t launch(const dgw_ctx* c, const StageArgs& a0, int mode, cudaStream_t s)
 {
     StageArgs a = a0;
-    a.tmap = tensor_map(c, a.Uk);
+    a.tmap = tensor_map(c, a.Uk, 0);
+    a.tmap_un = (a.cn != 0.0 && a.Un) ? tensor_map(c, a.Un, 1) : nullptr;
     const bool f64 = c->params.prec == DGW_FP64;
     if (c->mesh.dim == 1)
         return f64 ? launch_stage_f64_d1(a, c->p, c->flux.kind, mode, s)

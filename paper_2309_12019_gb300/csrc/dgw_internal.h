@@ -62,6 +62,7 @@ struct StageArgs {
     double* gamma_out;     // optional per-element gamma (double)
     unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x kBoxY2 x K), or null
+    const CUtensorMap* tmap_un;  // 2D: TMA descriptor of Un (box kTileX2 x kTileY2 x K), or null
 };
 
 // ------------------------------------------------------------------------------------

@@ -94,7 +94,9 @@ static cudaError_t upload(const HostTables& h)
 // Scalars of one launch, converted once on the host to the kernel precision.
 struct alignas(64) KParams {
     CUtensorMap tmap;    // TMA descriptor of Uk (valid when use_tma)
+    CUtensorMap tmap_un; // TMA descriptor of Un, tile box (valid when use_tma_un)
     int use_tma;
+    int use_tma_un;
     int cg_loads;        // load Uk / Un through L2 only (data written earlier in the same launch)
     const Real* Uk;
     const Real* Un;
@@ -250,16 +252,17 @@ __device__ __forceinline__ int wrap_y(const KParams& A, int gy)
     return -1;
 }
 
-// Bounded wait on phase 0 of an mbarrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait0(uint32_t bar)
+// Bounded wait for the completion of the given phase parity of an mbarrier; false if
+// it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
     for (int it = 0; it < (1 << 22); ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok) : "r"(bar) : "memory");
+            : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
         if (ok) return true;
     }
     return false;
@@ -328,7 +331,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                    "r"(0), "r"(bar)
                 : "memory");
         }
-        if (!mbar_wait0(bar)) fail_s = 1;
+        if (!mbar_wait(bar, 0)) fail_s = 1;
         __syncthreads();
         if (fail_s) {
             if (tid == 0) atomicOr(A.flag, 2u);
@@ -560,6 +563,22 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     }
     __syncthreads();
 
+    // The stage array is no longer read: bring the Un tile into it now, so that its
+    // load overlaps the face phase (second phase of the same mbarrier).
+    const bool un_tma = DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
+    if (un_tma && tid == 0) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+        const uint32_t bytes = (uint32_t)(sizeof(Real) * K * TY * TX);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];"
+            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&A.tmap_un)), "r"(tx0), "r"(ty0), "r"(0), "r"(bar)
+            : "memory");
+    }
+
     // ---- 2. faces: each face of the tile once, from the traces ----
     for (int f = tid; f < NFX + NFY; f += NT) {
         const bool xf = f < NFX;
@@ -656,6 +675,11 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     const Real gs = gamma * lamv / Real(P);   // gamma nu (2/h)
     Real chk = Real(0);                        // becomes NaN if any output is not finite
     const Real* __restrict__ un = A.Un + e;
+    const Real* sun = reinterpret_cast<const Real*>(&su[0][0][0]);   // Un tile [K][TY][TX]
+    if (un_tma && !mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1)) {
+        atomicOr(A.flag, 2u);
+        return;
+    }
     Real* __restrict__ uo = A.Uout + e;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -682,7 +706,10 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         if (DIM == 2) mi *= T.minv[j];
         const Real L = A.two_h * mi * r;
         Real out = A.cl * L + A.ck * c[k];
-        if (A.has_un) out += A.cn * (A.cg_loads ? __ldcg(un + k * E) : un[k * E]);
+        if (A.has_un) {
+            const Real unk = un_tma ? sun[(k * TY + ly) * TX + lx] : (A.cg_loads ? __ldcg(un + k * E) : un[k * E]);
+            out += A.cn * unk;
+        }
         chk = fma(out, Real(0), chk);
         uo[k * E] = out;
     }
@@ -706,10 +733,15 @@ static KParams make_params(const StageArgs& s)
     KParams a;
     memset(&a, 0, sizeof a);
     a.use_tma = 0;
+    a.use_tma_un = 0;
     a.cg_loads = 0;
     if (s.tmap) {
         a.tmap = *s.tmap;
         a.use_tma = 1;
+    }
+    if (s.tmap_un) {
+        a.tmap_un = *s.tmap_un;
+        a.use_tma_un = 1;
     }
     a.Uk = static_cast<const Real*>(s.Uk);
     a.Un = static_cast<const Real*>(s.Un);
@@ -743,6 +775,7 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
 {
     KParams A;
     A.use_tma = 0;
+    A.use_tma_un = 0;
     A.cg_loads = 1;
     const Real* U = static_cast<const Real*>(B.U) + I.off;
     const Real* S1 = static_cast<const Real*>(B.S1) + I.off;
