@@ -67,6 +67,13 @@ def dt_of(w):
     return I.cfl_dt(w["cfl"], w["speeds"], [h] * w["dim"])
 
 
+# DRAM bytes (read + write) per stage launch of the current stage kernel at the
+# 1024^2 Q3 KPP workload, averaged over the three stages of one step, from one ncu
+# capture (profiles/stage_kernel_kpp_1024x1024_q3.md).  Reset to None whenever the
+# stage kernel changes until it is captured again.
+STAGE_TRAFFIC_BYTES = 141.65e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -388,7 +395,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                         "frac": achieved / hbm,
+                         "traffic": STAGE_TRAFFIC_BYTES if args.workload == "kpp_1024x1024_q3" else None,
+                         "peak_source": src,
                          "kernel": "stage_kernel (3 launches per step)"},
             "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": r32.get("bytes"),
                     "d2h_bytes_per_step": r32.get("bytes")} if "t_e2e" in r32 else None,
