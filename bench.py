@@ -71,7 +71,7 @@ def dt_of(w):
 # 1024^2 Q3 KPP workload, averaged over the three stages of one step, from one ncu
 # capture (profiles/stage_kernel_kpp_1024x1024_q3.md).  Reset to None whenever the
 # stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = 141.65e6
+STAGE_TRAFFIC_BYTES = None
 
 
 def peaks():

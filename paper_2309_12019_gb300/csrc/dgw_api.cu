@@ -215,9 +215,9 @@ extern "C" dgw_status dgw_set_params(dgw_ctx* c, const dgw_params* s)
     return DGW_OK;
 }
 
-// TMA descriptor of a state array viewed as a 3D tensor (x: nx, y: ny, k: K) with the
-// stage-tile box (kBoxX2 x kBoxY2 x K).  Null when TMA does not apply: 1D meshes, or
-// row / plane strides that are not multiples of 16 bytes.
+// TMA descriptor of a state array viewed as a 3D tensor (x: nx, y: ny, k: K) with a
+// stage-tile box.  Null when TMA does not apply: 1D meshes, or row / plane strides that
+// are not multiples of 16 bytes.
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -235,7 +235,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// box kind 0: tile plus halo (kBoxX2 x kBoxY2 x K); 1: tile (kTileX2 x kTileY2 x K)
+// box kind 0: tile plus halo (kBoxX2 x (rows + 2) x K); 1: tile (kTileX2 x rows x K),
+// rows = stage_rows() of the context's precision
 static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U, int kind = 0)
 {
     dgw_ctx* c = const_cast<dgw_ctx*>(cc);
@@ -252,7 +253,8 @@ static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U, int kind 
     }
     cuuint64_t dims[3] = {nx, ny, (cuuint64_t)c->K};
     cuuint64_t strides[2] = {nx * eb, nx * ny * eb};
-    cuuint32_t box[3] = {(cuuint32_t)(kind == 0 ? kBoxX2 : kTileX2), (cuuint32_t)(kind == 0 ? kBoxY2 : kTileY2),
+    const int rows = stage_rows(eb == 8);
+    cuuint32_t box[3] = {(cuuint32_t)(kind == 0 ? kBoxX2 : kTileX2), (cuuint32_t)(kind == 0 ? rows + 2 : rows),
                          (cuuint32_t)c->K};
     cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;

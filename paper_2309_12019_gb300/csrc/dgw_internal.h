@@ -13,13 +13,18 @@ constexpr int kMaxN1 = kMaxP + 1;          // modes per direction
 constexpr int kMaxNQ = kMaxP + 2;          // Gauss points per direction (p + 2)
 constexpr int kMaxK = kMaxN1 * kMaxN1;     // modes per element (2D)
 
-// 2D stage tile: TX x TY cells, one thread each.  Its TMA box spans TX + 8 columns
-// (the halo column on each side, widened so the box starts on a 16-byte boundary)
-// and TY + 2 rows, for all K modes.
+// 2D tiles are kTileX2 threads wide.  The batch kernel runs kTileY2 thread rows of one
+// cell each.  The stage kernel runs stage_thread_rows() rows, and in float a thread
+// advances two cells stacked in y (their arithmetic paired on the packed FP32 pipe), so a
+// stage tile spans kTileX2 x stage_rows() cells.  Its TMA box spans kTileX2 + 8 columns
+// (the halo column on each side, widened so the box starts on a 16-byte boundary) and
+// stage_rows() + 2 rows, for all K modes.
 constexpr int kTileX2 = 32;
 constexpr int kTileY2 = 4;
 constexpr int kBoxX2 = kTileX2 + 8;
-constexpr int kBoxY2 = kTileY2 + 2;
+constexpr int stage_lanes(bool f64) { return f64 ? 1 : 2; }
+constexpr int stage_thread_rows(bool f64) { return f64 ? kTileY2 : 2 * kTileY2; }
+constexpr int stage_rows(bool f64) { return stage_thread_rows(f64) * stage_lanes(f64); }
 
 enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2 };
 enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3 };
@@ -61,8 +66,8 @@ struct StageArgs {
     double q, b, w_nbr, eps_w, eps_s;
     double* gamma_out;     // optional per-element gamma (double)
     unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
-    const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x kBoxY2 x K), or null
-    const CUtensorMap* tmap_un;  // 2D: TMA descriptor of Un (box kTileX2 x kTileY2 x K), or null
+    const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x (stage_rows + 2) x K), or null
+    const CUtensorMap* tmap_un;  // 2D: TMA descriptor of Un (box kTileX2 x stage_rows x K), or null
 };
 
 // ------------------------------------------------------------------------------------

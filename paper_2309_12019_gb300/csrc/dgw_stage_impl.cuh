@@ -3,7 +3,9 @@
 // Included by one translation unit per (precision, dimension) with DGW_REAL, DGW_DIM
 // and DGW_NS defined.  Each unit owns its copy of the constant-memory operator tables.
 //
-// One CTA owns a TX x TY tile of cells (one thread per cell).
+// One CTA of TX x TYT threads owns a tile of TX x (TYT L) cells: a thread advances L
+// cells stacked in y, L = 2 in the float 2D stage kernel (the two cells' arithmetic
+// issued as packed FP32 pairs), else 1.
 //   0. It stages the modal coefficients of the tile plus a one-cell face halo in shared
 //      memory: one TMA box load (2D, 16-byte aligned strides) waited on through an
 //      mbarrier with a bounded spin, else cooperative coalesced loads; periodic halo
@@ -12,7 +14,8 @@
 //      sensor from the four face neighbours (Sec. 4), the volume term (Eq. weak2) by
 //      sum factorisation, kept in registers.
 //   2. Every face of the tile once: both traces at the p+2 Gauss points, the local
-//      Lax-Friedrichs flux (Sec. 2), lifted onto the face Legendre modes.
+//      Lax-Friedrichs flux (Sec. 2), lifted onto the face Legendre modes, written over
+//      the face's minus-side trace.
 //   3. Per cell: face contributions, the stabilization gamma nu K c (Sec. 3), M^{-1}
 //      and the SSP-RK3 combination Uout = cn Un + ck Uk + cl L(Uk) (Eq. ssp).
 // Constant factors are folded so that, in the reference element,
@@ -31,15 +34,18 @@ using Real = DGW_REAL;
 constexpr int DIM = DGW_DIM;
 constexpr bool kF32 = sizeof(Real) == 4;
 
-// tile: 128 threads, one cell each
+// tiles: TX threads wide; the batch kernel runs TY thread rows of one cell each (NT
+// threads), the stage kernel TYS rows of LS cells each (NTS threads)
 constexpr int TX = DIM == 1 ? 128 : kTileX2;
 constexpr int TY = DIM == 1 ? 1 : kTileY2;
 constexpr int NT = TX * TY;
+constexpr int TYS = DIM == 1 ? 1 : stage_thread_rows(!kF32);
+constexpr int NTS = TX * TYS;
 constexpr int HX = TX + 8;                 // staged columns: tile at [OX, OX+TX), halo OX-1, OX+TX
 constexpr int OX = 4;
-constexpr int HY = DIM == 1 ? 1 : TY + 2;  // staged rows
 constexpr int OY = DIM == 1 ? 0 : 1;       // row offset of the tile inside the stage
-static_assert(DIM == 1 || (HX == kBoxX2 && HY == kBoxY2), "TMA box and stage layout disagree");
+constexpr int LS = DIM == 2 ? stage_lanes(!kF32) : 1;
+static_assert(DIM == 1 || (HX == kBoxX2 && TYS * LS == stage_rows(!kF32)), "TMA box and stage layout disagree");
 
 template <int P>
 struct Tab {
@@ -47,6 +53,8 @@ struct Tab {
     Real g[NQ], w[NQ];
     Real B[NQ][N1];      // P_i(g_q)
     Real D[NQ][N1];      // P_i'(g_q)
+    Real WB[NQ][N1];     // w_q P_i(g_q)
+    Real WD[NQ][N1];     // w_q P_i'(g_q)
     Real T[2][N1][N1];   // Hermite shift: coefficient of P_i in P_m(xi + 2) / P_m(xi - 2)
     Real Gu[K][K];       // seminorm Gram, upper triangle with doubled off-diagonal
     Real A1[N1][N1];     // int P_i' P_m'
@@ -71,7 +79,12 @@ static cudaError_t upload(const HostTables& h)
     for (int q = 0; q < NQ; ++q) {
         t.g[q] = (Real)h.g[q];
         t.w[q] = (Real)h.w[q];
-        for (int i = 0; i < N1; ++i) { t.B[q][i] = (Real)h.B[q][i]; t.D[q][i] = (Real)h.D[q][i]; }
+        for (int i = 0; i < N1; ++i) {
+            t.B[q][i] = (Real)h.B[q][i];
+            t.D[q][i] = (Real)h.D[q][i];
+            t.WB[q][i] = (Real)(h.w[q] * h.B[q][i]);
+            t.WD[q][i] = (Real)(h.w[q] * h.D[q][i]);
+        }
     }
     for (int s = 0; s < 2; ++s)
         for (int i = 0; i < N1; ++i)
@@ -162,6 +175,46 @@ __device__ __forceinline__ Real speed_norm(const KParams& A, Real u, Real x, Rea
     return spd;
 }
 
+// ------------------------------------------------------------------------------------
+// Cells per thread.  With L = 2 (float, 2D) a thread advances two cells stacked in y and
+// each arithmetic step of the pair is one packed FP32 instruction (FFMA2 / FMUL2 / FADD2,
+// sm_100 and later): V = float2, lane l holding cell l.  L = 1 is plain scalar code.
+// ------------------------------------------------------------------------------------
+template <int L> struct VecOf { using type = Real; };
+template <> struct VecOf<2> { using type = float2; };
+
+__device__ __forceinline__ Real& lane(Real& v, int) { return v; }
+__device__ __forceinline__ Real lane(const Real& v, int) { return v; }
+__device__ __forceinline__ float& lane(float2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ float lane(const float2& v, int l) { return l ? v.y : v.x; }
+
+template <class V> __device__ __forceinline__ V vbc(Real s) { return s; }
+template <> __device__ __forceinline__ float2 vbc<float2>(Real s) { return make_float2((float)s, (float)s); }
+
+__device__ __forceinline__ Real vfma(Real a, Real b, Real c) { return fma(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vfma(float a, float2 b, float2 c) { return __ffma2_rn(make_float2(a, a), b, c); }
+__device__ __forceinline__ Real vmul(Real a, Real b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float a, float2 b) { return __fmul2_rn(make_float2(a, a), b); }
+__device__ __forceinline__ Real vadd(Real a, Real b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ Real vsub(Real a, Real b) { return a - b; }
+// a - b as one fused step: b * (-1) + a rounds once, exactly like the subtraction
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ Real vmax(Real a, Real b) { return fmax(a, b); }
+__device__ __forceinline__ float2 vmax(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+
+template <class V> struct Lanes { static constexpr int n = 1; };
+template <> struct Lanes<float2> { static constexpr int n = 2; };
+
+template <int FLUX, class V>
+__device__ __forceinline__ void vol_flux_v(const KParams& A, V u, Real x, V y, V& fx, V& fy, V& spd)
+{
+#pragma unroll
+    for (int l = 0; l < Lanes<V>::n; ++l) vol_flux<FLUX>(A, lane(u, l), x, lane(y, l), lane(fx, l), lane(fy, l), lane(spd, l));
+}
+
 // F'(u) along the axis (inflow test of the ghost state).
 template <int FLUX>
 __device__ __forceinline__ Real dflux_axis(const KParams& A, int axis, Real u, Real x, Real y)
@@ -205,20 +258,20 @@ __device__ __forceinline__ Real llf(const KParams& A, int axis, Real uL, Real uR
 }
 
 // v^T G v over modes >= 1; G vanishes unless both Legendre degree pairs have even sums.
-template <int P>
-__device__ __forceinline__ Real qform(const Tab<P>& T, const Real* v)
+template <int P, class V>
+__device__ __forceinline__ V qform(const Tab<P>& T, const V* v)
 {
     constexpr int N1 = P + 1, K = Tab<P>::K;
-    Real s = Real(0);
+    V s = vbc<V>(0);
 #pragma unroll
     for (int a = 1; a < K; ++a) {
-        Real t = Real(0);
+        V t = vbc<V>(0);
 #pragma unroll
         for (int b = a; b < K; ++b) {
             const int ia = a % N1, ja = a / N1, ib = b % N1, jb = b / N1;
-            if (((ia + ib) & 1) == 0 && ((ja + jb) & 1) == 0) t = fma(T.Gu[a][b], v[b], t);
+            if (((ia + ib) & 1) == 0 && ((ja + jb) & 1) == 0) t = vfma(T.Gu[a][b], v[b], t);
         }
-        s = fma(v[a], t, s);
+        s = vfma(v[a], t, s);
     }
     return s;
 }
@@ -268,38 +321,48 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// Shared memory of one tile (carved from dynamic shared memory).
-template <int P>
+// Shared memory of one tile of TX x (TYT * L) cells (carved from dynamic shared memory).
+template <int P, int L, int TYT>
 struct TileSmem {
     static constexpr int N1 = P + 1, K = Tab<P>::K, TN = DIM == 1 ? 1 : N1;
-    alignas(128) Real su[K][HY][HX];
-    // cell index innermost: a warp touches consecutive words (no bank conflicts)
-    Real trx[TY][2][TN][TX + 2];                          // x-traces, col = lx + 1
-    Real trys[DIM == 2 ? TY + 2 : 1][2][TN][TX];          // y-traces, row = ly + 1
-    Real hfx[TY][TN][TX + 1];
-    Real hfy[DIM == 2 ? TY + 1 : 1][TN][TX];
-    Real lam_s[TY][TX];
+    static constexpr int TYC = TYT * L;                   // cell rows
+    static constexpr int HYC = DIM == 1 ? 1 : TYC + 2;    // staged rows
+    alignas(128) Real su[K][HYC][HX];
+    // cell index innermost: a warp touches consecutive words (no bank conflicts).
+    // The face phase overwrites the minus-side trace of every face with the face's
+    // lifted flux: trx[r][1][t][c] becomes the flux of x-face c of row r (between cells
+    // c - 1 and c), trys[r][1][t][c] that of y-face r of column c.  Each such slot is
+    // read by its own face only, before the write.
+    Real trx[TYC][2][TN][TX + 2];                         // x-traces, col = lx + 1
+    Real trys[DIM == 2 ? TYC + 2 : 1][2][TN][TX];         // y-traces, row = cell row + 1
+    Real lam_s[TYC][TX];
     alignas(8) uint64_t mbar;
     int fail_s;
 };
 
-// One tile of one stage.  Called by all NT threads of a CTA together (it contains
+// One tile of one stage.  Called by all TX x TYT threads of a CTA together (it contains
 // CTA barriers); tx0, ty0: first cell of the tile.  MODE 0: stage / residual;
-// MODE 1: sensor only.
-template <int P, int FLUX, int MODE>
-__device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P>& S)
+// MODE 1: sensor only.  Thread (lx, ly) owns the cells (lx, L ly + l), l < L; with
+// L = 2 their arithmetic runs as packed pairs (lane l = cell l).  Lanes of cells outside
+// the mesh (ragged tiles) compute on zero-filled data and store nothing.
+template <int P, int FLUX, int MODE, int L, int TYT>
+__device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P, L, TYT>& S)
 {
+    static_assert(L == 1 || (kF32 && DIM == 2), "two cells per thread: float, 2D only");
+    using V = typename VecOf<L>::type;
     constexpr int N1 = P + 1, NQ = P + 2;
     constexpr int K = Tab<P>::K;
-    constexpr int NFX = (TX + 1) * TY;                 // x-faces of the tile
-    constexpr int NFY = DIM == 2 ? TX * (TY + 1) : 0;  // y-faces
-    constexpr int TN = DIM == 1 ? 1 : N1;              // trace / face coefficients
+    constexpr int NT = TX * TYT;                         // threads
+    constexpr int TYC = TYT * L;                         // cell rows of the tile
+    constexpr int HYC = DIM == 1 ? 1 : TYC + 2;          // staged rows
+    constexpr int TXL = TX / L;
+    constexpr int NFX = (TX + 1) * TYT;                  // x-face items; lanes: the thread row's L cell rows
+    constexpr int NFY = DIM == 2 ? TXL * (TYC + 1) : 0;  // y-face items; lanes: columns c + l TXL
+    constexpr int TN = DIM == 1 ? 1 : N1;                // trace / face coefficients
     const Tab<P>& T = tab<P>();
     auto& su = S.su;
     auto& trx = S.trx;
     auto& trys = S.trys;
-    auto& hfx = S.hfx;
-    auto& hfy = S.hfy;
     auto& lam_s = S.lam_s;
     auto& mbar = S.mbar;
     auto& fail_s = S.fail_s;
@@ -320,7 +383,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         }
         __syncthreads();
         if (tid == 0) {
-            const uint32_t bytes = (uint32_t)(sizeof(Real) * K * HY * HX);
+            const uint32_t bytes = (uint32_t)(sizeof(Real) * K * HYC * HX);
             const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(bar), "r"(bytes) : "memory");
@@ -339,11 +402,11 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         }
         // periodic images of halo cells that lie outside the box's wrap-free view
         const bool edge = (periodic_x && (tx0 == 0 || tx0 + TX >= A.nx)) ||
-                          (periodic_y && (ty0 == 0 || ty0 + TY >= A.ny));
+                          (periodic_y && (ty0 == 0 || ty0 + TYC >= A.ny));
         if (edge) {
-            for (int idx = tid; idx < K * HY * HX; idx += NT) {
-                const int k = idx / (HY * HX);
-                const int rem = idx - k * (HY * HX);
+            for (int idx = tid; idx < K * HYC * HX; idx += NT) {
+                const int k = idx / (HYC * HX);
+                const int rem = idx - k * (HYC * HX);
                 const int r = rem / HX, cc = rem - r * HX;
                 const int ux = tx0 - OX + cc, uy = ty0 - OY + r;     // unwrapped
                 if (ux < -1 || ux > A.nx || uy < -1 || uy > A.ny) continue;
@@ -357,14 +420,19 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
             __syncthreads();
         }
     } else {
-        for (int idx = tid; idx < HY * HX; idx += NT) {
+        for (int idx = tid; idx < HYC * HX; idx += NT) {
             const int r = idx / HX, cc = idx - r * HX;
             if (cc < OX - 1 || cc > OX + TX) continue;
-            const bool corner = DIM == 2 && (r == 0 || r == HY - 1) && (cc == OX - 1 || cc == OX + TX);
+            const bool corner = DIM == 2 && (r == 0 || r == HYC - 1) && (cc == OX - 1 || cc == OX + TX);
             if (corner) continue;
             const int gx = wrap_x(A, tx0 - OX + cc);
             const int gy = DIM == 2 ? wrap_y(A, ty0 - OY + r) : 0;
-            if (gx < 0 || gy < 0) continue;
+            if (gx < 0 || gy < 0) {
+                // no cell here: zeros keep the arithmetic of masked lanes finite
+#pragma unroll
+                for (int k = 0; k < K; ++k) su[k][r][cc] = Real(0);
+                continue;
+            }
             const Real* src = A.Uk + (int64_t)gy * A.nx + gx;
             if (A.cg_loads) {
 #pragma unroll
@@ -378,45 +446,59 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     }
 
     const int lx = tid % TX, ly = tid / TX;
-    const int gx = tx0 + lx, gy = ty0 + ly;
-    const bool in_domain = gx < A.nx && (DIM == 1 || gy < A.ny);
-    const int sr = ly + OY, sc = lx + OX;
-
-    Real c[K];
+    const int gx = tx0 + lx;
+    const int sc = lx + OX;
+    int cy[L], gy[L];          // tile row and mesh row of lane l's cell
+    bool in[L];
+    bool any_in = false;
 #pragma unroll
-    for (int k = 0; k < K; ++k) c[k] = su[k][sr][sc];
+    for (int l = 0; l < L; ++l) {
+        cy[l] = L * ly + l;
+        gy[l] = ty0 + cy[l];
+        in[l] = gx < A.nx && (DIM == 1 || gy[l] < A.ny);
+        any_in = any_in || in[l];
+    }
 
-    // ---- 1a. traces of this cell's slot (also for slots that hold periodic images) ----
+    V c[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int l = 0; l < L; ++l) lane(c[k], l) = su[k][cy[l] + OY][sc];
+
+    // ---- 1a. traces of this thread's slots (also for slots that hold periodic images) ----
     if (MODE == 0) {
 #pragma unroll
         for (int t = 0; t < TN; ++t) {
-            Real xm = Real(0), xp = Real(0), ym = Real(0), yp = Real(0);
+            V xm = vbc<V>(0), xp = vbc<V>(0), ym = vbc<V>(0), yp = vbc<V>(0);
 #pragma unroll
             for (int n = 0; n < N1; ++n) {
-                const Real kx = DIM == 1 ? c[n] : c[n + N1 * t];
-                xp += kx;
-                xm += (n & 1) ? -kx : kx;
+                const V kx = DIM == 1 ? c[n] : c[n + N1 * t];
+                xp = vadd(xp, kx);
+                xm = (n & 1) ? vsub(xm, kx) : vadd(xm, kx);
                 if (DIM == 2) {
-                    const Real ky = c[t + N1 * n];
-                    yp += ky;
-                    ym += (n & 1) ? -ky : ky;
+                    const V ky = c[t + N1 * n];
+                    yp = vadd(yp, ky);
+                    ym = (n & 1) ? vsub(ym, ky) : vadd(ym, ky);
                 }
             }
-            trx[ly][0][t][lx + 1] = xm;
-            trx[ly][1][t][lx + 1] = xp;
-            if (DIM == 2) {
-                trys[ly + 1][0][t][lx] = ym;
-                trys[ly + 1][1][t][lx] = yp;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                trx[cy[l]][0][t][lx + 1] = lane(xm, l);
+                trx[cy[l]][1][t][lx + 1] = lane(xp, l);
+                if (DIM == 2) {
+                    trys[cy[l] + 1][0][t][lx] = lane(ym, l);
+                    trys[cy[l] + 1][1][t][lx] = lane(yp, l);
+                }
             }
         }
         // halo cells: the one trace that faces the tile
-        constexpr int NH = 2 * TY + (DIM == 2 ? 2 * TX : 0);
+        constexpr int NH = 2 * TYC + (DIM == 2 ? 2 * TX : 0);
         for (int hidx = tid; hidx < NH; hidx += NT) {
             int r, cc, side, axis;
-            if (hidx < TY) { r = hidx + OY; cc = OX - 1; axis = 0; side = 1; }
-            else if (hidx < 2 * TY) { r = hidx - TY + OY; cc = OX + TX; axis = 0; side = 0; }
-            else if (hidx < 2 * TY + TX) { r = 0; cc = OX + hidx - 2 * TY; axis = 1; side = 1; }
-            else { r = HY - 1; cc = OX + hidx - 2 * TY - TX; axis = 1; side = 0; }
+            if (hidx < TYC) { r = hidx + OY; cc = OX - 1; axis = 0; side = 1; }
+            else if (hidx < 2 * TYC) { r = hidx - TYC + OY; cc = OX + TX; axis = 0; side = 0; }
+            else if (hidx < 2 * TYC + TX) { r = 0; cc = OX + hidx - 2 * TYC; axis = 1; side = 1; }
+            else { r = HYC - 1; cc = OX + hidx - 2 * TYC - TX; axis = 1; side = 0; }
 #pragma unroll
             for (int t = 0; t < TN; ++t) {
                 Real v = Real(0);
@@ -427,138 +509,163 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                     v += (side == 0 && (n & 1)) ? -ck : ck;
                 }
                 if (axis == 0) trx[r - OY][side][t][cc == OX - 1 ? 0 : TX + 1] = v;
-                else trys[r == 0 ? 0 : TY + 1][side][t][cc - OX] = v;
+                else trys[r == 0 ? 0 : TYC + 1][side][t][cc - OX] = v;
             }
         }
-        if (need_lam) lam_s[ly][lx] = Real(0);
+        if (need_lam) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) lam_s[cy[l]][lx] = Real(0);
+        }
     }
 
     // ---- 1b. sensor (Sec. 4): Hermite candidates of the face neighbours ----
-    Real gamma = (MODE == 0 && A.stab == STAB_LO) ? Real(1) : Real(0);
-    if ((MODE == 1 || A.stab == STAB_WENO) && in_domain) {
-        bool has[2 * DIM];
-        int me = 0;
+    V gamma = vbc<V>((MODE == 0 && A.stab == STAB_LO) ? Real(1) : Real(0));
+    if ((MODE == 1 || A.stab == STAB_WENO) && any_in) {
+        bool has[2 * DIM][L];   // face neighbour f of lane l's cell exists
+        V wsum;
+        const V beta0 = qform<P>(T, c);
+        const V d0 = vadd(vbc<V>(A.eps_w), beta0);
 #pragma unroll
-        for (int f = 0; f < 2 * DIM; ++f) {
-            const int nx_ = gx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
-            const int ny_ = gy + (f == 2 ? -1 : (f == 3 ? 1 : 0));
-            has[f] = (f < 2) ? (wrap_x(A, nx_) >= 0) : (wrap_y(A, ny_) >= 0);
-            me += has[f] ? 1 : 0;
+        for (int l = 0; l < L; ++l) {
+            int me = 0;
+#pragma unroll
+            for (int f = 0; f < 2 * DIM; ++f) {
+                const int nx_ = gx + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+                const int ny_ = gy[l] + (f == 2 ? -1 : (f == 3 ? 1 : 0));
+                has[f][l] = (f < 2) ? (wrap_x(A, nx_) >= 0) : (wrap_y(A, ny_) >= 0);
+                me += has[f][l] ? 1 : 0;
+            }
+            lane(wsum, l) = (Real(1) - Real(me) * A.w_nbr) / (lane(d0, l) * lane(d0, l));
         }
-        const Real beta0 = qform<P>(T, c);
-        const Real d0 = A.eps_w + beta0;
-        Real wsum = (Real(1) - Real(me) * A.w_nbr) / (d0 * d0);
-        Real dacc[K];
+        V dacc[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) dacc[k] = Real(0);
+        for (int k = 0; k < K; ++k) dacc[k] = vbc<V>(0);
 #pragma unroll
         for (int f = 0; f < 2 * DIM; ++f) {
-            if (!has[f]) continue;
-            const int axis = f >> 1, side = f & 1;
-            const int nr = sr + (f == 2 ? -1 : (f == 3 ? 1 : 0));
-            const int nc = sc + (f == 0 ? -1 : (f == 1 ? 1 : 0));
-            Real cn[K];
+            bool any = false;
 #pragma unroll
-            for (int k = 0; k < K; ++k) cn[k] = su[k][nr][nc];
-            Real cl[K];
+            for (int l = 0; l < L; ++l) any = any || has[f][l];
+            if (!any) continue;
+            const int axis = f >> 1, side = f & 1;
+            const int dr = f == 2 ? -1 : (f == 3 ? 1 : 0);
+            const int nc = sc + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+            V cn[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int l = 0; l < L; ++l) lane(cn[k], l) = su[k][cy[l] + OY + dr][nc];
+            V cl[K];
 #pragma unroll
             for (int k = 1; k < K; ++k) {
                 const int i = k % N1, j = k / N1;
                 const int a = axis == 0 ? i : j;
-                Real sacc = Real(0);
+                V sacc = vbc<V>(0);
 #pragma unroll
                 for (int m = 0; m < N1; ++m) {
                     if (m < a) continue;   // P_m(xi +- 2) has degree m
                     const int km = axis == 0 ? m + N1 * j : i + N1 * m;
-                    sacc = fma(T.T[side][a][m], cn[km], sacc);
+                    sacc = vfma(T.T[side][a][m], cn[km], sacc);
                 }
                 cl[k] = sacc;
             }
-            cl[0] = Real(0);
-            const Real dl = A.eps_w + qform<P>(T, cl);
-            const Real wl = A.w_nbr / (dl * dl);
-            wsum += wl;
+            cl[0] = vbc<V>(0);
+            const V dl = vadd(vbc<V>(A.eps_w), qform<P>(T, cl));
+            V wl;
 #pragma unroll
-            for (int k = 1; k < K; ++k) dacc[k] = fma(wl, c[k] - cl[k], dacc[k]);
+            for (int l = 0; l < L; ++l)
+                lane(wl, l) = has[f][l] ? A.w_nbr / (lane(dl, l) * lane(dl, l)) : Real(0);
+            wsum = vadd(wsum, wl);
+#pragma unroll
+            for (int k = 1; k < K; ++k) dacc[k] = vfma(wl, vsub(c[k], cl[k]), dacc[k]);
         }
         // U - U* = sum_l w_l (c - c_l)
-        const Real inv = Real(1) / wsum;
+        V inv;
 #pragma unroll
-        for (int k = 1; k < K; ++k) dacc[k] *= inv;
-        dacc[0] = Real(0);
-        const Real num = sqrt_r(fmax(qform<P>(T, dacc), Real(0)));
-        if (num <= A.eps_s) {
-            gamma = Real(0);
-        } else if (beta0 <= Real(0)) {
-            gamma = Real(1);
-        } else {
-            const Real r = num / sqrt_r(beta0);
-            gamma = r < Real(1) ? r : Real(1);
-            if (!A.q_one) gamma = pow(gamma, A.q);
-            if (r < A.b) gamma = Real(0);
+        for (int l = 0; l < L; ++l) lane(inv, l) = Real(1) / lane(wsum, l);
+#pragma unroll
+        for (int k = 1; k < K; ++k) dacc[k] = vmul(dacc[k], inv);
+        dacc[0] = vbc<V>(0);
+        const V qd = qform<P>(T, dacc);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const Real num = sqrt_r(fmax(lane(qd, l), Real(0)));
+            const Real b0 = lane(beta0, l);
+            Real g;
+            if (num <= A.eps_s) {
+                g = Real(0);
+            } else if (b0 <= Real(0)) {
+                g = Real(1);
+            } else {
+                const Real r = num / sqrt_r(b0);
+                g = r < Real(1) ? r : Real(1);
+                if (!A.q_one) g = pow(g, A.q);
+                if (r < A.b) g = Real(0);
+            }
+            lane(gamma, l) = g;
+            if (MODE == 1 && in[l]) A.gamma_out[(int64_t)gy[l] * A.nx + gx] = (double)g;
         }
-        if (MODE == 1) A.gamma_out[(int64_t)gy * A.nx + gx] = (double)gamma;
     }
     if (MODE == 1) return;
 
     // ---- 1c. volume term (Eq. weak2): acc_ij = sum_q W_q [D_i B_j Fx + B_i D_j Fy] ----
-    Real acc[K];
+    V acc[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = Real(0);
-    Real lam = Real(0);
+    for (int k = 0; k < K; ++k) acc[k] = vbc<V>(0);
+    V lam = vbc<V>(0);
     const Real xc = A.x0 + (Real(gx) + Real(0.5)) * A.h;
-    const Real yc = DIM == 2 ? A.y0 + (Real(gy) + Real(0.5)) * A.h : Real(0);
-    if (DIM == 1) {
+    V yc;
+#pragma unroll
+    for (int l = 0; l < L; ++l) lane(yc, l) = DIM == 2 ? A.y0 + (Real(gy[l]) + Real(0.5)) * A.h : Real(0);
+    if constexpr (DIM == 1) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            Real u = Real(0);
+            V u = vbc<V>(0);
 #pragma unroll
-            for (int i = 0; i < N1; ++i) u = fma(c[i], T.B[q][i], u);
-            Real fx, fy, spd;
-            vol_flux<FLUX>(A, u, xc + A.hh * T.g[q], Real(0), fx, fy, spd);
-            lam = fmax(lam, spd);
-            const Real wf = T.w[q] * fx;
+            for (int i = 0; i < N1; ++i) u = vfma(T.B[q][i], c[i], u);
+            V fx, fy, spd;
+            vol_flux_v<FLUX>(A, u, xc + A.hh * T.g[q], vbc<V>(0), fx, fy, spd);
+            lam = vmax(lam, spd);
 #pragma unroll
-            for (int i = 0; i < N1; ++i) acc[i] = fma(T.D[q][i], wf, acc[i]);
+            for (int i = 0; i < N1; ++i) acc[i] = vfma(T.WD[q][i], fx, acc[i]);
         }
     } else {
-        Real tmp[N1][NQ];
+        V tmp[N1][NQ];
 #pragma unroll
         for (int j = 0; j < N1; ++j)
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
-                Real sacc = Real(0);
+                V sacc = vbc<V>(0);
 #pragma unroll
-                for (int i = 0; i < N1; ++i) sacc = fma(c[i + N1 * j], T.B[qx][i], sacc);
+                for (int i = 0; i < N1; ++i) sacc = vfma(T.B[qx][i], c[i + N1 * j], sacc);
                 tmp[j][qx] = sacc;
             }
 #pragma unroll
         for (int qy = 0; qy < NQ; ++qy) {
-            const Real y = yc + A.hh * T.g[qy];
-            Real px[N1], py[N1];
+            V y;
 #pragma unroll
-            for (int i = 0; i < N1; ++i) { px[i] = Real(0); py[i] = Real(0); }
+            for (int l = 0; l < L; ++l) lane(y, l) = lane(yc, l) + A.hh * T.g[qy];
+            V px[N1], py[N1];
+#pragma unroll
+            for (int i = 0; i < N1; ++i) { px[i] = vbc<V>(0); py[i] = vbc<V>(0); }
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
-                Real u = Real(0);
+                V u = vbc<V>(0);
 #pragma unroll
-                for (int j = 0; j < N1; ++j) u = fma(tmp[j][qx], T.B[qy][j], u);
-                Real fx, fy, spd;
-                vol_flux<FLUX>(A, u, xc + A.hh * T.g[qx], y, fx, fy, spd);
-                lam = fmax(lam, spd);
-                const Real wfx = T.w[qx] * fx, wfy = T.w[qx] * fy;
+                for (int j = 0; j < N1; ++j) u = vfma(T.B[qy][j], tmp[j][qx], u);
+                V fx, fy, spd;
+                vol_flux_v<FLUX>(A, u, xc + A.hh * T.g[qx], y, fx, fy, spd);
+                lam = vmax(lam, spd);
 #pragma unroll
                 for (int i = 0; i < N1; ++i) {
-                    px[i] = fma(T.D[qx][i], wfx, px[i]);
-                    py[i] = fma(T.B[qx][i], wfy, py[i]);
+                    px[i] = vfma(T.WD[qx][i], fx, px[i]);
+                    py[i] = vfma(T.WB[qx][i], fy, py[i]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < N1; ++j) {
-                const Real bj = T.w[qy] * T.B[qy][j], dj = T.w[qy] * T.D[qy][j];
+            for (int j = 0; j < N1; ++j)
 #pragma unroll
-                for (int i = 0; i < N1; ++i) acc[i + N1 * j] = fma(bj, px[i], fma(dj, py[i], acc[i + N1 * j]));
-            }
+                for (int i = 0; i < N1; ++i)
+                    acc[i + N1 * j] = vfma(T.WB[qy][j], px[i], vfma(T.WD[qy][j], py[i], acc[i + N1 * j]));
         }
     }
     __syncthreads();
@@ -568,7 +675,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     const bool un_tma = DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
     if (un_tma && tid == 0) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
-        const uint32_t bytes = (uint32_t)(sizeof(Real) * K * TY * TX);
+        const uint32_t bytes = (uint32_t)(sizeof(Real) * K * TYC * TX);
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
@@ -582,150 +689,222 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     // ---- 2. faces: each face of the tile once, from the traces ----
     for (int f = tid; f < NFX + NFY; f += NT) {
         const bool xf = f < NFX;
-        int flx, fly;              // tile position of the cell on the plus side of the face
-        if (xf) { fly = f / (TX + 1); flx = f - fly * (TX + 1); }
-        else { const int g = f - NFX; fly = g / TX; flx = g - fly * TX; }
-        const int fgx = tx0 + flx, fgy = ty0 + fly;   // plus-side cell (global, unwrapped)
-        if (xf) { if (fgx > A.nx || fgy >= A.ny) continue; }
-        else { if (fgy > A.ny || fgx >= A.nx) continue; }
-        const int axis = xf ? 0 : 1;
-        const bool minus_in = xf ? (fgx - 1 >= 0 || periodic_x) : (fgy - 1 >= 0 || periodic_y);
-        const bool plus_in = xf ? (fgx < A.nx || periodic_x) : (fgy < A.ny || periodic_y);
-        Real tm[TN], tp[TN];
+        int flx[L], fly[L];        // tile position of the cell on the plus side of lane l's face
+        if (xf) {
+            const int p = f / (TX + 1), col = f - p * (TX + 1);
 #pragma unroll
-        for (int t = 0; t < TN; ++t) {
-            if (xf) { tm[t] = trx[fly][1][t][flx]; tp[t] = trx[fly][0][t][flx + 1]; }
-            else { tm[t] = trys[DIM == 2 ? fly : 0][1][t][flx]; tp[t] = trys[DIM == 2 ? fly + 1 : 0][0][t][flx]; }
+            for (int l = 0; l < L; ++l) { flx[l] = col; fly[l] = L * p + l; }
+        } else {
+            const int g = f - NFX, row = g / TXL, col = g - row * TXL;
+#pragma unroll
+            for (int l = 0; l < L; ++l) { flx[l] = col + l * TXL; fly[l] = row; }
         }
-        Real hq[TN];
+        bool valid[L];
+        bool anyv = false;
 #pragma unroll
-        for (int t = 0; t < TN; ++t) hq[t] = Real(0);
-        Real lm = Real(0), lp = Real(0);
+        for (int l = 0; l < L; ++l) {
+            const int fgx = tx0 + flx[l], fgy = ty0 + fly[l];
+            valid[l] = xf ? (fgx <= A.nx && fgy < A.ny) : (fgy <= A.ny && fgx < A.nx);
+            anyv = anyv || valid[l];
+        }
+        if (!anyv) continue;
+        const int axis = xf ? 0 : 1;
+        // the lanes of an item share the face column (x-faces) or row (y-faces), hence
+        // the boundary situation
+        const int fgx0 = tx0 + flx[0], fgy0 = ty0 + fly[0];
+        const bool minus_in = xf ? (fgx0 - 1 >= 0 || periodic_x) : (fgy0 - 1 >= 0 || periodic_y);
+        const bool plus_in = xf ? (fgx0 < A.nx || periodic_x) : (fgy0 < A.ny || periodic_y);
+        V tm[TN], tp[TN];
+#pragma unroll
+        for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                if (xf) {
+                    lane(tm[t], l) = trx[fly[l]][1][t][flx[l]];
+                    lane(tp[t], l) = trx[fly[l]][0][t][flx[l] + 1];
+                } else {
+                    lane(tm[t], l) = trys[DIM == 2 ? fly[l] : 0][1][t][flx[l]];
+                    lane(tp[t], l) = trys[DIM == 2 ? fly[l] + 1 : 0][0][t][flx[l]];
+                }
+            }
+        V hq[TN];
+#pragma unroll
+        for (int t = 0; t < TN; ++t) hq[t] = vbc<V>(0);
+        V lm = vbc<V>(0), lp = vbc<V>(0);
         constexpr int NFQ = DIM == 1 ? 1 : NQ;
 #pragma unroll
         for (int q = 0; q < NFQ; ++q) {
-            Real uL = Real(0), uR = Real(0);
-            if (DIM == 1) { uL = tm[0]; uR = tp[0]; }
-            else {
+            V uL, uR;
+            if constexpr (DIM == 1) {
+                uL = tm[0];
+                uR = tp[0];
+            } else {
+                uL = vbc<V>(0);
+                uR = vbc<V>(0);
 #pragma unroll
-                for (int t = 0; t < TN; ++t) { uL = fma(tm[t], T.B[q][t], uL); uR = fma(tp[t], T.B[q][t], uR); }
+                for (int t = 0; t < TN; ++t) { uL = vfma(T.B[q][t], tm[t], uL); uR = vfma(T.B[q][t], tp[t], uR); }
             }
-            Real x = Real(0), y = Real(0);
-            if (FLUX == FLUX_ROTATION || need_lam || !minus_in || !plus_in) {
-                if (xf) { x = A.x0 + Real(fgx) * A.h; y = DIM == 2 ? A.y0 + (Real(fgy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
-                else { x = A.x0 + (Real(fgx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(fgy) * A.h; }
-            }
-            if (!minus_in) {
-                // ghost for the plus cell, whose outward normal is -e_axis
-                const int bside = xf ? 0 : 2;
-                uL = (A.bc[bside] == BC_INFLOW_ZERO && -dflux_axis<FLUX>(A, axis, uR, x, y) < Real(0)) ? Real(0) : uR;
-            } else if (!plus_in) {
-                const int bside = xf ? 1 : 3;
-                uR = (A.bc[bside] == BC_INFLOW_ZERO && dflux_axis<FLUX>(A, axis, uL, x, y) < Real(0)) ? Real(0) : uL;
-            }
-            if (need_lam) {
-                lm = fmax(lm, speed_norm<FLUX>(A, uL, x, y));
-                lp = fmax(lp, speed_norm<FLUX>(A, uR, x, y));
-            }
-            const Real H = llf<FLUX>(A, axis, uL, uR, x, y) * (DIM == 1 ? Real(1) : T.w[q]);
+            V H;
 #pragma unroll
-            for (int t = 0; t < TN; ++t) hq[t] = fma(DIM == 1 ? Real(1) : T.B[q][t], H, hq[t]);
+            for (int l = 0; l < L; ++l) {
+                Real x = Real(0), y = Real(0);
+                if (FLUX == FLUX_ROTATION || need_lam || !minus_in || !plus_in) {
+                    const int fgx = tx0 + flx[l], fgy = ty0 + fly[l];
+                    if (xf) { x = A.x0 + Real(fgx) * A.h; y = DIM == 2 ? A.y0 + (Real(fgy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
+                    else { x = A.x0 + (Real(fgx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(fgy) * A.h; }
+                }
+                Real ul = lane(uL, l), ur = lane(uR, l);
+                if (!minus_in) {
+                    // ghost for the plus cell, whose outward normal is -e_axis
+                    const int bside = xf ? 0 : 2;
+                    ul = (A.bc[bside] == BC_INFLOW_ZERO && -dflux_axis<FLUX>(A, axis, ur, x, y) < Real(0)) ? Real(0) : ur;
+                } else if (!plus_in) {
+                    const int bside = xf ? 1 : 3;
+                    ur = (A.bc[bside] == BC_INFLOW_ZERO && dflux_axis<FLUX>(A, axis, ul, x, y) < Real(0)) ? Real(0) : ul;
+                }
+                if (need_lam) {
+                    lane(lm, l) = fmax(lane(lm, l), speed_norm<FLUX>(A, ul, x, y));
+                    lane(lp, l) = fmax(lane(lp, l), speed_norm<FLUX>(A, ur, x, y));
+                }
+                lane(H, l) = llf<FLUX>(A, axis, ul, ur, x, y);
+            }
+#pragma unroll
+            for (int t = 0; t < TN; ++t) hq[t] = DIM == 1 ? vadd(hq[t], H) : vfma(T.WB[q][t], H, hq[t]);
         }
-        if (xf) {
+        // the flux replaces the minus-side trace, which only this face reads
 #pragma unroll
-            for (int t = 0; t < TN; ++t) hfx[fly][t][flx] = hq[t];
-        } else {
+        for (int l = 0; l < L; ++l) {
+            if (xf) {
 #pragma unroll
-            for (int t = 0; t < TN; ++t) hfy[DIM == 2 ? fly : 0][t][flx] = hq[t];
+                for (int t = 0; t < TN; ++t) trx[fly[l]][1][t][flx[l]] = lane(hq[t], l);
+            } else {
+#pragma unroll
+                for (int t = 0; t < TN; ++t) trys[DIM == 2 ? fly[l] : 0][1][t][flx[l]] = lane(hq[t], l);
+            }
         }
         if (need_lam) {
-            // only traces of this tile's cells that lie in the domain count
-            const int mlx = xf ? flx - 1 : flx, mly = xf ? fly : fly - 1;
-            if (minus_in && mlx >= 0 && mly >= 0 && (xf ? fgx - 1 < A.nx : fgy - 1 < A.ny))
-                atomic_max_nonneg(&lam_s[mly][mlx], lm);
-            if (plus_in && flx < TX && fly < TY && fgx < A.nx && fgy < A.ny)
-                atomic_max_nonneg(&lam_s[fly][flx], lp);
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                if (!valid[l]) continue;
+                // only traces of this tile's cells that lie in the domain count
+                const int fgx = tx0 + flx[l], fgy = ty0 + fly[l];
+                const int mlx = xf ? flx[l] - 1 : flx[l], mly = xf ? fly[l] : fly[l] - 1;
+                if (minus_in && mlx >= 0 && mly >= 0 && (xf ? fgx - 1 < A.nx : fgy - 1 < A.ny))
+                    atomic_max_nonneg(&lam_s[mly][mlx], lane(lm, l));
+                if (plus_in && flx[l] < TX && fly[l] < TYC && fgx < A.nx && fgy < A.ny)
+                    atomic_max_nonneg(&lam_s[fly[l]][flx[l]], lane(lp, l));
+            }
         }
     }
     __syncthreads();
-    if (!in_domain) return;
-    const int64_t e = (int64_t)gy * A.nx + gx;
+    if (!any_in) return;
 
     // ---- 3. faces: -phi_k(+1) H on the plus faces, +phi_k(-1) H on the minus faces ----
-    if (DIM == 1) {
-        const Real hm = hfx[0][0][lx], hp = hfx[0][0][lx + 1];
+    if constexpr (DIM == 1) {
+        const V hm = trx[0][1][0][lx], hp = trx[0][1][0][lx + 1];
+        const V de = vsub(hm, hp), dd = vadd(hm, hp);
 #pragma unroll
-        for (int n = 0; n < N1; ++n) acc[n] += ((n & 1) ? -hm : hm) - hp;
+        for (int n = 0; n < N1; ++n) acc[n] = (n & 1) ? vsub(acc[n], dd) : vadd(acc[n], de);
     } else {
 #pragma unroll
         for (int t = 0; t < N1; ++t) {
-            const Real xm = hfx[ly][t][lx], xp = hfx[ly][t][lx + 1];
-            const Real ym = hfy[DIM == 2 ? ly : 0][t][lx], yp = hfy[DIM == 2 ? ly + 1 : 0][t][lx];
+            V xm, xp, ym, yp;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                lane(xm, l) = trx[cy[l]][1][t][lx];
+                lane(xp, l) = trx[cy[l]][1][t][lx + 1];
+                lane(ym, l) = trys[cy[l]][1][t][lx];
+                lane(yp, l) = trys[cy[l] + 1][1][t][lx];
+            }
+            // even n: += (m - p); odd n: += (-m - p), i.e. -= (m + p)
+            const V dxe = vsub(xm, xp), dxo = vadd(xm, xp);
+            const V dye = vsub(ym, yp), dyo = vadd(ym, yp);
 #pragma unroll
             for (int n = 0; n < N1; ++n) {
-                acc[n + N1 * t] += ((n & 1) ? -xm : xm) - xp;
-                acc[t + N1 * n] += ((n & 1) ? -ym : ym) - yp;
+                acc[n + N1 * t] = (n & 1) ? vsub(acc[n + N1 * t], dxo) : vadd(acc[n + N1 * t], dxe);
+                acc[t + N1 * n] = (n & 1) ? vsub(acc[t + N1 * n], dyo) : vadd(acc[t + N1 * n], dye);
             }
         }
     }
-    if (need_lam) lam = fmax(lam, lam_s[ly][lx]);
+    if (need_lam) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) lane(lam, l) = fmax(lane(lam, l), lam_s[cy[l]][lx]);
+    }
 
     // stabilization (Sec. 3), M^{-1}, RK combination (Eq. ssp)
-    const Real lamv = A.lam_fixed ? A.lambda_nu : lam;
-    const Real gs = gamma * lamv / Real(P);   // gamma nu (2/h)
-    Real chk = Real(0);                        // becomes NaN if any output is not finite
-    const Real* __restrict__ un = A.Un + e;
-    const Real* sun = reinterpret_cast<const Real*>(&su[0][0][0]);   // Un tile [K][TY][TX]
+    V ngs;                     // -gamma nu (2/h), per cell
+    bool any_gamma = false;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const Real lamv = A.lam_fixed ? A.lambda_nu : lane(lam, l);
+        lane(ngs, l) = -(lane(gamma, l) * lamv / Real(P));
+        any_gamma = any_gamma || lane(gamma, l) != Real(0);
+    }
+    V chk = vbc<V>(0);         // becomes NaN if any output is not finite
+    const Real* sun = reinterpret_cast<const Real*>(&su[0][0][0]);   // Un tile [K][TYC][TX]
     if (un_tma && !mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1)) {
         atomicOr(A.flag, 2u);
         return;
     }
-    Real* __restrict__ uo = A.Uout + e;
+    int64_t e[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) e[l] = (int64_t)gy[l] * A.nx + gx;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int i = k % N1, j = k / N1;
-        Real r = acc[k];
-        if (gamma != Real(0)) {
-            Real kc = Real(0);
-            if (DIM == 1) {
+        V r = acc[k];
+        if (any_gamma) {
+            V kc;
+            if constexpr (DIM == 1) {
+                kc = vbc<V>(0);
 #pragma unroll
                 for (int m = 1; m < N1; ++m)
-                    if (((i + m) & 1) == 0 && i > 0) kc = fma(T.A1[i][m], c[m], kc);
+                    if (((i + m) & 1) == 0 && i > 0) kc = vfma(T.A1[i][m], c[m], kc);
             } else {
-                Real s1 = Real(0), s2 = Real(0);
+                V s1 = vbc<V>(0), s2 = vbc<V>(0);
 #pragma unroll
                 for (int m = 1; m < N1; ++m) {
-                    if (((i + m) & 1) == 0 && i > 0) s1 = fma(T.A1[i][m], c[m + N1 * j], s1);
-                    if (((j + m) & 1) == 0 && j > 0) s2 = fma(T.A1[j][m], c[i + N1 * m], s2);
+                    if (((i + m) & 1) == 0 && i > 0) s1 = vfma(T.A1[i][m], c[m + N1 * j], s1);
+                    if (((j + m) & 1) == 0 && j > 0) s2 = vfma(T.A1[j][m], c[i + N1 * m], s2);
                 }
-                kc = s1 * T.A0[j] + T.A0[i] * s2;
+                kc = vfma(T.A0[i], s2, vmul(T.A0[j], s1));
             }
-            r -= gs * kc;
+            r = vfma(ngs, kc, r);
         }
         Real mi = T.minv[i];
         if (DIM == 2) mi *= T.minv[j];
-        const Real L = A.two_h * mi * r;
-        Real out = A.cl * L + A.ck * c[k];
+        const V Lk = vmul(A.two_h * mi, r);
+        V out = vfma(A.cl, Lk, vmul(A.ck, c[k]));
         if (A.has_un) {
-            const Real unk = un_tma ? sun[(k * TY + ly) * TX + lx] : (A.cg_loads ? __ldcg(un + k * E) : un[k * E]);
-            out += A.cn * unk;
+            V unk;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const Real* un = A.Un + e[l] + k * E;
+                lane(unk, l) = un_tma ? sun[(k * TYC + cy[l]) * TX + lx]
+                                      : (in[l] ? (A.cg_loads ? __ldcg(un) : *un) : Real(0));
+            }
+            out = vfma(A.cn, unk, out);
         }
-        chk = fma(out, Real(0), chk);
-        uo[k * E] = out;
+        chk = vfma(out, vbc<V>(0), chk);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            if (in[l]) A.Uout[e[l] + k * E] = lane(out, l);
     }
-    if (chk != chk) atomicOr(A.flag, 1u);
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        if (in[l] && lane(chk, l) != lane(chk, l)) atomicOr(A.flag, 1u);
 }
 
 template <int P, int FLUX, int MODE>
-__global__ void __launch_bounds__(NT, kF32 ? 6 : 3) stage_kernel(const __grid_constant__ KParams A)
+__global__ void __launch_bounds__(NTS, LS == 2 ? 512 / NTS : (kF32 ? 6 : 3)) stage_kernel(const __grid_constant__ KParams A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     if ((__cvta_generic_to_shared(smem_raw) & 127u) != 0) {   // TMA needs an aligned box
         if (threadIdx.x == 0) atomicOr(A.flag, 2u);
         return;
     }
-    TileSmem<P>& S = *reinterpret_cast<TileSmem<P>*>(smem_raw);
-    process_tile<P, FLUX, MODE>(A, blockIdx.x * TX, DIM == 2 ? blockIdx.y * TY : 0, S);
+    TileSmem<P, LS, TYS>& S = *reinterpret_cast<TileSmem<P, LS, TYS>*>(smem_raw);
+    process_tile<P, FLUX, MODE, LS, TYS>(A, blockIdx.x * TX, DIM == 2 ? blockIdx.y * (TYS * LS) : 0, S);
 }
 
 static KParams make_params(const StageArgs& s)
@@ -804,11 +983,11 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     A.cn = (Real)(r == 0 ? 0.0 : (r == 1 ? 0.75 : 1.0 / 3.0));
     A.ck = (Real)(r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0));
     A.cl = (Real)(r == 0 ? dt : (r == 1 ? 0.25 * dt : 2.0 / 3.0 * dt));
-    TileSmem<P>& S = *reinterpret_cast<TileSmem<P>*>(smem);
+    TileSmem<P, 1, TY>& S = *reinterpret_cast<TileSmem<P, 1, TY>*>(smem);
     for (int t = tile0; t < tile0 + ntile; ++t) {
         const int tx0 = (t % I.ntx) * TX;
         const int ty0 = DIM == 2 ? (t / I.ntx) * TY : 0;
-        process_tile<P, FLUX, 0>(A, tx0, ty0, S);
+        process_tile<P, FLUX, 0, 1, TY>(A, tx0, ty0, S);
         __syncthreads();
     }
 }
@@ -824,7 +1003,8 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 // so every item an item waits for was dequeued earlier by a resident CTA (the launch is
 // cooperative, hence all CTAs are resident) and no wait can deadlock; each wait is
 // still bounded, and a wait that gives up stops the whole launch through B.abort.
-constexpr size_t kTileSmemMax = sizeof(TileSmem<3>) > sizeof(TileSmem<2>) ? sizeof(TileSmem<3>) : sizeof(TileSmem<2>);
+constexpr size_t kTileSmemMax =
+    sizeof(TileSmem<3, 1, TY>) > sizeof(TileSmem<2, 1, TY>) ? sizeof(TileSmem<3, 1, TY>) : sizeof(TileSmem<2, 1, TY>);
 constexpr size_t kBatchSmem = (kTileSmemMax + 127) / 128 * 128 + 128;   // tile + scheduler words
 
 __global__ void __launch_bounds__(NT, kF32 ? 6 : 3) batch_kernel(const BatchArgs B)
@@ -954,22 +1134,24 @@ template <int P, int FLUX>
 static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
 {
     const KParams a = make_params(s);
-    dim3 grid((s.nx + TX - 1) / TX, DIM == 2 ? (s.ny + TY - 1) / TY : 1);
+    constexpr int TYC = TYS * LS;
+    dim3 grid((s.nx + TX - 1) / TX, DIM == 2 ? (s.ny + TYC - 1) / TYC : 1);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    const size_t smem = sizeof(TileSmem<P>);
-    if (smem > 48 * 1024) {
-        // opt in once per instantiation to more than 48 KB of dynamic shared memory
-        static bool opted[2] = {false, false};
-        if (!opted[mode]) {
-            cudaError_t e = mode == 0
-                ? cudaFuncSetAttribute(stage_kernel<P, FLUX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                : cudaFuncSetAttribute(stage_kernel<P, FLUX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            opted[mode] = true;
-        }
+    const size_t smem = sizeof(TileSmem<P, LS, TYS>);
+    // once per instantiation: opt in to more than 48 KB of dynamic shared memory where
+    // needed, and prefer the largest shared-memory carveout (several tiles per SM)
+    static bool opted[2] = {false, false};
+    if (!opted[mode]) {
+        const void* fn = mode == 0 ? (const void*)stage_kernel<P, FLUX, 0> : (const void*)stage_kernel<P, FLUX, 1>;
+        cudaError_t e = cudaSuccess;
+        if (smem > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        opted[mode] = true;
     }
-    if (mode == 0) stage_kernel<P, FLUX, 0><<<grid, NT, smem, st>>>(a);
-    else stage_kernel<P, FLUX, 1><<<grid, NT, smem, st>>>(a);
+    if (mode == 0) stage_kernel<P, FLUX, 0><<<grid, NTS, smem, st>>>(a);
+    else stage_kernel<P, FLUX, 1><<<grid, NTS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
