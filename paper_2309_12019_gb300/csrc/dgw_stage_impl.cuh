@@ -140,6 +140,11 @@ __device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sinco
 __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 
+// a / b for the sensor weights: the hardware reciprocal in float (at most 2 ulp; the
+// divisors here lie in [1e-12, 1e30]), the correctly rounded quotient in double.
+__device__ __forceinline__ float div_w(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_w(double a, double b) { return a / b; }
+
 constexpr double kPi = 3.14159265358979323846;
 
 // Flux F(u) at (x, y) and |F'(u)|_2 (1D: only the x component).
@@ -257,12 +262,15 @@ __device__ __forceinline__ Real llf(const KParams& A, int axis, Real uL, Real uR
     }
 }
 
-// v^T G v over modes >= 1; G vanishes unless both Legendre degree pairs have even sums.
+// v^T G v over modes >= 1; G vanishes unless both Legendre degree pairs have even sums,
+// so it splits into the four parity classes of (i, j), summed in independent chains.
 template <int P, class V>
 __device__ __forceinline__ V qform(const Tab<P>& T, const V* v)
 {
     constexpr int N1 = P + 1, K = Tab<P>::K;
-    V s = vbc<V>(0);
+    V s[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = vbc<V>(0);
 #pragma unroll
     for (int a = 1; a < K; ++a) {
         V t = vbc<V>(0);
@@ -271,9 +279,10 @@ __device__ __forceinline__ V qform(const Tab<P>& T, const V* v)
             const int ia = a % N1, ja = a / N1, ib = b % N1, jb = b / N1;
             if (((ia + ib) & 1) == 0 && ((ja + jb) & 1) == 0) t = vfma(T.Gu[a][b], v[b], t);
         }
-        s = vfma(v[a], t, s);
+        const int cls = ((a % N1) & 1) + 2 * ((a / N1) & 1);
+        s[cls] = vfma(v[a], t, s[cls]);
     }
-    return s;
+    return vadd(vadd(s[0], s[1]), vadd(s[2], s[3]));
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(float* a, float v)
@@ -535,7 +544,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                 has[f][l] = (f < 2) ? (wrap_x(A, nx_) >= 0) : (wrap_y(A, ny_) >= 0);
                 me += has[f][l] ? 1 : 0;
             }
-            lane(wsum, l) = (Real(1) - Real(me) * A.w_nbr) / (lane(d0, l) * lane(d0, l));
+            lane(wsum, l) = div_w(Real(1) - Real(me) * A.w_nbr, lane(d0, l) * lane(d0, l));
         }
         V dacc[K];
 #pragma unroll
@@ -573,7 +582,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
             V wl;
 #pragma unroll
             for (int l = 0; l < L; ++l)
-                lane(wl, l) = has[f][l] ? A.w_nbr / (lane(dl, l) * lane(dl, l)) : Real(0);
+                lane(wl, l) = has[f][l] ? div_w(A.w_nbr, lane(dl, l) * lane(dl, l)) : Real(0);
             wsum = vadd(wsum, wl);
 #pragma unroll
             for (int k = 1; k < K; ++k) dacc[k] = vfma(wl, vsub(c[k], cl[k]), dacc[k]);
@@ -581,7 +590,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         // U - U* = sum_l w_l (c - c_l)
         V inv;
 #pragma unroll
-        for (int l = 0; l < L; ++l) lane(inv, l) = Real(1) / lane(wsum, l);
+        for (int l = 0; l < L; ++l) lane(inv, l) = div_w(Real(1), lane(wsum, l));
 #pragma unroll
         for (int k = 1; k < K; ++k) dacc[k] = vmul(dacc[k], inv);
         dacc[0] = vbc<V>(0);
@@ -837,7 +846,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         const Real lamv = A.lam_fixed ? A.lambda_nu : lane(lam, l);
-        lane(ngs, l) = -(lane(gamma, l) * lamv / Real(P));
+        lane(ngs, l) = -(lane(gamma, l) * lamv * Real(1.0 / P));
         any_gamma = any_gamma || lane(gamma, l) != Real(0);
     }
     V chk = vbc<V>(0);         // becomes NaN if any output is not finite
