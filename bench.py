@@ -71,7 +71,58 @@ def dt_of(w):
 # 1024^2 Q3 KPP workload, averaged over the three stages of one step, from one ncu
 # capture (profiles/stage_kernel_kpp_1024x1024_q3.md).  Reset to None whenever the
 # stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = None
+STAGE_TRAFFIC_BYTES = 138.4e6
+
+# FP32 peak of one GB300 from its unit counts and maximum clock: 152 SMs x 128 FP32
+# lanes x 2 flops per FMA x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def qform_flops(p, dim):
+    """Flops of one seminorm quadratic form v^T G v over the parity-class blocks of G."""
+    n1 = p + 1
+    k = n1 ** dim
+    pairs = sum(1 for a in range(1, k) for b in range(a, k)
+                if (a % n1 + b % n1) % 2 == 0 and (a // n1 + b // n1) % 2 == 0)
+    return 2 * pairs + 2 * (k - 1) + 3
+
+
+def stage_flops_per_cell(dim, p, flux, stab):
+    """Algorithmic FP32 flops of one stage per cell, following the stage kernel's
+    sum-factorised operators (an FMA counts 2, any other arithmetic operation 1), and the
+    number of sin/cos pairs (KPP flux).  Faces: dim owned faces per cell."""
+    n1, nq = p + 1, p + 2
+    k = n1 ** dim
+    kpp = flux == "kpp"
+    red = 6                                        # 2 pi reduction of one sin/cos argument
+    f = 0
+    if stab == "weno":                             # Hermite candidates, indicators, blend
+        qf = qform_flops(p, dim)
+        for axis in range(dim):
+            shift = sum(2 * (n1 - ((c % n1) if axis == 0 else (c // n1))) for c in range(1, k))
+            f += 2 * (shift + qf + 4 + 3 * (k - 1))
+        f += 2 * qf + 2 + 3 + 1 + (k - 1) + 3
+    if dim == 2:                                   # volume: interpolation, flux, projection
+        f += 2 * n1 * nq * n1 + 2 * nq * nq * n1 + nq * nq * 4 * n1 + 4 * k * nq
+        npts = nq * nq
+    else:
+        npts = nq
+        f += nq * 4 * n1
+    f += npts * (red if kpp else 2)
+    nfq = nq if dim == 2 else 1                    # faces: traces at the points, LLF, lift
+    llf = 2 * red + 14 if kpp else 6
+    f += dim * nfq * ((4 * n1 if dim == 2 else 0) + llf + (2 * n1 if dim == 2 else n1))
+    f += 2 * dim * k                               # face traces
+    f += 4 * n1 + 2 * k if dim == 2 else 2 + 2 * n1   # face contributions
+    if stab != "dg":                               # gamma nu K c
+        for c in range(k):
+            i, j = c % n1, c // n1
+            s1 = sum(1 for m in range(1, n1) if (i + m) % 2 == 0 and i > 0)
+            s2 = sum(1 for m in range(1, n1) if (j + m) % 2 == 0 and j > 0) if dim == 2 else 0
+            f += 2 * (s1 + s2) + 5
+    f += 6 * k                                     # M^-1 and the RK combination
+    sincos = (npts + dim * nfq * 2) if kpp else 0
+    return f, sincos
 
 
 def peaks():
@@ -388,17 +439,23 @@ def main():
     if rank != 0:
         return
     hbm, src = peaks()
-    per_launch_s = t / (3 * args.steps)
+    per_launch_s = t / (3 * args.steps)     # only stage kernels run in the timed region
     alg_bytes = 8.0 / 3.0 * N * 4          # per stage: 8 state-array passes per step / 3 stages
     achieved = alg_bytes / per_launch_s / 1e9
+    cells = w["nx"] * w["ny"]
+    fpc, sincos = stage_flops_per_cell(w["dim"], w["p"], w["flux"], w["stab"])
+    tflops = fpc * cells / per_launch_s / 1e12
     line = {"metric": metric, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP32_PEAK_TFLOPS,
                          "traffic": STAGE_TRAFFIC_BYTES if args.workload == "kpp_1024x1024_q3" else None,
-                         "peak_source": src,
-                         "kernel": "stage_kernel (3 launches per step)"},
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                         "flops_per_cell": fpc, "sincos_per_cell": sincos,
+                         "kernel": "stage_kernel (3 launches per step)",
+                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                 "peak_source": src, "bytes_per_launch": alg_bytes}},
             "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": r32.get("bytes"),
                     "d2h_bytes_per_step": r32.get("bytes")} if "t_e2e" in r32 else None,
             "gpu_launches": r32["launches"], "clocks": r32["clocks"], "mass_after": r32["mass"]}
