@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include "dgw_internal.h"
 #include "dgw_math.cuh"
@@ -696,15 +697,17 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     }
 
     // ---- 2. faces: each face of the tile once, from the traces ----
-    for (int f = tid; f < NFX + NFY; f += NT) {
-        const bool xf = f < NFX;
+    // item f of the x-faces (xf true) or of the y-faces; XF is a compile-time or a
+    // run-time flag
+    auto face_item = [&](auto XF, const int f) {
+        const bool xf = XF;
         int flx[L], fly[L];        // tile position of the cell on the plus side of lane l's face
         if (xf) {
             const int p = f / (TX + 1), col = f - p * (TX + 1);
 #pragma unroll
             for (int l = 0; l < L; ++l) { flx[l] = col; fly[l] = L * p + l; }
         } else {
-            const int g = f - NFX, row = g / TXL, col = g - row * TXL;
+            const int row = f / TXL, col = f - row * TXL;
 #pragma unroll
             for (int l = 0; l < L; ++l) { flx[l] = col + l * TXL; fly[l] = row; }
         }
@@ -716,7 +719,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
             valid[l] = xf ? (fgx <= A.nx && fgy < A.ny) : (fgy <= A.ny && fgx < A.nx);
             anyv = anyv || valid[l];
         }
-        if (!anyv) continue;
+        if (!anyv) return;
         const int axis = xf ? 0 : 1;
         // the lanes of an item share the face column (x-faces) or row (y-faces), hence
         // the boundary situation
@@ -804,6 +807,16 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                     atomic_max_nonneg(&lam_s[fly[l]][flx[l]], lane(lp, l));
             }
         }
+    };
+    if constexpr (FLUX == FLUX_KPP) {
+        // one body for both orientations: two copies of the sin/cos-heavy flux cost more
+        // in instruction fetch than the orientation selects cost in issue
+        for (int f = tid; f < NFX + NFY; f += NT) face_item(f < NFX, f < NFX ? f : f - NFX);
+    } else {
+        for (int f = tid; f < NFX; f += NT) face_item(std::integral_constant<bool, true>(), f);
+        // the y-faces continue the x-faces' numbering across the threads, so no thread
+        // takes more than one item above the even share
+        for (int f = (tid + NT - NFX % NT) % NT; f < NFY; f += NT) face_item(std::integral_constant<bool, false>(), f);
     }
     __syncthreads();
     if (!any_in) return;

@@ -120,6 +120,31 @@ def test_residual_fp32_random(oracle_mod, dim, p, flux, stab):
     assert H.rel_l2(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("p,flux,stab,bc,ny", [(3, "kpp", "weno", "outflow", 21), (2, "rotation", "weno", "inflow_zero", 17),
+                                               (1, "advect", "weno", "periodic", 19), (3, "burgers", "lo", "periodic", 33)])
+def test_residual_fp32_tma_ragged_rows(oracle_mod, p, flux, stab, bc, ny):
+    """FP32 2D residual on meshes whose width takes the TMA box path (36 cells: 16-byte
+    rows) and whose odd row count leaves the second cell of the last thread row outside
+    the mesh (two cells per thread in float)."""
+    s = H.spec(2, p, 36, ny=ny, flux=flux, stab=stab, bc=bc)
+    U = H.state_for(s, seed=550 + p).astype(np.float32).astype(np.float64)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    got = gpu_residual(gpu(s, "fp32"), U)
+    assert H.rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("nx,ny,p,bc", [(36, 21, 3, "outflow"), (19, 13, 2, "periodic"), (32, 16, 1, "inflow_zero")])
+def test_sensor_fp32(oracle_mod, nx, ny, p, bc):
+    """Sensor-only launch in float, lane by lane: gamma within 1e-4 of the FP64 oracle on
+    the float-representable state."""
+    s = H.spec(2, p, nx, ny=ny, bc=bc)
+    U = H.state_for(s, seed=580 + p).astype(np.float32).astype(np.float64)
+    g_ref, _, _ = oracle_mod.sensor(oracle_mod.Problem(**s), U)
+    g = gpu_sensor(gpu(s, "fp32"), U)
+    assert np.max(np.abs(g - g_ref)) <= 1e-4
+    assert 0.05 < np.mean(g > 1e-3)
+
+
 @pytest.mark.parametrize("dim,p,flux", [(1, 3, "advect"), (2, 2, "advect"), (2, 3, "burgers")])
 def test_rk3_fp32_smooth(oracle_mod, dim, p, flux):
     """FP32 SSP-RK3 on smooth projected data: relative L2 <= 2e-5 after 20 steps."""
