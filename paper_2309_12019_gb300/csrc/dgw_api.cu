@@ -48,6 +48,8 @@ static dgw_status fail(dgw_status s, const char* fmt, ...)
     } while (0)
 
 using GraphKey = std::tuple<void*, double, int, cudaStream_t>;
+// (U_in, U_out, dt, stream, copy flags) of a pipelined host step
+using BandKey = std::tuple<const void*, void*, double, cudaStream_t, int>;
 
 struct dgw_ctx {
     int device = 0;
@@ -72,7 +74,15 @@ struct dgw_ctx {
     void* adj_b1 = nullptr;      // adjoint: lambda of stage 2
     void* adj_b2 = nullptr;      // adjoint: lambda of stage 1
     std::map<std::pair<const void*, int>, bool> no_tmap;
+    // dgw_rk_step_host pipeline: streams for input copies, the three stages and output
+    // copies, one event per (stream, band), and the join events
+    cudaStream_t band_st[5] = {};
+    cudaEvent_t band_ev[5][16] = {};
+    cudaEvent_t band_join[2] = {};
+    std::map<BandKey, cudaGraphExec_t> band_graphs;   // null: replay not possible (direct launches)
 };
+
+static const int kBands = 16;
 
 static const int kMassBlocks = 1024;
 static const int kMassThreads = 256;
@@ -175,6 +185,9 @@ static void drop_graphs(dgw_ctx* c)
 {
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
+    for (auto& kv : c->band_graphs)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    c->band_graphs.clear();
 }
 
 extern "C" dgw_status dgw_destroy(dgw_ctx* c)
@@ -191,6 +204,13 @@ extern "C" dgw_status dgw_destroy(dgw_ctx* c)
     cudaFree(c->adj_b2);
     cudaFree(c->partial);
     cudaFree(c->flag);
+    for (int i = 0; i < 5; ++i) {
+        if (c->band_st[i]) cudaStreamDestroy(c->band_st[i]);
+        for (int b = 0; b < kBands; ++b)
+            if (c->band_ev[i][b]) cudaEventDestroy(c->band_ev[i][b]);
+    }
+    for (int i = 0; i < 2; ++i)
+        if (c->band_join[i]) cudaEventDestroy(c->band_join[i]);
     delete c;
     return DGW_OK;
 }
@@ -426,22 +446,152 @@ extern "C" dgw_status dgw_rk_step(dgw_ctx* c, void* U, double dt, int nsteps, vo
     return DGW_OK;
 }
 
+// One SSP-RK3 step of a 2D mesh that is not periodic in y, as a wavefront over bands of
+// tile rows: stage r of band b reads stage r - 1 on bands b - 1 .. b + 1 only, so the input
+// copy of a band, the three stages and the output copy of a finished band overlap.  Five
+// streams (input copies, stages 1-3, output copies) ordered by one event per (stream,
+// band), joined to the caller's stream s at both ends.  copy_in: U_in (host) is copied to
+// c->Uhost_dev band by band first; copy_out: the result is copied to U_out band by band.
+// Stage 3 writes U in place; every band that still reads the old U at a halo row (stage 1
+// of the band above) finished before the band's stage 3, which waits for stage 2 of the
+// band above, which waited for stage 1 two bands above.
+static dgw_status banded_step(dgw_ctx* c, const void* U_in, void* U_out, double dt, bool copy_in,
+                              bool copy_out, cudaStream_t s)
+{
+    const int rows = stage_rows(c->eb == 8);
+    const int trows = (c->mesh.ny + rows - 1) / rows;
+    const int nb = trows < kBands ? trows : kBands;
+    cudaStream_t* st = c->band_st;
+    auto& ev = c->band_ev;
+    DGW_CUDA(cudaEventRecord(c->band_join[0], s));
+    for (int i = 0; i < 5; ++i) DGW_CUDA(cudaStreamWaitEvent(st[i], c->band_join[0], 0));
+
+    int t0[kBands + 1];                 // band b: tile rows [t0[b], t0[b + 1])
+    for (int b = 0; b <= nb; ++b) t0[b] = (int)((int64_t)trows * b / nb);
+    const size_t eb = (size_t)c->eb, nx = (size_t)c->mesh.nx, pitch = (size_t)c->E * eb;
+    auto row_span = [&](int b, size_t* off, size_t* width) {
+        const int r0 = t0[b] * rows;
+        const int r1 = t0[b + 1] * rows < c->mesh.ny ? t0[b + 1] * rows : c->mesh.ny;
+        *off = (size_t)r0 * nx * eb;
+        *width = (size_t)(r1 - r0) * nx * eb;
+    };
+    char* U = static_cast<char*>(c->Uhost_dev);
+    if (copy_in)
+        for (int b = 0; b < nb; ++b) {
+            size_t off, width;
+            row_span(b, &off, &width);
+            DGW_CUDA(cudaMemcpy2DAsync(U + off, pitch, static_cast<const char*>(U_in) + off, pitch, width,
+                                       (size_t)c->K, cudaMemcpyHostToDevice, st[0]));
+            DGW_CUDA(cudaEventRecord(ev[0][b], st[0]));
+        }
+    StageArgs a = base_args(c);
+    for (int r = 0; r < 3; ++r) {
+        if (r == 0) { a.Uk = U; a.Un = nullptr; a.Uout = c->S1; a.cn = 0.0; a.ck = 1.0; a.cl = dt; }
+        if (r == 1) { a.Uk = c->S1; a.Un = U; a.Uout = c->S2; a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt; }
+        if (r == 2) { a.Uk = c->S2; a.Un = U; a.Uout = U; a.cn = 1.0 / 3.0; a.ck = 2.0 / 3.0; a.cl = 2.0 / 3.0 * dt; }
+        for (int b = 0; b < nb; ++b) {
+            const int dep = b + 1 < nb ? b + 1 : nb - 1;     // highest band read (halo row)
+            if (r > 0 || copy_in) DGW_CUDA(cudaStreamWaitEvent(st[1 + r], ev[r][dep], 0));
+            a.tile_row0 = t0[b];
+            a.tile_rows = t0[b + 1] - t0[b];
+            DGW_CUDA(launch(c, a, 0, st[1 + r]));
+            DGW_CUDA(cudaEventRecord(ev[1 + r][b], st[1 + r]));
+        }
+    }
+    if (copy_out) {
+        for (int b = 0; b < nb; ++b) {
+            size_t off, width;
+            row_span(b, &off, &width);
+            DGW_CUDA(cudaStreamWaitEvent(st[4], ev[3][b], 0));
+            DGW_CUDA(cudaMemcpy2DAsync(static_cast<char*>(U_out) + off, pitch, U + off, pitch, width,
+                                       (size_t)c->K, cudaMemcpyDeviceToHost, st[4]));
+        }
+        DGW_CUDA(cudaEventRecord(c->band_join[1], st[4]));
+    } else {
+        DGW_CUDA(cudaEventRecord(c->band_join[1], st[3]));
+    }
+    // the last output copy (or the last stage-3 band) comes after every other operation
+    DGW_CUDA(cudaStreamWaitEvent(s, c->band_join[1], 0));
+    return DGW_OK;
+}
+
+static dgw_status band_resources(dgw_ctx* c)
+{
+    for (int i = 0; i < 5; ++i) {
+        if (!c->band_st[i]) DGW_CUDA(cudaStreamCreateWithFlags(&c->band_st[i], cudaStreamNonBlocking));
+        for (int b = 0; b < kBands; ++b)
+            if (!c->band_ev[i][b]) DGW_CUDA(cudaEventCreateWithFlags(&c->band_ev[i][b], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < 2; ++i)
+        if (!c->band_join[i]) DGW_CUDA(cudaEventCreateWithFlags(&c->band_join[i], cudaEventDisableTiming));
+    return DGW_OK;
+}
+
+// banded_step, replayed from a graph cached per (U_in, U_out, dt, stream, copies) when the
+// stream can be captured; launched directly otherwise (the legacy stream, a stream that is
+// itself being captured, or host memory that a graph cannot copy from).
+static dgw_status banded(dgw_ctx* c, const void* U_in, void* U_out, double dt, bool copy_in, bool copy_out,
+                         cudaStream_t s)
+{
+    dgw_status st = band_resources(c);
+    if (st != DGW_OK) return st;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (s != nullptr) DGW_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (s == nullptr || cap != cudaStreamCaptureStatusNone) return banded_step(c, U_in, U_out, dt, copy_in, copy_out, s);
+    const BandKey key{U_in, U_out, dt, s, (copy_in ? 1 : 0) | (copy_out ? 2 : 0)};
+    auto it = c->band_graphs.find(key);
+    if (it == c->band_graphs.end()) {
+        if (c->band_graphs.size() >= 8) {
+            for (auto& kv : c->band_graphs)
+                if (kv.second) cudaGraphExecDestroy(kv.second);
+            c->band_graphs.clear();
+        }
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const dgw_status sc = banded_step(c, U_in, U_out, dt, copy_in, copy_out, s);
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (sc == DGW_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();    // a refused capture leaves no error behind for later calls
+        it = c->band_graphs.emplace(key, exec).first;
+    }
+    if (!it->second) return banded_step(c, U_in, U_out, dt, copy_in, copy_out, s);
+    DGW_CUDA(cudaGraphLaunch(it->second, s));
+    return DGW_OK;
+}
+
 extern "C" dgw_status dgw_rk_step_host(dgw_ctx* c, const void* U_in, void* U_out, double dt,
                                        int nsteps, void* stream)
 {
     dgw_status st = check_ctx(c);
     if (st != DGW_OK) return st;
     if (!U_in || !U_out) return fail(DGW_EINVAL, "NULL host array");
+    if (nsteps < 1) return fail(DGW_EINVAL, "nsteps < 1");
+    if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
     const size_t bytes = (size_t)c->K * c->E * c->eb;
     if (!c->Uhost_dev) {
         cudaError_t e = cudaMalloc(&c->Uhost_dev, bytes);
         if (e != cudaSuccess) return fail(DGW_ENOMEM, "dgw_rk_step_host: %s", cudaGetErrorString(e));
     }
     cudaStream_t s = (cudaStream_t)stream;
-    DGW_CUDA(cudaMemcpyAsync(c->Uhost_dev, U_in, bytes, cudaMemcpyHostToDevice, s));
-    st = dgw_rk_step(c, c->Uhost_dev, dt, nsteps, stream);
-    if (st != DGW_OK) return st;
-    DGW_CUDA(cudaMemcpyAsync(U_out, c->Uhost_dev, bytes, cudaMemcpyDeviceToHost, s));
+    const int rows = stage_rows(c->eb == 8);
+    const bool pipelined = c->mesh.dim == 2 && c->mesh.bc[2] != DGW_BC_PERIODIC && c->mesh.ny >= 2 * rows;
+    if (!pipelined) {
+        DGW_CUDA(cudaMemcpyAsync(c->Uhost_dev, U_in, bytes, cudaMemcpyHostToDevice, s));
+        st = dgw_rk_step(c, c->Uhost_dev, dt, nsteps, stream);
+        if (st != DGW_OK) return st;
+        DGW_CUDA(cudaMemcpyAsync(U_out, c->Uhost_dev, bytes, cudaMemcpyDeviceToHost, s));
+    } else if (nsteps == 1) {
+        st = banded(c, U_in, U_out, dt, true, true, s);
+        if (st != DGW_OK) return st;
+    } else {
+        st = banded(c, U_in, nullptr, dt, true, false, s);
+        if (st == DGW_OK && nsteps > 2) st = dgw_rk_step(c, c->Uhost_dev, dt, nsteps - 2, stream);
+        if (st == DGW_OK) st = banded(c, nullptr, U_out, dt, false, true, s);
+        if (st != DGW_OK) return st;
+    }
     DGW_CUDA(cudaStreamSynchronize(s));
     return DGW_OK;
 }

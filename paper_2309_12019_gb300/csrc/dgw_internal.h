@@ -68,6 +68,8 @@ struct StageArgs {
     unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x (stage_rows + 2) x K), or null
     const CUtensorMap* tmap_un;  // 2D: TMA descriptor of Un (box kTileX2 x stage_rows x K), or null
+    int tile_row0;         // 2D: first tile row of the launch
+    int tile_rows;         // 2D: tile rows of the launch (0: through the last row of the mesh)
 };
 
 // ------------------------------------------------------------------------------------

@@ -112,6 +112,7 @@ struct alignas(64) KParams {
     int use_tma;
     int use_tma_un;
     int cg_loads;        // load Uk / Un through L2 only (data written earlier in the same launch)
+    int tile_row0;       // first tile row of a stage launch over a band of rows
     const Real* Uk;
     const Real* Un;
     Real* Uout;
@@ -926,7 +927,7 @@ __global__ void __launch_bounds__(NTS, LS == 2 ? 512 / NTS : (kF32 ? 6 : 3)) sta
         return;
     }
     TileSmem<P, LS, TYS>& S = *reinterpret_cast<TileSmem<P, LS, TYS>*>(smem_raw);
-    process_tile<P, FLUX, MODE, LS, TYS>(A, blockIdx.x * TX, DIM == 2 ? blockIdx.y * (TYS * LS) : 0, S);
+    process_tile<P, FLUX, MODE, LS, TYS>(A, blockIdx.x * TX, DIM == 2 ? (blockIdx.y + A.tile_row0) * (TYS * LS) : 0, S);
 }
 
 static KParams make_params(const StageArgs& s)
@@ -936,6 +937,7 @@ static KParams make_params(const StageArgs& s)
     a.use_tma = 0;
     a.use_tma_un = 0;
     a.cg_loads = 0;
+    a.tile_row0 = DIM == 2 ? s.tile_row0 : 0;
     if (s.tmap) {
         a.tmap = *s.tmap;
         a.use_tma = 1;
@@ -978,6 +980,7 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     A.use_tma = 0;
     A.use_tma_un = 0;
     A.cg_loads = 1;
+    A.tile_row0 = 0;
     const Real* U = static_cast<const Real*>(B.U) + I.off;
     const Real* S1 = static_cast<const Real*>(B.S1) + I.off;
     const Real* S2 = static_cast<const Real*>(B.S2) + I.off;
@@ -1157,7 +1160,10 @@ static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
 {
     const KParams a = make_params(s);
     constexpr int TYC = TYS * LS;
-    dim3 grid((s.nx + TX - 1) / TX, DIM == 2 ? (s.ny + TYC - 1) / TYC : 1);
+    const int trows = (s.ny + TYC - 1) / TYC;
+    if (DIM == 2 && (s.tile_row0 < 0 || s.tile_rows < 0 || s.tile_row0 + s.tile_rows > trows)) return cudaErrorInvalidValue;
+    const int grows = DIM == 2 ? (s.tile_rows > 0 ? s.tile_rows : trows - s.tile_row0) : 1;
+    dim3 grid((s.nx + TX - 1) / TX, grows);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     const size_t smem = sizeof(TileSmem<P, LS, TYS>);
     // once per instantiation: opt in to more than 48 KB of dynamic shared memory where

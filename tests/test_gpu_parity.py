@@ -263,6 +263,29 @@ def test_host_entry_matches_device_entry():
     assert np.array_equal(out.numpy(), Ud.cpu().numpy())
 
 
+@pytest.mark.parametrize("prec,nx,ny,flux,bc,nsteps,alias", [
+    ("fp32", 40, 70, "kpp", "outflow", 1, False),        # 5 bands, the last one 6 rows
+    ("fp32", 64, 128, "advect", "inflow_zero", 2, True),  # 8 bands; first and last step banded
+    ("fp64", 36, 72, "burgers", "outflow", 1, False),     # 18 tile rows in 8 uneven bands
+    ("fp64", 20, 20, "advect", "periodic", 3, True),      # periodic in y: whole-array copies
+])
+def test_host_entry_pipelined_matches_device_entry(prec, nx, ny, flux, bc, nsteps, alias):
+    """The host-buffer entry point (input copy, stages and output copy pipelined over
+    bands of rows) gives the device entry point's result bit for bit, also with the
+    output written over the input buffer."""
+    s = H.spec(2, 3 if flux == "kpp" else 2, nx, ny=ny, flux=flux, bc=bc)
+    U = H.state_for(s, seed=7).astype(np.float32 if prec == "fp32" else np.float64)
+    ctx = gpu(s, prec)
+    dt = 0.01 / max(nx, ny)
+    Ud = to_dev(U, prec)
+    ctx.rk_step(Ud, dt, nsteps)
+    Uh = torch.tensor(U).pin_memory()
+    out = Uh if alias else torch.empty_like(Uh).pin_memory()
+    ctx.rk_step_host(Uh, out, dt, nsteps)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), Ud.cpu().numpy())
+
+
 def test_nonfinite_detected():
     """An absurd time step overflows the update; the stage kernel flags it and
     dgw_sync_status reports DGW_ENONFINITE (then clears the flag)."""
