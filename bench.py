@@ -340,7 +340,7 @@ def run_adjoint(local, n=512, steps=200, every=20):
     fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     out = {"workload": f"adjoint_burgers_{n}x{n}_q2", "dtype": "f32", "steps": steps, "checkpoint_every": every,
            "dofs": 9 * n * n, "forward_ms_per_step": fwd / steps, "backward_ms_per_step": bwd / steps,
-           "backward_over_forward": bwd / fwd, "misfit": float(J),
+           "backward_over_forward": bwd / fwd, "misfit": float(J.detach()),
            "grad_finite": bool(torch.isfinite(U0g.grad).all().item())}
     c.close()
     return out
@@ -393,6 +393,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ensemble and the smaller configurations")
+    ap.add_argument("--only", choices=["ensemble", "adjoint"],
+                    help="run one secondary leg alone (--steps steps) and print its line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world, rank, local = dist_setup(args)
@@ -416,6 +418,15 @@ def main():
                                  "sample": sample},
                 "e2e": {"value": v, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+
+    if args.only:
+        if rank == 0:
+            if args.only == "ensemble":
+                leg = run_ensemble(args.steps, args.warmup, local)
+            else:
+                leg = run_adjoint(local, steps=args.steps, every=min(20, args.steps))
+            print(json.dumps(dict(leg, leg=args.only)))
         return
 
     r32 = run_gpu(w, "fp32", args.steps, args.warmup, world, local, measure_e2e=not args.no_e2e)
