@@ -679,43 +679,46 @@ struct dgw_batch {
     std::vector<int> dims;
     int64_t total = 0;
     BatchInst* d_inst = nullptr;
-    BatchItem* d_items[2] = {nullptr, nullptr};
-    int nitems[2] = {0, 0};
+    BatchItem* d_items[2][kMaxP + 1] = {};     // per (dimension, degree)
+    int nitems[2][kMaxP + 1] = {};
     void* S1 = nullptr;
     void* S2 = nullptr;
-    unsigned long long* counters = nullptr;   // queue[2] then done[n]
+    unsigned long long* counters = nullptr;   // queue[kQueues], one per (dimension, degree), then done[n]
     unsigned* flag = nullptr;
     int* abort = nullptr;
-    int grid[2] = {0, 0};
+    int grid[2][kMaxP + 1] = {};
     int chunk = 4;
-    int blocks_per_sm[2] = {0, 0};
+    int blocks_per_sm[2][kMaxP + 1] = {};
     int sms = 0;
     long long wait_limit = 1ll << 24;
     int unreachable = 0;
 };
 
+static const int kQueues = 2 * (kMaxP + 1);
+
 static dgw_status batch_build_items(dgw_batch* b)
 {
-    for (int d = 0; d < 2; ++d) {
-        std::vector<int> order;
-        for (int i = 0; i < b->n; ++i)
-            if (b->dims[i] == d + 1) order.push_back(i);
-        // longest instances first, so the tail of each stage is made of small items
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int x, int y) { return b->inst[x].ntiles > b->inst[y].ntiles; });
-        std::vector<BatchItem> items;
-        for (int i : order)
-            for (int t = 0; t < b->inst[i].ntiles; t += b->chunk)
-                items.push_back(BatchItem{i, t, std::min(b->chunk, b->inst[i].ntiles - t), 0});
-        cudaFree(b->d_items[d]);
-        b->d_items[d] = nullptr;
-        b->nitems[d] = (int)items.size();
-        if (!items.empty()) {
-            DGW_CUDA(cudaMalloc(&b->d_items[d], sizeof(BatchItem) * items.size()));
-            DGW_CUDA(cudaMemcpy(b->d_items[d], items.data(), sizeof(BatchItem) * items.size(),
-                                cudaMemcpyHostToDevice));
+    for (int d = 0; d < 2; ++d)
+        for (int p = 1; p <= kMaxP; ++p) {
+            std::vector<int> order;
+            for (int i = 0; i < b->n; ++i)
+                if (b->dims[i] == d + 1 && b->inst[i].p == p) order.push_back(i);
+            // longest instances first, so the tail of each stage is made of small items
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int x, int y) { return b->inst[x].ntiles > b->inst[y].ntiles; });
+            std::vector<BatchItem> items;
+            for (int i : order)
+                for (int t = 0; t < b->inst[i].ntiles; t += b->chunk)
+                    items.push_back(BatchItem{i, t, std::min(b->chunk, b->inst[i].ntiles - t), 0});
+            cudaFree(b->d_items[d][p]);
+            b->d_items[d][p] = nullptr;
+            b->nitems[d][p] = (int)items.size();
+            if (!items.empty()) {
+                DGW_CUDA(cudaMalloc(&b->d_items[d][p], sizeof(BatchItem) * items.size()));
+                DGW_CUDA(cudaMemcpy(b->d_items[d][p], items.data(), sizeof(BatchItem) * items.size(),
+                                    cudaMemcpyHostToDevice));
+            }
         }
-    }
     return DGW_OK;
 }
 
@@ -724,8 +727,8 @@ extern "C" dgw_status dgw_batch_destroy(dgw_batch* b)
     if (!b) return DGW_OK;
     cudaDeviceSynchronize();
     cudaFree(b->d_inst);
-    cudaFree(b->d_items[0]);
-    cudaFree(b->d_items[1]);
+    for (int d = 0; d < 2; ++d)
+        for (int p = 0; p <= kMaxP; ++p) cudaFree(b->d_items[d][p]);
     cudaFree(b->S1);
     cudaFree(b->S2);
     cudaFree(b->counters);
@@ -806,7 +809,7 @@ extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int*
     const size_t bytes = (size_t)b->total * b->eb;
     if (ce == cudaSuccess) ce = cudaMalloc(&b->S1, bytes);
     if (ce == cudaSuccess) ce = cudaMalloc(&b->S2, bytes);
-    if (ce == cudaSuccess) ce = cudaMalloc(&b->counters, sizeof(unsigned long long) * (2 + n));
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->counters, sizeof(unsigned long long) * (kQueues + n));
     if (ce == cudaSuccess) ce = cudaMalloc(&b->flag, sizeof(unsigned));
     if (ce == cudaSuccess) ce = cudaMemset(b->flag, 0, sizeof(unsigned));
     if (ce == cudaSuccess) ce = cudaMalloc(&b->abort, sizeof(int));
@@ -819,10 +822,18 @@ extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int*
         return s2;
     }
     const bool f64 = b->eb == 8;
-    b->blocks_per_sm[0] = f64 ? batch_blocks_per_sm_f64_d1() : batch_blocks_per_sm_f32_d1();
-    b->blocks_per_sm[1] = f64 ? batch_blocks_per_sm_f64_d2() : batch_blocks_per_sm_f32_d2();
-    for (int d = 0; d < 2; ++d) b->grid[d] = b->blocks_per_sm[d] * b->sms;
-    if (b->grid[0] <= 0 || b->grid[1] <= 0) {
+    bool bad = false;
+    for (int d = 0; d < 2; ++d)
+        for (int p = 1; p <= kMaxP; ++p) {
+            bool used = false;
+            for (int i = 0; i < n; ++i) used = used || (b->dims[i] == d + 1 && b->inst[i].p == p);
+            if (!used) continue;
+            b->blocks_per_sm[d][p] = d == 0 ? (f64 ? batch_blocks_per_sm_f64_d1(p) : batch_blocks_per_sm_f32_d1(p))
+                                            : (f64 ? batch_blocks_per_sm_f64_d2(p) : batch_blocks_per_sm_f32_d2(p));
+            b->grid[d][p] = b->blocks_per_sm[d][p] * b->sms;
+            bad = bad || b->grid[d][p] <= 0;
+        }
+    if (bad) {
         dgw_batch_destroy(b);
         return fail(DGW_ECUDA, "dgw_batch_create: occupancy query failed");
     }
@@ -891,35 +902,39 @@ extern "C" dgw_status dgw_batch_project(dgw_batch* b, int nq, int first, int cou
     return DGW_OK;
 }
 
+// One persistent launch per (dimension, degree) present, in turn on the stream; each
+// advances its instances through all 3 * nsteps stages.
 static dgw_status batch_enqueue(dgw_batch* b, void* U, int nsteps, cudaStream_t s)
 {
-    DGW_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (2 + b->n), s));
+    DGW_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (kQueues + b->n), s));
     DGW_CUDA(cudaMemsetAsync(b->abort, 0, sizeof(int), s));
-    for (int d = 0; d < 2; ++d) {
-        if (b->nitems[d] == 0) continue;
-        BatchArgs a;
-        std::memset(&a, 0, sizeof a);
-        a.inst = b->d_inst;
-        a.items = b->d_items[d];
-        a.nitems = b->nitems[d];
-        a.nstages = 3 * nsteps;
-        a.U = U;
-        a.S1 = b->S1;
-        a.S2 = b->S2;
-        a.queue = b->counters + d;
-        a.done = b->counters + 2;
-        a.flag = b->flag;
-        a.abort = b->abort;
-        a.stab = b->params.stab;
-        a.q = b->params.q; a.b = b->params.b; a.w_nbr = b->params.w_nbr;
-        a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s;
-        a.wait_limit = b->wait_limit;
-        a.unreachable = b->unreachable;
-        const bool f64 = b->eb == 8;
-        cudaError_t e = d == 0 ? (f64 ? launch_batch_f64_d1(a, b->grid[0], s) : launch_batch_f32_d1(a, b->grid[0], s))
-                               : (f64 ? launch_batch_f64_d2(a, b->grid[1], s) : launch_batch_f32_d2(a, b->grid[1], s));
-        if (e != cudaSuccess) return fail(DGW_ECUDA, "batch launch: %s", cudaGetErrorString(e));
-    }
+    for (int d = 0; d < 2; ++d)
+        for (int p = 1; p <= kMaxP; ++p) {
+            if (b->nitems[d][p] == 0) continue;
+            BatchArgs a;
+            std::memset(&a, 0, sizeof a);
+            a.inst = b->d_inst;
+            a.items = b->d_items[d][p];
+            a.nitems = b->nitems[d][p];
+            a.nstages = 3 * nsteps;
+            a.U = U;
+            a.S1 = b->S1;
+            a.S2 = b->S2;
+            a.queue = b->counters + d * (kMaxP + 1) + p;
+            a.done = b->counters + kQueues;
+            a.flag = b->flag;
+            a.abort = b->abort;
+            a.stab = b->params.stab;
+            a.q = b->params.q; a.b = b->params.b; a.w_nbr = b->params.w_nbr;
+            a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s;
+            a.wait_limit = b->wait_limit;
+            a.unreachable = b->unreachable;
+            const bool f64 = b->eb == 8;
+            const int g = b->grid[d][p];
+            cudaError_t e = d == 0 ? (f64 ? launch_batch_f64_d1(a, p, g, s) : launch_batch_f32_d1(a, p, g, s))
+                                   : (f64 ? launch_batch_f64_d2(a, p, g, s) : launch_batch_f32_d2(a, p, g, s));
+            if (e != cudaSuccess) return fail(DGW_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+        }
     return DGW_OK;
 }
 

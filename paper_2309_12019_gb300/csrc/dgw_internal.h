@@ -74,8 +74,8 @@ struct StageArgs {
 
 // ------------------------------------------------------------------------------------
 // Batched ensemble: many independent meshes advanced by one persistent kernel per
-// dimension.  Work item = (stage, instance, chunk of tiles); an item waits only for its
-// own instance's previous stage (per-instance counters, bounded spin).
+// dimension and degree.  Work item = (stage, instance, chunk of tiles); an item waits
+// only for its own instance's previous stage (per-instance counters, bounded spin).
 // ------------------------------------------------------------------------------------
 struct BatchInst {
     int64_t off;           // first coefficient of the instance in the packed state
@@ -128,14 +128,14 @@ cudaError_t launch_stage_f32_d2(const StageArgs& a, int p, int flux, int mode, c
 cudaError_t launch_stage_f64_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 cudaError_t launch_stage_f64_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 
-cudaError_t launch_batch_f32_d1(const BatchArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_batch_f32_d2(const BatchArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_batch_f64_d1(const BatchArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_batch_f64_d2(const BatchArgs& a, int grid, cudaStream_t s);
-int batch_blocks_per_sm_f32_d1();
-int batch_blocks_per_sm_f32_d2();
-int batch_blocks_per_sm_f64_d1();
-int batch_blocks_per_sm_f64_d2();
+cudaError_t launch_batch_f32_d1(const BatchArgs& a, int p, int grid, cudaStream_t s);
+cudaError_t launch_batch_f32_d2(const BatchArgs& a, int p, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64_d1(const BatchArgs& a, int p, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64_d2(const BatchArgs& a, int p, int grid, cudaStream_t s);
+int batch_blocks_per_sm_f32_d1(int p);
+int batch_blocks_per_sm_f32_d2(int p);
+int batch_blocks_per_sm_f64_d1(int p);
+int batch_blocks_per_sm_f64_d2(int p);
 
 cudaError_t launch_vjp_f32_d1(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);
 cudaError_t launch_vjp_f32_d2(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);

@@ -356,7 +356,10 @@ struct TileSmem {
 // MODE 1: sensor only.  Thread (lx, ly) owns the cells (lx, L ly + l), l < L; with
 // L = 2 their arithmetic runs as packed pairs (lane l = cell l).  Lanes of cells outside
 // the mesh (ragged tiles) compute on zero-filled data and store nothing.
-template <int P, int FLUX, int MODE, int L, int TYT>
+// TMA: the TMA staging paths are compiled in (the batch kernel builds its launch scalars
+// per work item in registers and never stages by TMA; taking the tensor map's address
+// would put those scalars in local memory).
+template <int P, int FLUX, int MODE, int L, int TYT, bool TMA = true>
 __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P, L, TYT>& S)
 {
     static_assert(L == 1 || (kF32 && DIM == 2), "two cells per thread: float, 2D only");
@@ -385,7 +388,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     const bool periodic_y = DIM == 2 && A.bc[2] == BC_PERIODIC;
 
     // ---- 0. stage the tile and its face halo ----
-    if (DIM == 2 && A.use_tma) {
+    if (TMA && DIM == 2 && A.use_tma) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
         if (tid == 0) {
             fail_s = 0;
@@ -683,7 +686,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 
     // The stage array is no longer read: bring the Un tile into it now, so that its
     // load overlaps the face phase (second phase of the same mbarrier).
-    const bool un_tma = DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
+    const bool un_tma = TMA && DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
     if (un_tma && tid == 0) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
         const uint32_t bytes = (uint32_t)(sizeof(Real) * K * TYC * TX);
@@ -1012,7 +1015,7 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     for (int t = tile0; t < tile0 + ntile; ++t) {
         const int tx0 = (t % I.ntx) * TX;
         const int ty0 = DIM == 2 ? (t / I.ntx) * TY : 0;
-        process_tile<P, FLUX, 0, 1, TY>(A, tx0, ty0, S);
+        process_tile<P, FLUX, 0, 1, TY, false>(A, tx0, ty0, S);
         __syncthreads();
     }
 }
@@ -1024,19 +1027,25 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
-// Persistent kernel over all work items of all stages: items are dequeued in order,
-// so every item an item waits for was dequeued earlier by a resident CTA (the launch is
-// cooperative, hence all CTAs are resident) and no wait can deadlock; each wait is
-// still bounded, and a wait that gives up stops the whole launch through B.abort.
-constexpr size_t kTileSmemMax =
-    sizeof(TileSmem<3, 1, TY>) > sizeof(TileSmem<2, 1, TY>) ? sizeof(TileSmem<3, 1, TY>) : sizeof(TileSmem<2, 1, TY>);
-constexpr size_t kBatchSmem = (kTileSmemMax + 127) / 128 * 128 + 128;   // tile + scheduler words
-
-__global__ void __launch_bounds__(NT, kF32 ? 6 : 3) batch_kernel(const BatchArgs B)
+// Persistent kernel over all work items of all stages of the instances of degree P:
+// items are dequeued in order, so every item an item waits for was dequeued earlier by a
+// resident CTA (the launch is cooperative, hence all CTAs are resident) and no wait can
+// deadlock; each wait is still bounded, and a wait that gives up stops the whole launch
+// through B.abort.  One kernel per degree keeps each variant's registers to its own
+// needs; instances of different degree never wait on each other.
+template <int P>
+constexpr size_t batch_smem_bytes()
 {
+    return (sizeof(TileSmem<P, 1, TY>) + 127) / 128 * 128 + 128;   // tile + scheduler words
+}
+
+template <int P>
+__global__ void __launch_bounds__(NT, kF32 ? (P == 1 ? 8 : 6) : 3) batch_kernel(const BatchArgs B)
+{
+    constexpr size_t kSmem = batch_smem_bytes<P>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    long long& s_w = *reinterpret_cast<long long*>(smem_raw + kBatchSmem - 128);
-    int& s_ok = *reinterpret_cast<int*>(smem_raw + kBatchSmem - 64);
+    long long& s_w = *reinterpret_cast<long long*>(smem_raw + kSmem - 128);
+    int& s_ok = *reinterpret_cast<int*>(smem_raw + kSmem - 64);
     const long long total = (long long)B.nitems * B.nstages;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1071,14 +1080,9 @@ __global__ void __launch_bounds__(NT, kF32 ? 6 : 3) batch_kernel(const BatchArgs
         if (!s_ok) break;
         __threadfence();
         const int r = g % 3;
-        switch (I.p * 8 + I.flux) {
-        case 1 * 8 + FLUX_ADVECT: batch_tiles<1, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw); break;
-        case 2 * 8 + FLUX_ADVECT: batch_tiles<2, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw); break;
-        case 3 * 8 + FLUX_ADVECT: batch_tiles<3, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw); break;
-        case 1 * 8 + FLUX_BURGERS: batch_tiles<1, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw); break;
-        case 2 * 8 + FLUX_BURGERS: batch_tiles<2, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw); break;
-        case 3 * 8 + FLUX_BURGERS: batch_tiles<3, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw); break;
-        default: break;
+        if (I.p == P) {
+            if (I.flux == FLUX_ADVECT) batch_tiles<P, FLUX_ADVECT>(B, I, r, it.tile0, it.ntile, smem_raw);
+            else if (I.flux == FLUX_BURGERS) batch_tiles<P, FLUX_BURGERS>(B, I, r, it.tile0, it.ntile, smem_raw);
         }
         __threadfence();
         __syncthreads();
@@ -1086,29 +1090,52 @@ __global__ void __launch_bounds__(NT, kF32 ? 6 : 3) batch_kernel(const BatchArgs
     }
 }
 
-static int batch_blocks_per_sm()
+template <int P>
+static int batch_blocks_per_sm_p()
 {
-    if (kBatchSmem > 48 * 1024 &&
-        cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess)
+    constexpr size_t kSmem = batch_smem_bytes<P>();
+    if (kSmem > 48 * 1024 &&
+        cudaFuncSetAttribute(batch_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, NT, kBatchSmem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<P>, NT, kSmem) != cudaSuccess) return 0;
     return n;
 }
 
-static cudaError_t launch_batch(const BatchArgs& a, int grid, cudaStream_t st)
+static int batch_blocks_per_sm(int p)
+{
+    switch (p) {
+    case 1: return batch_blocks_per_sm_p<1>();
+    case 2: return batch_blocks_per_sm_p<2>();
+    case 3: return batch_blocks_per_sm_p<3>();
+    default: return 0;
+    }
+}
+
+template <int P>
+static cudaError_t launch_batch_p(const BatchArgs& a, int grid, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = kBatchSmem;
+    cfg.dynamicSmemBytes = batch_smem_bytes<P>();
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_kernel, a);
+    return cudaLaunchKernelEx(&cfg, batch_kernel<P>, a);
+}
+
+static cudaError_t launch_batch(const BatchArgs& a, int p, int grid, cudaStream_t st)
+{
+    switch (p) {
+    case 1: return launch_batch_p<1>(a, grid, st);
+    case 2: return launch_batch_p<2>(a, grid, st);
+    case 3: return launch_batch_p<3>(a, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 #include "dgw_adjoint_impl.cuh"

@@ -9,11 +9,11 @@ cudaError_t launch_stage_f64_d1(const StageArgs& a, int p, int flux, int mode, c
 {
     return f64_d1::launch(a, p, flux, mode, s);
 }
-cudaError_t launch_batch_f64_d1(const BatchArgs& a, int grid, cudaStream_t s)
+cudaError_t launch_batch_f64_d1(const BatchArgs& a, int p, int grid, cudaStream_t s)
 {
-    return f64_d1::launch_batch(a, grid, s);
+    return f64_d1::launch_batch(a, p, grid, s);
 }
-int batch_blocks_per_sm_f64_d1() { return f64_d1::batch_blocks_per_sm(); }
+int batch_blocks_per_sm_f64_d1(int p) { return f64_d1::batch_blocks_per_sm(p); }
 cudaError_t launch_vjp_f64_d1(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s)
 {
     return f64_d1::launch_vjp(a, p, flux, lam, ws, wn, s);
