@@ -74,15 +74,17 @@ struct dgw_ctx {
     void* adj_b1 = nullptr;      // adjoint: lambda of stage 2
     void* adj_b2 = nullptr;      // adjoint: lambda of stage 1
     std::map<std::pair<const void*, int>, bool> no_tmap;
-    // dgw_rk_step_host pipeline: streams for input copies, the three stages and output
-    // copies, one event per (stream, band), and the join events
-    cudaStream_t band_st[5] = {};
-    cudaEvent_t band_ev[5][16] = {};
+    // dgw_rk_step_host pipeline: streams for input copies, output copies and a pool per
+    // stage; one event per (input copy or stage, band); the join events
+    cudaStream_t band_st[2 + 3 * 4] = {};
+    cudaEvent_t band_ev[4][16] = {};
     cudaEvent_t band_join[2] = {};
     std::map<BandKey, cudaGraphExec_t> band_graphs;   // null: replay not possible (direct launches)
 };
 
 static const int kBands = 16;
+static const int kStageStreams = 4;          // band kernels of one stage run concurrently
+static const int kBandStreams = 2 + 3 * kStageStreams;
 
 static const int kMassBlocks = 1024;
 static const int kMassThreads = 256;
@@ -204,11 +206,11 @@ extern "C" dgw_status dgw_destroy(dgw_ctx* c)
     cudaFree(c->adj_b2);
     cudaFree(c->partial);
     cudaFree(c->flag);
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < kBandStreams; ++i)
         if (c->band_st[i]) cudaStreamDestroy(c->band_st[i]);
+    for (int i = 0; i < 4; ++i)
         for (int b = 0; b < kBands; ++b)
             if (c->band_ev[i][b]) cudaEventDestroy(c->band_ev[i][b]);
-    }
     for (int i = 0; i < 2; ++i)
         if (c->band_join[i]) cudaEventDestroy(c->band_join[i]);
     delete c;
@@ -447,14 +449,17 @@ extern "C" dgw_status dgw_rk_step(dgw_ctx* c, void* U, double dt, int nsteps, vo
 }
 
 // One SSP-RK3 step of a 2D mesh that is not periodic in y, as a wavefront over bands of
-// tile rows: stage r of band b reads stage r - 1 on bands b - 1 .. b + 1 only, so the input
-// copy of a band, the three stages and the output copy of a finished band overlap.  Five
-// streams (input copies, stages 1-3, output copies) ordered by one event per (stream,
-// band), joined to the caller's stream s at both ends.  copy_in: U_in (host) is copied to
-// c->Uhost_dev band by band first; copy_out: the result is copied to U_out band by band.
-// Stage 3 writes U in place; every band that still reads the old U at a halo row (stage 1
-// of the band above) finished before the band's stage 3, which waits for stage 2 of the
-// band above, which waited for stage 1 two bands above.
+// tile rows: stage r of band b reads stage r - 1 on bands b - 1 .. b + 1 only, and bands of
+// one stage do not depend on each other.  So the input copy of a band, the three stages
+// and the output copy of a finished band overlap, and band kernels of a stage run
+// concurrently.  Streams: input copies (in order), output copies (in order), and a pool
+// of kStageStreams per stage (band b on stream b mod kStageStreams); one event per (input
+// copy or stage, band); all joined to the caller's stream s at both ends.  copy_in: U_in
+// (host) is copied to c->Uhost_dev band by band first; copy_out: the result is copied to
+// U_out band by band.  Stage 3 writes U in place; the old U of band b is still read by
+// stage 1 of bands b - 1 and b + 1 (halo rows) and by stages 2, 3 of band b (own rows):
+// stage 3 of band b waits for stage 2 of bands b - 1 .. b + 1, which waited for stage 1
+// of bands b - 2 .. b + 2.
 static dgw_status banded_step(dgw_ctx* c, const void* U_in, void* U_out, double dt, bool copy_in,
                               bool copy_out, cudaStream_t s)
 {
@@ -462,9 +467,11 @@ static dgw_status banded_step(dgw_ctx* c, const void* U_in, void* U_out, double 
     const int trows = (c->mesh.ny + rows - 1) / rows;
     const int nb = trows < kBands ? trows : kBands;
     cudaStream_t* st = c->band_st;
+    cudaStream_t in_st = st[0], out_st = st[1];
+    auto stage_st = [&](int r, int b) { return st[2 + r * kStageStreams + b % kStageStreams]; };
     auto& ev = c->band_ev;
     DGW_CUDA(cudaEventRecord(c->band_join[0], s));
-    for (int i = 0; i < 5; ++i) DGW_CUDA(cudaStreamWaitEvent(st[i], c->band_join[0], 0));
+    for (int i = 0; i < kBandStreams; ++i) DGW_CUDA(cudaStreamWaitEvent(st[i], c->band_join[0], 0));
 
     int t0[kBands + 1];                 // band b: tile rows [t0[b], t0[b + 1])
     for (int b = 0; b <= nb; ++b) t0[b] = (int)((int64_t)trows * b / nb);
@@ -481,8 +488,8 @@ static dgw_status banded_step(dgw_ctx* c, const void* U_in, void* U_out, double 
             size_t off, width;
             row_span(b, &off, &width);
             DGW_CUDA(cudaMemcpy2DAsync(U + off, pitch, static_cast<const char*>(U_in) + off, pitch, width,
-                                       (size_t)c->K, cudaMemcpyHostToDevice, st[0]));
-            DGW_CUDA(cudaEventRecord(ev[0][b], st[0]));
+                                       (size_t)c->K, cudaMemcpyHostToDevice, in_st));
+            DGW_CUDA(cudaEventRecord(ev[0][b], in_st));
         }
     StageArgs a = base_args(c);
     for (int r = 0; r < 3; ++r) {
@@ -490,38 +497,45 @@ static dgw_status banded_step(dgw_ctx* c, const void* U_in, void* U_out, double 
         if (r == 1) { a.Uk = c->S1; a.Un = U; a.Uout = c->S2; a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt; }
         if (r == 2) { a.Uk = c->S2; a.Un = U; a.Uout = U; a.cn = 1.0 / 3.0; a.ck = 2.0 / 3.0; a.cl = 2.0 / 3.0 * dt; }
         for (int b = 0; b < nb; ++b) {
-            const int dep = b + 1 < nb ? b + 1 : nb - 1;     // highest band read (halo row)
-            if (r > 0 || copy_in) DGW_CUDA(cudaStreamWaitEvent(st[1 + r], ev[r][dep], 0));
+            cudaStream_t ks = stage_st(r, b);
+            if (r == 0) {
+                // the input copies complete in order: the highest band read suffices
+                if (copy_in) DGW_CUDA(cudaStreamWaitEvent(ks, ev[0][b + 1 < nb ? b + 1 : nb - 1], 0));
+            } else {
+                for (int d = b - 1; d <= b + 1; ++d)
+                    if (d >= 0 && d < nb) DGW_CUDA(cudaStreamWaitEvent(ks, ev[r][d], 0));
+            }
             a.tile_row0 = t0[b];
             a.tile_rows = t0[b + 1] - t0[b];
-            DGW_CUDA(launch(c, a, 0, st[1 + r]));
-            DGW_CUDA(cudaEventRecord(ev[1 + r][b], st[1 + r]));
+            DGW_CUDA(launch(c, a, 0, ks));
+            DGW_CUDA(cudaEventRecord(ev[1 + r][b], ks));
         }
     }
     if (copy_out) {
         for (int b = 0; b < nb; ++b) {
             size_t off, width;
             row_span(b, &off, &width);
-            DGW_CUDA(cudaStreamWaitEvent(st[4], ev[3][b], 0));
+            DGW_CUDA(cudaStreamWaitEvent(out_st, ev[3][b], 0));
             DGW_CUDA(cudaMemcpy2DAsync(static_cast<char*>(U_out) + off, pitch, U + off, pitch, width,
-                                       (size_t)c->K, cudaMemcpyDeviceToHost, st[4]));
+                                       (size_t)c->K, cudaMemcpyDeviceToHost, out_st));
         }
-        DGW_CUDA(cudaEventRecord(c->band_join[1], st[4]));
+        // the last output copy comes after every other operation (each copy waited for its
+        // band's stage 3, which waited for everything before it)
+        DGW_CUDA(cudaEventRecord(c->band_join[1], out_st));
+        DGW_CUDA(cudaStreamWaitEvent(s, c->band_join[1], 0));
     } else {
-        DGW_CUDA(cudaEventRecord(c->band_join[1], st[3]));
+        for (int b = 0; b < nb; ++b) DGW_CUDA(cudaStreamWaitEvent(s, ev[3][b], 0));
     }
-    // the last output copy (or the last stage-3 band) comes after every other operation
-    DGW_CUDA(cudaStreamWaitEvent(s, c->band_join[1], 0));
     return DGW_OK;
 }
 
 static dgw_status band_resources(dgw_ctx* c)
 {
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < kBandStreams; ++i)
         if (!c->band_st[i]) DGW_CUDA(cudaStreamCreateWithFlags(&c->band_st[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 4; ++i)
         for (int b = 0; b < kBands; ++b)
             if (!c->band_ev[i][b]) DGW_CUDA(cudaEventCreateWithFlags(&c->band_ev[i][b], cudaEventDisableTiming));
-    }
     for (int i = 0; i < 2; ++i)
         if (!c->band_join[i]) DGW_CUDA(cudaEventCreateWithFlags(&c->band_join[i], cudaEventDisableTiming));
     return DGW_OK;
