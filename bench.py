@@ -328,6 +328,13 @@ def run_adjoint(local, n=512, steps=200, every=20):
     c.project(torch.tensor(I.u0_fourier_steps(pt, X, Y).reshape(-1), device=dev), Ut)
     c.rk_step(Ut, dt, steps)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    # untimed warm-up: three rollouts of one checkpoint segment with their backward passes
+    # on this context (first launches of the adjoint kernels, the context's adjoint
+    # buffers, the allocator's room for a segment's recomputed states)
+    for _ in range(3):
+        Uw = U0.clone().requires_grad_(True)
+        adjoint.misfit(c, adjoint.rollout(c, Uw, dt, min(steps, every), every=every), Ut).backward()
+    del Uw
     U0g = U0.clone().requires_grad_(True)
     torch.cuda.synchronize()
     ev[0].record()
