@@ -3,7 +3,8 @@
 Workload (default): the 2D KPP problem u_t + div(sin u, cos u) = 0 on
 [-2,2]x[-2.5,1.5], 1024x1024 square cells, Q3 (16 modes per cell, 16,777,216 DOFs),
 FP32 state and arithmetic, outflow boundaries, lambda_e = 2, WENO sensor with q = 1,
-SSP-RK3 at CFL 0.05 (dt = 9.765625e-5).  Initial data 7 pi/2 inside the unit disc,
+SSP-RK3 at CFL 0.02 (dt = 3.90625e-5; the stabilization term gamma nu K limits the step:
+lambda dt / h must stay below 0.044 at p = 3 in 2D).  Initial data 7 pi/2 inside the unit disc,
 pi/4 outside, L2-projected by the library from 8x8 Gauss samples per cell.
 
 A "step" is one full SSP-RK3 step (three fused stage kernels).  The metric is
@@ -36,13 +37,15 @@ from paper_2309_12019_gb300 import inputs as I  # noqa: E402
 WORKLOADS = {
     "kpp_1024x1024_q3": dict(dim=2, nx=1024, ny=1024, p=3, box=(-2.0, 2.0, -2.5, 1.5),
                              bc=("outflow",) * 4, flux="kpp", lambda_nu=2.0, stab="weno",
-                             cfl=0.05, speeds=(1.0, 1.0), u0="kpp"),
+                             cfl=0.02, speeds=(1.0, 1.0), u0="kpp"),
     "rotation_256x256_q2": dict(dim=2, nx=256, ny=256, p=2, box=(0.0, 1.0, 0.0, 1.0),
                                 bc=("inflow_zero",) * 4, flux="rotation", center=(0.5, 0.5), omega=1.0,
                                 stab="weno", cfl=0.1, speeds=(0.5, 0.5), u0="rotation"),
     "advect1d_128_p2": dict(dim=1, nx=128, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4,
                             flux="advect", a=(1.0, 0.0), stab="weno", cfl=0.1, speeds=(1.0,), u0="mixed1d"),
 }
+# the KPP workload with the comparison sensor of Zhao et al. (Sec. 5.6) in place of Eq. (sensor)
+WORKLOADS["kpp_1024x1024_q3_zhao"] = dict(WORKLOADS["kpp_1024x1024_q3"], stab="zhao")
 
 SPEC_KEYS = ("dim", "nx", "ny", "p", "box", "bc", "flux", "lambda_nu", "stab", "center", "omega", "a")
 
@@ -96,7 +99,7 @@ def stage_flops_per_cell(dim, p, flux, stab):
     kpp = flux == "kpp"
     red = 6                                        # 2 pi reduction of one sin/cos argument
     f = 0
-    if stab == "weno":                             # Hermite candidates, indicators, blend
+    if stab in ("weno", "zhao"):                   # Hermite candidates, indicators, blend
         qf = qform_flops(p, dim)
         for axis in range(dim):
             shift = sum(2 * (n1 - ((c % n1) if axis == 0 else (c // n1))) for c in range(1, k))
@@ -239,7 +242,8 @@ def run_gpu(w, prec, steps, warmup, world, local, measure_e2e):
     barrier(world)
     t_dev = ev0.elapsed_time(ev1) / 1e3
     ctx.sync_status(stream)
-    res = dict(N=N, t=t_dev, clocks=clk.summary(), launches=3 * steps, mass=ctx.mass(U, stream))
+    res = dict(N=N, t=t_dev, clocks=clk.summary(), launches=3 * steps, mass=ctx.mass(U, stream),
+               mean_range=[float(U[0].min()), float(U[0].max())])
     if measure_e2e:
         # end to end through the host-buffer entry point: H2D + step + D2H every step
         Uh = U0.cpu().pin_memory()
@@ -358,7 +362,8 @@ def run_small(name, prec, steps, warmup, local):
     w = WORKLOADS[name]
     r = run_gpu(w, prec, steps, warmup, 1, local, measure_e2e=False)
     return {"workload": name, "dtype": "f64" if prec == "fp64" else "f32", "value": 3 * r["N"] * steps / r["t"],
-            "unit": "DOF-updates/s", "steps": steps, "ms_per_step": 1e3 * r["t"] / steps}
+            "unit": "DOF-updates/s", "steps": steps, "ms_per_step": 1e3 * r["t"] / steps,
+            "cell_mean_range_after": r["mean_range"]}
 
 
 def run_reference(w, steps, warmup, budget_s=12.0):
@@ -451,7 +456,8 @@ def main():
     if not args.no_extras:
         extras["ensemble"] = run_ensemble(100, 3, local)
         extras["adjoint"] = run_adjoint(local)
-        extras["others"] = [run_small("rotation_256x256_q2", "fp64", 100, 5, local),
+        extras["others"] = [run_small("kpp_1024x1024_q3_zhao", "fp32", 100, 5, local),
+                            run_small("rotation_256x256_q2", "fp64", 100, 5, local),
                             run_small("rotation_256x256_q2", "fp32", 100, 5, local),
                             run_small("advect1d_128_p2", "fp64", 1280, 10, local)]
     if rank != 0:
@@ -476,7 +482,8 @@ def main():
                                  "peak_source": src, "bytes_per_launch": alg_bytes}},
             "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": r32.get("bytes"),
                     "d2h_bytes_per_step": r32.get("bytes")} if "t_e2e" in r32 else None,
-            "gpu_launches": r32["launches"], "clocks": r32["clocks"], "mass_after": r32["mass"]}
+            "gpu_launches": r32["launches"], "clocks": r32["clocks"], "mass_after": r32["mass"],
+            "cell_mean_range_after": r32["mean_range"]}
     if r64 is not None:
         line["fp64"] = {"value": 3 * N * r64["steps"] / r64["t"], "unit": "DOF-updates/s",
                         "ms_per_step": 1e3 * r64["t"] / r64["steps"], "steps": r64["steps"]}

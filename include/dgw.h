@@ -82,7 +82,7 @@ typedef struct {
                                volume and face Gauss points */
 } dgw_flux;
 
-typedef enum { DGW_STAB_DG = 0, DGW_STAB_LO = 1, DGW_STAB_WENO = 2 } dgw_stab;
+typedef enum { DGW_STAB_DG = 0, DGW_STAB_LO = 1, DGW_STAB_WENO = 2, DGW_STAB_ZHAO = 3 } dgw_stab;
 
 /* DGW_FP64: every operation in double.  DGW_FP32: state, residual and RK update in
  * float with float accumulation; operator tables are built in double and rounded. */
@@ -90,7 +90,11 @@ typedef enum { DGW_FP64 = 0, DGW_FP32 = 1 } dgw_prec;
 
 /* Stabilization and sensor parameters (Sec. 3-5). */
 typedef struct {
-    int stab;               /* dgw_stab: DG (none), LO (gamma = 1), WENO (Eq. sensor) */
+    int stab;               /* dgw_stab: DG (none), LO (gamma = 1), WENO (Eq. sensor), ZHAO
+                               (the comparison sensor of Zhao et al. that Sec. 5.6 restates:
+                               gamma = sum_l |w_l / lin_l - 1|^theta / (|1 / min lin - 1|^theta
+                               + m_e) over the same candidates and weights; 0 without
+                               neighbours; q and b do not apply; needs w_nbr > 0) */
     double q;               /* sensor exponent, Eq. (sensor); the paper uses 1 */
     double b;               /* threshold of Eq. (gensensor); 0 recovers Eq. (sensor) */
     double w_nbr;           /* linear weight of each neighbour candidate (paper: 1e-2);
@@ -98,6 +102,7 @@ typedef struct {
     double eps_w;           /* nonlinear weights w_l ~ lin_l / (eps_w + beta_l)^2 (1e-6) */
     double eps_s;           /* ||U - U*||_e <= eps_s gives gamma = 0 (1e-12) */
     int prec;               /* dgw_prec */
+    double theta;           /* exponent of the ZHAO sensor (> 0); the paper uses 1 */
 } dgw_params;
 
 typedef struct dgw_ctx dgw_ctx;

@@ -46,6 +46,10 @@
  *      (unless a fixed value is given, as the paper does for the KPP problem).
  *   R8 boundary ghosts: periodic wrap; inflow-zero sets U+ = 0 where F'(U-).n < 0 and
  *      U+ = U- elsewhere; outflow sets U+ = U-.
+ *   R13 the comparison sensor of Zhao et al. (restated in Sec. 5.6), stab = ZHAO:
+ *      gamma^Z = sum_l |w_l / lin_l - 1|^theta / (|1 / min_l lin_l - 1|^theta + m_e) with
+ *      the weights of R3; with no neighbour candidate (m_e = 0) the weights are the linear
+ *      ones and gamma^Z = 0.  It replaces gamma_e in Eq. (astab); q and b do not apply.
  *
  * Mode ordering: k = i + (p+1)*j, i the Legendre degree along x, j along y (1D: k = i).
  * State layout: U[k*E + e], element e = iy*nx + ix.
@@ -65,7 +69,7 @@
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW_ZERO = 1, ORC_BC_OUTFLOW = 2 };
 enum { ORC_FLUX_ADVECT = 0, ORC_FLUX_ROTATION = 1, ORC_FLUX_BURGERS = 2, ORC_FLUX_KPP = 3 };
-enum { ORC_STAB_DG = 0, ORC_STAB_LO = 1, ORC_STAB_WENO = 2 };
+enum { ORC_STAB_DG = 0, ORC_STAB_LO = 1, ORC_STAB_WENO = 2, ORC_STAB_ZHAO = 3 };
 
 typedef struct {
     int dim, nx, ny, p;
@@ -78,6 +82,7 @@ typedef struct {
     double lambda_nu;        /* > 0: fixed lambda_e for nu_e */
     int stab;
     double q, b, w_nbr, eps_w, eps_s;
+    double theta;            /* exponent of the Zhao et al. sensor (stab = ZHAO) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -481,6 +486,15 @@ static double sensor_elem(const orc_problem* P, const double* U, long e,
         gamma = pow(r < 1.0 ? r : 1.0, P->q);
         if (r < P->b) gamma = 0.0;
     }
+    if (P->stab == ORC_STAB_ZHAO) {
+        /* R13: deviation of the nonlinear weights from the linear ones, scaled by its
+         * largest possible value (all weight on the candidate of smallest linear weight) */
+        double minlin = lin[0];
+        for (int l = 1; l <= m; ++l) minlin = lin[l] < minlin ? lin[l] : minlin;
+        double dev = 0.0;
+        for (int l = 0; l <= m; ++l) dev += pow(fabs(wt[l] / wsum / lin[l] - 1.0), P->theta);
+        gamma = m == 0 ? 0.0 : dev / (pow(fabs(1.0 / minlin - 1.0), P->theta) + m);
+    }
     if (ratio_out) *ratio_out = r;
     return gamma;
 }
@@ -609,6 +623,7 @@ int orc_check(const orc_problem* P)
         double hx = hx_of(P), hy = hy_of(P);
         if (fabs(hx - hy) > 1e-12 * hx) return -1;
     }
+    if (P->stab == ORC_STAB_ZHAO && !(P->w_nbr > 0.0 && P->theta > 0.0)) return -1;   /* lin_l > 0 */
     return 0;
 }
 

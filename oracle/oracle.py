@@ -31,7 +31,7 @@ _lib = None
 
 BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2}
 FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3}
-STAB = {"dg": 0, "lo": 1, "weno": 2}
+STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +62,7 @@ class _Problem(ctypes.Structure):
         ("stab", ctypes.c_int),
         ("q", ctypes.c_double), ("b", ctypes.c_double), ("w_nbr", ctypes.c_double),
         ("eps_w", ctypes.c_double), ("eps_s", ctypes.c_double),
+        ("theta", ctypes.c_double),
     ]
 
 
@@ -85,6 +86,7 @@ class Problem:
     w_nbr: float = 1e-2
     eps_w: float = 1e-6
     eps_s: float = 1e-12
+    theta: float = 1.0
 
     @property
     def E(self) -> int:
@@ -110,6 +112,7 @@ class Problem:
         s.omega, s.lambda_nu = self.omega, self.lambda_nu
         s.stab = STAB[self.stab]
         s.q, s.b, s.w_nbr, s.eps_w, s.eps_s = self.q, self.b, self.w_nbr, self.eps_w, self.eps_s
+        s.theta = self.theta
         return s
 
 

@@ -105,20 +105,22 @@ extern "C" void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s)
     if (s) {
         std::memset(s, 0, sizeof *s);
         s->stab = DGW_STAB_WENO; s->q = 1.0; s->b = 0.0; s->w_nbr = 1e-2;
-        s->eps_w = 1e-6; s->eps_s = 1e-12; s->prec = DGW_FP64;
+        s->eps_w = 1e-6; s->eps_s = 1e-12; s->prec = DGW_FP64; s->theta = 1.0;
     }
 }
 
 static dgw_status check_params(const dgw_params* s, int dim)
 {
     if (!s) return fail(DGW_EINVAL, "params is NULL");
-    if (s->stab < DGW_STAB_DG || s->stab > DGW_STAB_WENO) return fail(DGW_EINVAL, "bad stab %d", s->stab);
+    if (s->stab < DGW_STAB_DG || s->stab > DGW_STAB_ZHAO) return fail(DGW_EINVAL, "bad stab %d", s->stab);
     if (s->prec != DGW_FP64 && s->prec != DGW_FP32) return fail(DGW_EINVAL, "bad prec %d", s->prec);
     if (!(s->q > 0.0) || !std::isfinite(s->q)) return fail(DGW_EINVAL, "q must be > 0");
     if (!(s->b >= 0.0 && s->b <= 1.0)) return fail(DGW_EINVAL, "b must lie in [0, 1]");
     if (!(s->w_nbr >= 0.0 && s->w_nbr * 2 * dim < 1.0))
         return fail(DGW_EINVAL, "w_nbr must lie in [0, 1/(2 dim))");
     if (!(s->eps_w > 0.0) || !(s->eps_s >= 0.0)) return fail(DGW_EINVAL, "eps_w > 0 and eps_s >= 0 required");
+    if (s->stab == DGW_STAB_ZHAO && !(s->w_nbr > 0.0 && s->theta > 0.0 && std::isfinite(s->theta)))
+        return fail(DGW_EINVAL, "the ZHAO sensor needs w_nbr > 0 and a finite theta > 0");
     return DGW_OK;
 }
 
@@ -315,6 +317,7 @@ static StageArgs base_args(const dgw_ctx* c)
     a.w_nbr = c->params.w_nbr;
     a.eps_w = c->params.eps_w;
     a.eps_s = c->params.eps_s;
+    a.theta = c->params.theta;
     a.flag = c->flag;
     return a;
 }
@@ -940,7 +943,7 @@ static dgw_status batch_enqueue(dgw_batch* b, void* U, int nsteps, cudaStream_t 
             a.abort = b->abort;
             a.stab = b->params.stab;
             a.q = b->params.q; a.b = b->params.b; a.w_nbr = b->params.w_nbr;
-            a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s;
+            a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s; a.theta = b->params.theta;
             a.wait_limit = b->wait_limit;
             a.unreachable = b->unreachable;
             const bool f64 = b->eb == 8;
@@ -1092,6 +1095,8 @@ static dgw_status adjoint_ready(dgw_ctx* c)
             return fail(DGW_EUNSUPPORTED, "the adjoint is built for periodic meshes");
     if (c->flux.kind != DGW_FLUX_ADVECT && c->flux.kind != DGW_FLUX_BURGERS)
         return fail(DGW_EUNSUPPORTED, "the adjoint is built for the advection and Burgers fluxes");
+    if (c->params.stab == DGW_STAB_ZHAO)
+        return fail(DGW_EUNSUPPORTED, "the adjoint differentiates the DG, LO and WENO stabilizations");
     const size_t bytes = (size_t)c->K * c->E * c->eb;
     cudaError_t e = cudaSuccess;
     if (!c->adj_ws) e = cudaMalloc(&c->adj_ws, bytes);

@@ -28,7 +28,7 @@ constexpr int stage_rows(bool f64) { return stage_thread_rows(f64) * stage_lanes
 
 enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2 };
 enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3 };
-enum : int { STAB_DG = 0, STAB_LO = 1, STAB_WENO = 2 };
+enum : int { STAB_DG = 0, STAB_LO = 1, STAB_WENO = 2, STAB_ZHAO = 3 };
 
 // Operator tables of degree p, built once in double on the host (dgw_tables.cu) and
 // rounded to the kernel precision when uploaded.  Reference element [-1, 1]^d.
@@ -63,7 +63,7 @@ struct StageArgs {
     int bc[4];
     double a0, a1, cx, cy, omega, lambda_nu;
     int stab;
-    double q, b, w_nbr, eps_w, eps_s;
+    double q, b, w_nbr, eps_w, eps_s, theta;
     double* gamma_out;     // optional per-element gamma (double)
     unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x (stage_rows + 2) x K), or null
@@ -103,7 +103,7 @@ struct BatchArgs {
     unsigned* flag;                // bit 0: non-finite; bit 1: a bounded wait gave up
     int* abort;                    // set when a wait gave up: every CTA stops
     int stab;
-    double q, b, w_nbr, eps_w, eps_s;
+    double q, b, w_nbr, eps_w, eps_s, theta;
     long long wait_limit;          // spin iterations before a wait gives up
     int unreachable;               // diagnostic: ask one tile more than exists (wait must give up)
 };

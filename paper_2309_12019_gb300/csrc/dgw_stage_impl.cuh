@@ -128,6 +128,8 @@ struct alignas(64) KParams {
     Real x0, y0, h, hh, two_h;
     Real a0, a1, cx, cy, omega, lambda_nu;
     Real q, b, w_nbr, eps_w, eps_s;
+    Real theta;          // exponent of the Zhao et al. sensor (stab == STAB_ZHAO)
+    int theta_one;       // theta == 1
     Real cn, ck, cl;
 };
 
@@ -263,6 +265,10 @@ __device__ __forceinline__ Real llf(const KParams& A, int axis, Real uL, Real uR
         return Real(0.5) * (fL + fR) - Real(0.5) * s * (uR - uL);
     }
 }
+
+// x^theta of the Zhao et al. sensor (theta = 1 in the paper)
+template <class KP>
+__device__ __forceinline__ Real zpow(const KP& A, Real x) { return A.theta_one ? x : pow(x, A.theta); }
 
 // v^T G v over modes >= 1; G vanishes unless both Legendre degree pairs have even sums,
 // so it splits into the four parity classes of (i, j), summed in independent chains.
@@ -534,9 +540,10 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 
     // ---- 1b. sensor (Sec. 4): Hermite candidates of the face neighbours ----
     V gamma = vbc<V>((MODE == 0 && A.stab == STAB_LO) ? Real(1) : Real(0));
-    if ((MODE == 1 || A.stab == STAB_WENO) && any_in) {
+    if ((MODE == 1 || A.stab >= STAB_WENO) && any_in) {
         bool has[2 * DIM][L];   // face neighbour f of lane l's cell exists
         V wsum;
+        V wnb[2 * DIM];         // unnormalised neighbour weights (zero where missing)
         const V beta0 = qform<P>(T, c);
         const V d0 = vadd(vbc<V>(A.eps_w), beta0);
 #pragma unroll
@@ -551,11 +558,13 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
             }
             lane(wsum, l) = div_w(Real(1) - Real(me) * A.w_nbr, lane(d0, l) * lane(d0, l));
         }
+        const V w0 = wsum;      // unnormalised weight of the cell's own candidate
         V dacc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) dacc[k] = vbc<V>(0);
 #pragma unroll
         for (int f = 0; f < 2 * DIM; ++f) {
+            wnb[f] = vbc<V>(0);
             bool any = false;
 #pragma unroll
             for (int l = 0; l < L; ++l) any = any || has[f][l];
@@ -589,34 +598,60 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
             for (int l = 0; l < L; ++l)
                 lane(wl, l) = has[f][l] ? div_w(A.w_nbr, lane(dl, l) * lane(dl, l)) : Real(0);
             wsum = vadd(wsum, wl);
+            wnb[f] = wl;
 #pragma unroll
             for (int k = 1; k < K; ++k) dacc[k] = vfma(wl, vsub(c[k], cl[k]), dacc[k]);
         }
-        // U - U* = sum_l w_l (c - c_l)
         V inv;
 #pragma unroll
         for (int l = 0; l < L; ++l) lane(inv, l) = div_w(Real(1), lane(wsum, l));
+        if (A.stab == STAB_ZHAO) {
+            // the comparison sensor of Zhao et al. restated in Sec. 5.6: deviation of the
+            // nonlinear weights from the linear ones, over its largest possible value (all
+            // weight on the candidate of smallest linear weight); 0 without neighbours
 #pragma unroll
-        for (int k = 1; k < K; ++k) dacc[k] = vmul(dacc[k], inv);
-        dacc[0] = vbc<V>(0);
-        const V qd = qform<P>(T, dacc);
+            for (int l = 0; l < L; ++l) {
+                int me = 0;
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const Real num = sqrt_r(fmax(lane(qd, l), Real(0)));
-            const Real b0 = lane(beta0, l);
-            Real g;
-            if (num <= A.eps_s) {
-                g = Real(0);
-            } else if (b0 <= Real(0)) {
-                g = Real(1);
-            } else {
-                const Real r = num / sqrt_r(b0);
-                g = r < Real(1) ? r : Real(1);
-                if (!A.q_one) g = pow(g, A.q);
-                if (r < A.b) g = Real(0);
+                for (int f = 0; f < 2 * DIM; ++f) me += has[f][l] ? 1 : 0;
+                Real g = Real(0);
+                if (me > 0) {
+                    const Real lin0 = Real(1) - Real(me) * A.w_nbr;
+                    const Real iw = lane(inv, l);
+                    Real dev = zpow(A, fabs(lane(w0, l) * iw / lin0 - Real(1)));
+#pragma unroll
+                    for (int f = 0; f < 2 * DIM; ++f)
+                        if (has[f][l]) dev += zpow(A, fabs(lane(wnb[f], l) * iw / A.w_nbr - Real(1)));
+                    const Real minlin = lin0 < A.w_nbr ? lin0 : A.w_nbr;
+                    g = dev / (zpow(A, fabs(Real(1) / minlin - Real(1))) + Real(me));
+                }
+                lane(gamma, l) = g;
+                if (MODE == 1 && in[l]) A.gamma_out[(int64_t)gy[l] * A.nx + gx] = (double)g;
             }
-            lane(gamma, l) = g;
-            if (MODE == 1 && in[l]) A.gamma_out[(int64_t)gy[l] * A.nx + gx] = (double)g;
+        } else {
+            // U - U* = sum_l w_l (c - c_l)
+#pragma unroll
+            for (int k = 1; k < K; ++k) dacc[k] = vmul(dacc[k], inv);
+            dacc[0] = vbc<V>(0);
+            const V qd = qform<P>(T, dacc);
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const Real num = sqrt_r(fmax(lane(qd, l), Real(0)));
+                const Real b0 = lane(beta0, l);
+                Real g;
+                if (num <= A.eps_s) {
+                    g = Real(0);
+                } else if (b0 <= Real(0)) {
+                    g = Real(1);
+                } else {
+                    const Real r = num / sqrt_r(b0);
+                    g = r < Real(1) ? r : Real(1);
+                    if (!A.q_one) g = pow(g, A.q);
+                    if (r < A.b) g = Real(0);
+                }
+                lane(gamma, l) = g;
+                if (MODE == 1 && in[l]) A.gamma_out[(int64_t)gy[l] * A.nx + gx] = (double)g;
+            }
         }
     }
     if (MODE == 1) return;
@@ -968,6 +1003,8 @@ static KParams make_params(const StageArgs& s)
     a.omega = (Real)s.omega; a.lambda_nu = (Real)s.lambda_nu;
     a.q = (Real)s.q; a.b = (Real)s.b; a.w_nbr = (Real)s.w_nbr; a.eps_w = (Real)s.eps_w;
     a.eps_s = (Real)s.eps_s;
+    a.theta = (Real)s.theta;
+    a.theta_one = s.theta == 1.0;
     a.cn = (Real)s.cn; a.ck = (Real)s.ck; a.cl = (Real)s.cl;
     return a;
 }
@@ -1007,6 +1044,8 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     A.omega = (Real)I.omega; A.lambda_nu = (Real)I.lambda_nu;
     A.q = (Real)B.q; A.b = (Real)B.b; A.w_nbr = (Real)B.w_nbr; A.eps_w = (Real)B.eps_w;
     A.eps_s = (Real)B.eps_s;
+    A.theta = (Real)B.theta;
+    A.theta_one = B.theta == 1.0;
     const double dt = I.dt;
     A.cn = (Real)(r == 0 ? 0.0 : (r == 1 ? 0.75 : 1.0 / 3.0));
     A.ck = (Real)(r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0));

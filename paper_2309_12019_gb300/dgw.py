@@ -19,7 +19,7 @@ _lib = None
 
 BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2}
 FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3}
-STAB = {"dg": 0, "lo": 1, "weno": 2}
+STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 PREC = {"fp64": 0, "fp32": 1}
 
 STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ECUDA", -4: "DGW_EUNSUPPORTED",
@@ -47,7 +47,7 @@ class Flux(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("stab", ctypes.c_int), ("q", ctypes.c_double), ("b", ctypes.c_double),
                 ("w_nbr", ctypes.c_double), ("eps_w", ctypes.c_double), ("eps_s", ctypes.c_double),
-                ("prec", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("theta", ctypes.c_double)]
 
 
 # every symbol declared in include/dgw.h
@@ -146,6 +146,7 @@ class Problem:
     eps_w: float = 1e-6
     eps_s: float = 1e-12
     prec: str = "fp64"
+    theta: float = 1.0
 
     @property
     def E(self) -> int:
@@ -168,7 +169,7 @@ class Problem:
         f.omega, f.lambda_nu = self.omega, self.lambda_nu
         s = Params()
         s.stab, s.q, s.b, s.w_nbr = STAB[self.stab], self.q, self.b, self.w_nbr
-        s.eps_w, s.eps_s, s.prec = self.eps_w, self.eps_s, PREC[self.prec]
+        s.eps_w, s.eps_s, s.prec, s.theta = self.eps_w, self.eps_s, PREC[self.prec], self.theta
         return m, f, s
 
 

@@ -147,6 +147,11 @@ def sensor(P, U):
         beta = np.array([_seminorm2(m, cl, c) for cl in cands])
         wt = lin / (P.eps_w + beta) ** 2
         w = wt / wt.sum()
+        if P.stab == "zhao":
+            # Zhao et al.'s sensor as restated in Sec. 5.6 (no neighbour: weights = linear)
+            gam[e] = 0.0 if me == 0 else (np.sum(np.abs(w / lin - 1) ** P.theta) /
+                                          (abs(1 / lin.min() - 1) ** P.theta + me))
+            continue
         ustar = sum(wl * cl for wl, cl in zip(w, cands))
         num = np.sqrt(_seminorm2(m, ce - ustar, c))
         den = np.sqrt(_seminorm2(m, ce, c))
@@ -187,7 +192,7 @@ def residual(P, U):
     m = Mesh(P)
     E, K = P.E, P.K
     L = np.zeros((K, E))
-    gam = sensor(P, U) if P.stab == "weno" else np.full(E, 1.0 if P.stab == "lo" else 0.0)
+    gam = sensor(P, U) if P.stab in ("weno", "zhao") else np.full(E, 1.0 if P.stab == "lo" else 0.0)
     for e in range(E):
         c = m.centre(e)
         ce = U[:, e]

@@ -188,3 +188,15 @@ def test_burgers_512_q2_fp32_gradient_vs_fd16():
         ad = float((g * v).sum())
         worst = max(worst, abs(ad - fd) / abs(fd))
     assert worst <= 1e-4, worst
+
+
+def test_adjoint_refuses_zhao_sensor():
+    """The discrete adjoint differentiates the DG, LO and WENO stabilizations; a context
+    with the Zhao et al. comparison sensor gets DGW_EUNSUPPORTED, not a wrong gradient."""
+    s = H.spec(2, 2, 8, flux="burgers", stab="zhao")
+    ctx = dgw.Context(dgw.Problem(**s, prec="fp64"))
+    U = torch.zeros((ctx.K, ctx.E), dtype=torch.float64, device="cuda")
+    with pytest.raises(dgw.DGWError) as ei:
+        ctx.residual_vjp(U, U.clone(), torch.empty_like(U))
+    assert ei.value.status == -4
+    ctx.close()

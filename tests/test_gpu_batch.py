@@ -164,3 +164,18 @@ def test_ensemble_workload_instances_match_oracle(oracle_mod):
     for j, s in enumerate(specs):
         ref = oracle_mod.rk3(oracle_mod.Problem(**s), refs[j], dts[j], 4)
         assert H.rel_l2(b.view(U, j).cpu().numpy(), ref) <= 1e-12, (j, s["dim"], s["p"], s["nx"])
+
+
+def test_batch_zhao_fp64_matches_oracle(oracle_mod):
+    """The batch kernels with the Zhao et al. sensor (stab = zhao), against the oracle."""
+    specs = [dict(s, stab="zhao") for s in _specs(4)]
+    b = _batch(specs, "fp64")
+    states = [H.state_for(s, seed=930 + i) for i, s in enumerate(specs)]
+    dts = [0.005 / s["nx"] for s in specs]
+    b.set_dt(dts)
+    U = _pack(b, states, torch.float64)
+    b.rk_step(U, 4)
+    b.sync_status()
+    for i, s in enumerate(specs):
+        ref = oracle_mod.rk3(oracle_mod.Problem(**s), states[i], dts[i], 4)
+        assert H.rel_l2(b.view(U, i).cpu().numpy(), ref) <= 1e-12, (i, s)

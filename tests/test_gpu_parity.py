@@ -120,6 +120,45 @@ def test_residual_fp32_random(oracle_mod, dim, p, flux, stab):
     assert H.rel_l2(got, ref) <= 1e-5
 
 
+ZHAO_CASES = [(1, 1, "burgers", "periodic"), (1, 3, "advect", "outflow"), (2, 1, "advect", "periodic"),
+              (2, 2, "rotation", "inflow_zero"), (2, 3, "kpp", "outflow"), (2, 3, "burgers", "periodic")]
+
+
+@pytest.mark.parametrize("dim,p,flux,bc", ZHAO_CASES)
+def test_zhao_sensor_and_residual_fp64(oracle_mod, dim, p, flux, bc):
+    """The comparison sensor of Zhao et al. (stab = zhao, Sec. 5.6) in double: sensor-only
+    launch and stabilized residual against the oracle."""
+    s = H.spec(dim, p, 300 if dim == 1 else 19, ny=13, flux=flux, stab="zhao", bc=bc)
+    U = H.state_for(s, seed=600 + p)
+    g_ref, _, _ = oracle_mod.sensor(oracle_mod.Problem(**s), U)
+    g = gpu_sensor(gpu(s), U)
+    assert np.max(np.abs(g - g_ref)) <= 1e-12
+    assert 0.05 < np.mean(g > 1e-3)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    assert H.rel_l2(gpu_residual(gpu(s), U), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,p,flux,bc", [(36, 21, 3, "kpp", "outflow"), (19, 13, 2, "advect", "periodic"),
+                                             (32, 17, 1, "rotation", "inflow_zero")])
+def test_zhao_fp32(oracle_mod, nx, ny, p, flux, bc):
+    """The Zhao et al. sensor in float, two cells per thread: sensor within 1e-4 and
+    residual within 1e-5 (relative L2) of the oracle on the float-representable state."""
+    s = H.spec(2, p, nx, ny=ny, flux=flux, stab="zhao", bc=bc)
+    U = H.state_for(s, seed=620 + p).astype(np.float32).astype(np.float64)
+    g_ref, _, _ = oracle_mod.sensor(oracle_mod.Problem(**s), U)
+    assert np.max(np.abs(gpu_sensor(gpu(s, "fp32"), U) - g_ref)) <= 1e-4
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    assert H.rel_l2(gpu_residual(gpu(s, "fp32"), U), ref) <= 1e-5
+
+
+def test_zhao_parameter_checks():
+    """w_nbr = 0 (zero linear weights) and theta <= 0 are refused for the Zhao sensor."""
+    for kw in ({"w_nbr": 0.0}, {"theta": 0.0}):
+        with pytest.raises(dgw.DGWError) as ei:
+            gpu(H.spec(2, 2, 8, stab="zhao", **kw))
+        assert ei.value.status == -1
+
+
 @pytest.mark.parametrize("p,flux,stab,bc,ny", [(3, "kpp", "weno", "outflow", 21), (2, "rotation", "weno", "inflow_zero", 17),
                                                (1, "advect", "weno", "periodic", 19), (3, "burgers", "lo", "periodic", 33)])
 def test_residual_fp32_tma_ragged_rows(oracle_mod, p, flux, stab, bc, ny):
@@ -358,3 +397,21 @@ def test_fast_sincos_error_bound():
     xd = x.double()
     assert float((s.double() - torch.sin(xd)).abs().max()) <= 1e-6
     assert float((c.double() - torch.cos(xd)).abs().max()) <= 1e-6
+
+
+@pytest.mark.parametrize("stab", ["weno", "zhao"])
+def test_kpp_workload_stays_bounded(stab):
+    """The KPP workload's data and time step (CFL 0.02, within the stabilization's step
+    bound) on a 256^2 Q3 mesh in float: after 200 SSP-RK3 steps every cell mean stays
+    within 0.3 of the data range [pi/4, 7pi/2] (an unstable step grows them by orders of
+    magnitude within tens of steps)."""
+    import bench
+    w = dict(bench.WORKLOADS["kpp_1024x1024_q3"], nx=256, ny=256, stab=stab)
+    ctx = dgw.Context(dgw.Problem(**bench.spec_of(w), prec="fp32"))
+    U = torch.empty((ctx.K, ctx.E), dtype=torch.float32, device="cuda")
+    ctx.project(torch.tensor(bench.initial_samples(w), device="cuda"), U)
+    ctx.rk_step(U, bench.dt_of(w), 200)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert float(U[0].min()) > np.pi / 4 - 0.3 and float(U[0].max()) < 3.5 * np.pi + 0.3
+    ctx.close()

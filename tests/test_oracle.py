@@ -210,6 +210,46 @@ def test_sensor_worked_example_1d_p1(oracle_mod):
     assert abs((1 - g[1]) - 4.9e-11) < 0.1e-11
 
 
+def test_zhao_sensor_worked_values_1d_p1(oracle_mod):
+    """The comparison sensor of Zhao et al. restated in Sec. 5.6 (theta = 1), by hand on
+    1D p = 1 cells.  (i) Slopes (0.9, 1, 1.1): weights (0.977974, 0.015210, 0.006816)
+    against linear weights (0.98, 0.01, 0.01) give (0.0020673 + 0.5210 + 0.3184) / (99 + 2)
+    = 8.33136e-3.  (ii) A step cell between two constant cells: both neighbour candidates
+    are flat, each takes half of the weight: (1 + 49 + 49) / 101 = 99/101.  (iii) Flat
+    left neighbour, steep right one: all weight on the left candidate, the one of smallest
+    linear weight: (1 + 99 + 1) / 101 = 1."""
+    O = oracle_mod
+    P = O.Problem(dim=1, nx=3, p=1, stab="zhao")
+    g, _, _ = O.sensor(P, np.array([[0.0, 0.0, 0.0], [0.9, 1.0, 1.1]]))
+    assert abs(g[1] - 8.33136e-3) < 3e-6
+    g, _, _ = O.sensor(P, np.array([[0.0, 0.3, 0.0], [0.0, 0.5, 0.0]]))
+    assert abs(g[1] - 99.0 / 101.0) < 1e-9
+    g, _, _ = O.sensor(P, np.array([[0.0, 0.3, 0.0], [0.0, 0.5, 3.0]]))
+    assert abs(g[1] - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("dim,p", [(1, 2), (2, 1), (2, 3)])
+def test_zhao_sensor_range_invariance_and_polynomials(oracle_mod, dim, p):
+    """gamma^Z lies in [0, 1] (the denominator is the value for all weight on the candidate
+    of smallest linear weight), ignores constants, and vanishes up to round-off on global
+    polynomials (equal indicators make the weights the linear ones)."""
+    O = oracle_mod
+    n = 6
+    P = O.Problem(dim=dim, nx=n, ny=n, p=p, stab="zhao")
+    U = I.random_state(dim, p, P.E, seed=23, smooth=True)
+    g, _, _ = O.sensor(P, U)
+    U2 = U.copy()
+    U2[0] += 2.9
+    g2, _, _ = O.sensor(P, U2)
+    assert np.all((g >= 0) & (g <= 1)) and np.any(g > 1e-2)
+    assert np.max(np.abs(g - g2)) < 1e-12
+    Pp = O.Problem(dim=dim, nx=n, ny=n, p=p, box=(-1.0, 1.5, -1.0, 1.5), bc=("outflow",) * 4, stab="zhao")
+    X, Y = I.sample_points(dim, n, n, Pp.box, 8)
+    f = 0.3 + X - 0.7 * X ** p + (0.5 * Y ** p if dim == 2 else 0.0)
+    gp, _, _ = O.sensor(Pp, O.project(Pp, f))
+    assert np.max(np.abs(gp)) < 1e-13
+
+
 @pytest.mark.parametrize("dim,p", [(1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3)])
 def test_polynomial_reproduction(oracle_mod, dim, p):
     """Any global polynomial of V_p is reproduced by every Hermite candidate, so U* = U_h,
@@ -321,7 +361,8 @@ def test_mass_conservation_periodic(oracle_mod, dim, flux, stab):
 BF_CASES = [
     (1, p, fl, st, bc) for p in (1, 2, 3) for fl in ("advect", "burgers") for st in ("dg", "lo", "weno")
     for bc in ("periodic", "outflow")
-] + [(1, 2, "advect", "weno", "inflow_zero")] + [
+] + [(1, 2, "advect", "weno", "inflow_zero"), (1, 2, "burgers", "zhao", "outflow"), (1, 3, "advect", "zhao", "periodic"),
+       (2, 2, "advect", "zhao", "periodic"), (2, 3, "rotation", "zhao", "inflow_zero")] + [
     (2, p, fl, st, bc) for p in (1, 2, 3) for fl in ("advect", "rotation") for st in ("lo", "weno")
     for bc in ("periodic", "inflow_zero")
 ]
@@ -337,7 +378,7 @@ def test_bruteforce_agreement(oracle_mod, dim, p, flux, stab, bc):
     L = O.residual(P, U)
     Lb = bruteforce.residual(P, U)
     assert np.max(np.abs(L - Lb)) < 1e-12 * np.max(np.abs(Lb))
-    if stab == "weno":
+    if stab in ("weno", "zhao"):
         g, _, _ = O.sensor(P, U)
         assert np.max(np.abs(g - bruteforce.sensor(P, U))) < 1e-12
 
