@@ -103,6 +103,11 @@ typedef struct {
     double eps_s;           /* ||U - U*||_e <= eps_s gives gamma = 0 (1e-12) */
     int prec;               /* dgw_prec */
     double theta;           /* exponent of the ZHAO sensor (> 0); the paper uses 1 */
+    int rk_order;           /* SSP Runge-Kutta of dgw_rk_step / dgw_rk_step_host / the no-alloc
+                               step: 3 = Eq. (ssp) (default), 2 = the two-stage SSP method,
+                               4 = Ketcheson's ten-stage SSP method (Sec. 5 uses order p + 1;
+                               the paper names no scheme).  The adjoint and the batch step
+                               implement order 3 only and refuse the others. */
 } dgw_params;
 
 typedef struct dgw_ctx dgw_ctx;

@@ -687,6 +687,54 @@ void orc_rk3(const orc_problem* P, double* U, double dt, int nsteps)
     free(L); free(U1); free(U2);
 }
 
+/* SSP Runge-Kutta of order p + 1 for the convergence studies of Sec. 5 (reading R14: the
+ * paper names no scheme).  Order 2: the two-stage SSP method (Heun),
+ *   U1 = U + dt L(U),  U <- 1/2 U + 1/2 (U1 + dt L(U1)). */
+void orc_rk2(const orc_problem* P, double* U, double dt, int nsteps)
+{
+    long N = nelem(P) * nmodes(P);
+    double* L = malloc(sizeof(double) * N);
+    double* U1 = malloc(sizeof(double) * N);
+    for (int s = 0; s < nsteps; ++s) {
+        orc_residual(P, U, L);
+        for (long i = 0; i < N; ++i) U1[i] = U[i] + dt * L[i];
+        orc_residual(P, U1, L);
+        for (long i = 0; i < N; ++i) U[i] = 0.5 * U[i] + 0.5 * U1[i] + 0.5 * dt * L[i];
+    }
+    free(L); free(U1);
+}
+
+/* Order 4: the ten-stage low-storage SSP method of Ketcheson (2008), two registers:
+ *   q1 = q2 = U;  five times q1 <- q1 + dt/6 L(q1);
+ *   q2 <- q2/25 + 9/25 q1;  q1 <- 15 q2 - 5 q1;
+ *   four times q1 <- q1 + dt/6 L(q1);
+ *   U <- q2 + 3/5 q1 + dt/10 L(q1). */
+void orc_rk4(const orc_problem* P, double* U, double dt, int nsteps)
+{
+    long N = nelem(P) * nmodes(P);
+    double* L = malloc(sizeof(double) * N);
+    double* q1 = malloc(sizeof(double) * N);
+    double* q2 = malloc(sizeof(double) * N);
+    for (int s = 0; s < nsteps; ++s) {
+        for (long i = 0; i < N; ++i) q1[i] = q2[i] = U[i];
+        for (int k = 0; k < 5; ++k) {
+            orc_residual(P, q1, L);
+            for (long i = 0; i < N; ++i) q1[i] += dt / 6.0 * L[i];
+        }
+        for (long i = 0; i < N; ++i) {
+            q2[i] = q2[i] / 25.0 + 9.0 / 25.0 * q1[i];
+            q1[i] = 15.0 * q2[i] - 5.0 * q1[i];
+        }
+        for (int k = 0; k < 4; ++k) {
+            orc_residual(P, q1, L);
+            for (long i = 0; i < N; ++i) q1[i] += dt / 6.0 * L[i];
+        }
+        orc_residual(P, q1, L);
+        for (long i = 0; i < N; ++i) U[i] = q2[i] + 3.0 / 5.0 * q1[i] + dt / 10.0 * L[i];
+    }
+    free(L); free(q1); free(q2);
+}
+
 /* Sample layout for projection / error: f[e*nq^d + a + nq*b] at the physical points
  * x = xc + hx/2 * g_a, y = yc + hy/2 * g_b of the nq-point Gauss-Legendre rule. */
 

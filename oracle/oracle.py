@@ -128,6 +128,8 @@ def lib():
             L.orc_sensor.argtypes = [pp, dp, dp, dp, dp]
             L.orc_lambda.argtypes = [pp, dp, dp]
             L.orc_rk3.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
+            L.orc_rk2.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
+            L.orc_rk4.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
             L.orc_project.argtypes = [pp, ctypes.c_int, dp, dp]
             L.orc_l1_error.argtypes = [pp, dp, ctypes.c_int, dp]
             L.orc_l1_error.restype = ctypes.c_double
@@ -228,6 +230,15 @@ def rk3(P: Problem, U, dt: float, nsteps: int) -> np.ndarray:
     """nsteps steps of the optimal SSP-RK3 scheme (Eq. ssp); returns the new state."""
     c, U = _checked(P), _state(P, U).copy()
     lib().orc_rk3(ctypes.byref(c), _ptr(U), float(dt), int(nsteps))
+    return U
+
+
+def rk(P: Problem, U, dt: float, nsteps: int, order: int = 3) -> np.ndarray:
+    """nsteps steps of the SSP Runge-Kutta scheme of the given order: 2 (Heun), 3
+    (Eq. ssp) or 4 (Ketcheson's ten-stage method); returns the new state."""
+    c, U = _checked(P), _state(P, U).copy()
+    fn = {2: lib().orc_rk2, 3: lib().orc_rk3, 4: lib().orc_rk4}[order]
+    fn(ctypes.byref(c), _ptr(U), float(dt), int(nsteps))
     return U
 
 

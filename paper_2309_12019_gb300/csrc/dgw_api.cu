@@ -105,7 +105,7 @@ extern "C" void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s)
     if (s) {
         std::memset(s, 0, sizeof *s);
         s->stab = DGW_STAB_WENO; s->q = 1.0; s->b = 0.0; s->w_nbr = 1e-2;
-        s->eps_w = 1e-6; s->eps_s = 1e-12; s->prec = DGW_FP64; s->theta = 1.0;
+        s->eps_w = 1e-6; s->eps_s = 1e-12; s->prec = DGW_FP64; s->theta = 1.0; s->rk_order = 3;
     }
 }
 
@@ -121,6 +121,7 @@ static dgw_status check_params(const dgw_params* s, int dim)
     if (!(s->eps_w > 0.0) || !(s->eps_s >= 0.0)) return fail(DGW_EINVAL, "eps_w > 0 and eps_s >= 0 required");
     if (s->stab == DGW_STAB_ZHAO && !(s->w_nbr > 0.0 && s->theta > 0.0 && std::isfinite(s->theta)))
         return fail(DGW_EINVAL, "the ZHAO sensor needs w_nbr > 0 and a finite theta > 0");
+    if (s->rk_order < 2 || s->rk_order > 4) return fail(DGW_EINVAL, "rk_order must be 2, 3 or 4");
     return DGW_OK;
 }
 
@@ -374,11 +375,70 @@ extern "C" dgw_status dgw_sensor(dgw_ctx* c, const void* U, double* gamma, void*
     return DGW_OK;
 }
 
+// The register recombination of the ten-stage SSP method of order 4:
+// q2 <- q2/25 + 9/25 q1, then q1 <- 15 q2 - 5 q1 (with the new q2).
+template <typename Real>
+__global__ void rk4_mix_kernel(Real* __restrict__ q2, Real* __restrict__ q1, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Real b = q2[i] / Real(25) + Real(9) / Real(25) * q1[i];
+        q2[i] = b;
+        q1[i] = Real(15) * b - Real(5) * q1[i];
+    }
+}
+
+// SSP Runge-Kutta of order 2 and 4 (c->params.rk_order; Sec. 5 integrates with order
+// p + 1).  Order 2: S1 = U + dt L(U); U <- 1/2 U + 1/2 (S1 + dt L(S1)).  Order 4 (the
+// ten-stage method of Ketcheson): q2 lives in U, q1 alternates between S1 and S2;
+// five stages q1 <- q1 + dt/6 L(q1), the recombination, four more, and
+// U <- q2 + 3/5 q1 + dt/10 L(q1).  Final stages write U in place (own-element reads).
+static cudaError_t enqueue_steps_rk24(const dgw_ctx* c, void* U, double dt, int nsteps, cudaStream_t s)
+{
+    StageArgs a = base_args(c);
+    for (int n = 0; n < nsteps; ++n) {
+        if (c->params.rk_order == 2) {
+            a.Uk = U; a.Un = nullptr; a.Uout = c->S1;
+            a.cn = 0.0; a.ck = 1.0; a.cl = dt;
+            cudaError_t e = launch(c, a, 0, s);
+            if (e != cudaSuccess) return e;
+            a.Uk = c->S1; a.Un = U; a.Uout = U;
+            a.cn = 0.5; a.ck = 0.5; a.cl = 0.5 * dt;
+            e = launch(c, a, 0, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        void* q[2] = {c->S1, c->S2};
+        int cur = 0;                       // q1 is q[cur]
+        a.Un = nullptr; a.cn = 0.0; a.ck = 1.0; a.cl = dt / 6.0;
+        for (int k = 0; k < 9; ++k) {
+            a.Uk = k == 0 ? U : q[cur];
+            a.Uout = k == 0 ? q[0] : q[cur ^ 1];
+            cudaError_t e = launch(c, a, 0, s);
+            if (e != cudaSuccess) return e;
+            if (k > 0) cur ^= 1;
+            if (k == 4) {
+                const int64_t N = (int64_t)c->K * c->E;
+                const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 16);
+                if (c->eb == 8) rk4_mix_kernel<double><<<blocks, 256, 0, s>>>((double*)U, (double*)q[cur], N);
+                else rk4_mix_kernel<float><<<blocks, 256, 0, s>>>((float*)U, (float*)q[cur], N);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
+        }
+        a.Uk = q[cur]; a.Un = U; a.Uout = U;
+        a.cn = 1.0; a.ck = 3.0 / 5.0; a.cl = dt / 10.0;
+        cudaError_t e = launch(c, a, 0, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // One SSP-RK3 step (Eq. ssp): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
 // U <- 1/3 U + 2/3 (U2 + dt L(U2)).  The third stage writes U in place: each thread
-// reads U only at its own element there.
+// reads U only at its own element there.  Other orders: enqueue_steps_rk24.
 static cudaError_t enqueue_steps(const dgw_ctx* c, void* U, double dt, int nsteps, cudaStream_t s)
 {
+    if (c->params.rk_order != 3) return enqueue_steps_rk24(c, U, dt, nsteps, s);
     StageArgs a = base_args(c);
     for (int n = 0; n < nsteps; ++n) {
         a.Uk = U; a.Un = nullptr; a.Uout = c->S1;
@@ -594,7 +654,8 @@ extern "C" dgw_status dgw_rk_step_host(dgw_ctx* c, const void* U_in, void* U_out
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int rows = stage_rows(c->eb == 8);
-    const bool pipelined = c->mesh.dim == 2 && c->mesh.bc[2] != DGW_BC_PERIODIC && c->mesh.ny >= 2 * rows;
+    const bool pipelined = c->mesh.dim == 2 && c->mesh.bc[2] != DGW_BC_PERIODIC && c->mesh.ny >= 2 * rows &&
+                           c->params.rk_order == 3;
     if (!pipelined) {
         DGW_CUDA(cudaMemcpyAsync(c->Uhost_dev, U_in, bytes, cudaMemcpyHostToDevice, s));
         st = dgw_rk_step(c, c->Uhost_dev, dt, nsteps, stream);
@@ -761,6 +822,7 @@ extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int*
     if (!out || !meshes || !ps || !fluxes || !params || n < 1) return fail(DGW_EINVAL, "bad arguments to dgw_batch_create");
     *out = nullptr;
     dgw_status st = check_params(params, 2);
+    if (params->rk_order != 3) return fail(DGW_EUNSUPPORTED, "the batch step is SSP-RK3 (rk_order 3)");
     if (st != DGW_OK) return st;
     std::vector<BatchInst> insts;
     std::vector<int> dims;
@@ -1157,6 +1219,8 @@ extern "C" dgw_status dgw_adjoint_step(dgw_ctx* c, const void* U_n, const void* 
     if (st != DGW_OK) return st;
     if (!U_n || !lam_np1 || !lam_n) return fail(DGW_EINVAL, "NULL array");
     if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
+    if (c->params.rk_order != 3)
+        return fail(DGW_EUNSUPPORTED, "the adjoint step reverses the SSP-RK3 step (rk_order 3)");
     st = adjoint_ready(c);
     if (st != DGW_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;

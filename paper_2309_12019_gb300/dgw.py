@@ -47,7 +47,7 @@ class Flux(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("stab", ctypes.c_int), ("q", ctypes.c_double), ("b", ctypes.c_double),
                 ("w_nbr", ctypes.c_double), ("eps_w", ctypes.c_double), ("eps_s", ctypes.c_double),
-                ("prec", ctypes.c_int), ("theta", ctypes.c_double)]
+                ("prec", ctypes.c_int), ("theta", ctypes.c_double), ("rk_order", ctypes.c_int)]
 
 
 # every symbol declared in include/dgw.h
@@ -147,6 +147,7 @@ class Problem:
     eps_s: float = 1e-12
     prec: str = "fp64"
     theta: float = 1.0
+    rk_order: int = 3
 
     @property
     def E(self) -> int:
@@ -170,6 +171,7 @@ class Problem:
         s = Params()
         s.stab, s.q, s.b, s.w_nbr = STAB[self.stab], self.q, self.b, self.w_nbr
         s.eps_w, s.eps_s, s.prec, s.theta = self.eps_w, self.eps_s, PREC[self.prec], self.theta
+        s.rk_order = self.rk_order
         return m, f, s
 
 

@@ -415,3 +415,60 @@ def test_kpp_workload_stays_bounded(stab):
     ctx.sync_status()
     assert float(U[0].min()) > np.pi / 4 - 0.3 and float(U[0].max()) < 3.5 * np.pi + 0.3
     ctx.close()
+
+
+@pytest.mark.parametrize("order,dim,p,flux,bc", [(2, 1, 1, "burgers", "periodic"), (4, 1, 3, "advect", "outflow"),
+                                                 (2, 2, 1, "rotation", "inflow_zero"), (4, 2, 3, "kpp", "outflow"),
+                                                 (4, 2, 2, "burgers", "periodic")])
+def test_ssp_rk_orders_fp64(oracle_mod, order, dim, p, flux, bc):
+    """SSP Runge-Kutta of order 2 and 4 (rk_order; Sec. 5 uses order p + 1) against the
+    oracle's schemes, through the graph-replayed step and on the default stream."""
+    s = H.spec(dim, p, 200 if dim == 1 else 12, ny=9, flux=flux, bc=bc)
+    U = H.state_for(s, seed=700 + p)
+    dt, n = 0.02 / s["nx"], 5
+    ref = oracle_mod.rk(oracle_mod.Problem(**s), U, dt, n, order)
+    ctx = dgw.Context(dgw.Problem(**s, prec="fp64", rk_order=order))
+    for stream in (torch.cuda.Stream(), None):
+        Ud = to_dev(U, "fp64")
+        if stream is None:
+            ctx.rk_step(Ud, dt, n, stream=0)
+        else:
+            with torch.cuda.stream(stream):
+                ctx.rk_step(Ud, dt, n)
+        torch.cuda.synchronize()
+        assert H.rel_l2(Ud.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_ssp_rk_orders_fp32_and_host_entry(oracle_mod, order):
+    """Float steps of order 2 and 4 on smooth data within 2e-5 of the oracle, and the
+    host-buffer entry point bit for bit equal to the device entry point."""
+    n = 24
+    s = H.spec(2, 3, n, flux="advect")
+    X, Y = I.sample_points(2, n, n, s["box"], 8)
+    f = np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y) + 0.5
+    U = oracle_mod.project(oracle_mod.Problem(**s), f).astype(np.float32).astype(np.float64)
+    dt = I.cfl_dt(0.02, [0.9, 0.6], [1.0 / n] * 2)
+    ref = oracle_mod.rk(oracle_mod.Problem(**s), U, dt, 10, order)
+    ctx = dgw.Context(dgw.Problem(**s, prec="fp32", rk_order=order))
+    Ud = to_dev(U, "fp32")
+    ctx.rk_step(Ud, dt, 10)
+    torch.cuda.synchronize()
+    assert H.rel_l2(Ud.double().cpu().numpy(), ref) <= 2e-5
+    Uh = torch.tensor(U, dtype=torch.float32).pin_memory()
+    out = torch.empty_like(Uh).pin_memory()
+    ctx.rk_step_host(Uh, out, dt, 10)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), Ud.cpu().numpy())
+
+
+def test_rk_order_checks():
+    """rk_order outside {2, 3, 4} is refused; the adjoint step refuses orders other than 3."""
+    with pytest.raises(dgw.DGWError) as ei:
+        dgw.Context(dgw.Problem(**H.spec(1, 2, 8), rk_order=5))
+    assert ei.value.status == -1
+    ctx = dgw.Context(dgw.Problem(**H.spec(1, 2, 8, flux="burgers"), rk_order=4))
+    U = torch.zeros((ctx.K, ctx.E), dtype=torch.float64, device="cuda")
+    with pytest.raises(dgw.DGWError) as ei:
+        ctx.adjoint_step(U, U.clone(), torch.empty_like(U), 1e-3)
+    assert ei.value.status == -4
