@@ -77,7 +77,7 @@ def dt_of(w):
 # 1024^2 Q3 KPP workload, averaged over the three stages of one step, from one ncu
 # capture (profiles/stage_kernel_kpp_1024x1024_q3.md).  Reset to None whenever the
 # stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = 138.4e6
+STAGE_TRAFFIC_BYTES = 138.5e6
 
 # FP32 peak of one GB300 from its unit counts and maximum clock: 152 SMs x 128 FP32
 # lanes x 2 flops per FMA x 2.07 GHz.
