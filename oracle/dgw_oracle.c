@@ -46,6 +46,14 @@
  *      (unless a fixed value is given, as the paper does for the KPP problem).
  *   R8 boundary ghosts: periodic wrap; inflow-zero sets U+ = 0 where F'(U-).n < 0 and
  *      U+ = U- elsewhere; outflow sets U+ = U-.
+ *   R15 Euler system (1D, Sec. 5.6): U = (rho, rho v, rho E), p = (gamma - 1)(rho E -
+ *      rho v^2 / 2), F = (rho v, rho v^2 + p, (rho E + p) v); state layout
+ *      U[(comp (p+1) + k) E + e].  s+ of the LLF flux is read as the larger of |v| + c at
+ *      the two states (the maximum along the path in conservative variables has no
+ *      closed form); lambda_e = max (|v| + c) over the element's volume and face points.
+ *      Reflecting walls mirror the state: (rho, -rho v, rho E).  The sensor uses the
+ *      density alone, applied to all components; beyond a wall, as beyond any
+ *      non-periodic boundary, there is no neighbour candidate.
  *   R13 the comparison sensor of Zhao et al. (restated in Sec. 5.6), stab = ZHAO:
  *      gamma^Z = sum_l |w_l / lin_l - 1|^theta / (|1 / min_l lin_l - 1|^theta + m_e) with
  *      the weights of R3; with no neighbour candidate (m_e = 0) the weights are the linear
@@ -67,8 +75,8 @@
 #define ORC_MAXK ((ORC_MAXP + 1) * (ORC_MAXP + 1))
 #define ORC_MAXNQ 32
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW_ZERO = 1, ORC_BC_OUTFLOW = 2 };
-enum { ORC_FLUX_ADVECT = 0, ORC_FLUX_ROTATION = 1, ORC_FLUX_BURGERS = 2, ORC_FLUX_KPP = 3 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW_ZERO = 1, ORC_BC_OUTFLOW = 2, ORC_BC_REFLECT = 3 };
+enum { ORC_FLUX_ADVECT = 0, ORC_FLUX_ROTATION = 1, ORC_FLUX_BURGERS = 2, ORC_FLUX_KPP = 3, ORC_FLUX_EULER = 4 };
 enum { ORC_STAB_DG = 0, ORC_STAB_LO = 1, ORC_STAB_WENO = 2, ORC_STAB_ZHAO = 3 };
 
 typedef struct {
@@ -83,6 +91,7 @@ typedef struct {
     int stab;
     double q, b, w_nbr, eps_w, eps_s;
     double theta;            /* exponent of the Zhao et al. sensor (stab = ZHAO) */
+    double gas_gamma;        /* ratio of heat capacities (Euler) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -179,6 +188,8 @@ void orc_gauss_legendre(int n, double* x, double* w)
 static int nmodes1(const orc_problem* P) { return P->p + 1; }
 static int nmodes(const orc_problem* P) { return P->dim == 1 ? P->p + 1 : (P->p + 1) * (P->p + 1); }
 static long nelem(const orc_problem* P) { return P->dim == 1 ? (long)P->nx : (long)P->nx * P->ny; }
+static int ncomp(const orc_problem* P) { return P->flux == ORC_FLUX_EULER ? 3 : 1; }
+static long nstate(const orc_problem* P) { return nelem(P) * nmodes(P) * ncomp(P); }
 static double hx_of(const orc_problem* P) { return (P->x1 - P->x0) / P->nx; }
 static double hy_of(const orc_problem* P) { return P->dim == 1 ? 1.0 : (P->y1 - P->y0) / P->ny; }
 
@@ -606,6 +617,134 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
 }
 
 /* ------------------------------------------------------------------------- */
+/* Euler system in 1D (Sec. 5.6; reading R15)                                */
+/* ------------------------------------------------------------------------- */
+
+static void euler_flux(const orc_problem* P, const double q[3], double F[3])
+{
+    double v = q[1] / q[0];
+    double pr = (P->gas_gamma - 1.0) * (q[2] - 0.5 * q[1] * v);
+    F[0] = q[1];
+    F[1] = q[1] * v + pr;
+    F[2] = (q[2] + pr) * v;
+}
+
+/* |v| + c, the spectral radius of the flux Jacobian */
+static double euler_speed(const orc_problem* P, const double q[3])
+{
+    double v = q[1] / q[0];
+    double pr = (P->gas_gamma - 1.0) * (q[2] - 0.5 * q[1] * v);
+    return fabs(v) + sqrt(P->gas_gamma * pr / q[0]);
+}
+
+/* LLF flux for the normal n = +-1 (R15: s+ = the larger endpoint speed) */
+static void euler_llf(const orc_problem* P, const double um[3], const double up[3], double n, double H[3])
+{
+    double Fm[3], Fp[3];
+    euler_flux(P, um, Fm);
+    euler_flux(P, up, Fp);
+    double sm = euler_speed(P, um), sp = euler_speed(P, up);
+    double s = sm > sp ? sm : sp;
+    for (int c = 0; c < 3; ++c) H[c] = n * 0.5 * (Fm[c] + Fp[c]) - 0.5 * s * (up[c] - um[c]);
+}
+
+void orc_euler_llf(const orc_problem* P, const double* um, const double* up, double n, double* H)
+{
+    euler_llf(P, um, up, n, H);
+}
+
+static void load_comp(const orc_problem* P, const double* U, long e, int comp, double* c)
+{
+    long E = nelem(P);
+    int K = nmodes(P);
+    for (int k = 0; k < K; ++k) c[k] = U[((long)comp * K + k) * E + e];
+}
+
+/* lambda_e of R15: max (|v| + c) over the p+2 Gauss points and the two end points */
+static double euler_lambda_elem(const orc_problem* P, long e, double ce[3][ORC_MAXK])
+{
+    double qx[ORC_MAXNQ], qy[ORC_MAXNQ], qr[ORC_MAXNQ], qs[ORC_MAXNQ], qw[ORC_MAXNQ];
+    int nv = elem_quad(P, e, P->p + 2, qx, qy, qr, qs, qw);
+    double lam = 0.0;
+    for (int t = 0; t < nv + 2; ++t) {
+        double r = t < nv ? qr[t] : (t == nv ? -1.0 : 1.0), q[3];
+        for (int c = 0; c < 3; ++c) q[c] = poly_d(P, ce[c], 0, 0, r, 0.0);
+        double sp = euler_speed(P, q);
+        if (sp > lam) lam = sp;
+    }
+    return lam;
+}
+
+static void euler_residual_elem(const orc_problem* P, const double* U, long e, double* Le, double* gamma_out)
+{
+    int K = nmodes(P);
+    int nq = P->p + 2;
+    double ce[3][ORC_MAXK], cn[3][ORC_MAXK], R[3][ORC_MAXK];
+    double qx[ORC_MAXNQ], qy[ORC_MAXNQ], qr[ORC_MAXNQ], qs[ORC_MAXNQ], qw[ORC_MAXNQ];
+    double fx[ORC_MAXNQ], fy[ORC_MAXNQ], fr[ORC_MAXNQ], fs[ORC_MAXNQ], fw[ORC_MAXNQ], n[2];
+    memset(R, 0, sizeof R);
+    for (int c = 0; c < 3; ++c) load_comp(P, U, e, c, ce[c]);
+
+    /* volume: + int phi_k' F(U_h) dx */
+    int nv = elem_quad(P, e, nq, qx, qy, qr, qs, qw);
+    for (int t = 0; t < nv; ++t) {
+        double q[3], F[3];
+        for (int c = 0; c < 3; ++c) q[c] = poly_d(P, ce[c], 0, 0, qr[t], 0.0);
+        euler_flux(P, q, F);
+        for (int k = 0; k < K; ++k) {
+            double d = phi_d(P, k, 1, 0, qr[t], 0.0);
+            for (int c = 0; c < 3; ++c) R[c][k] += qw[t] * d * F[c];
+        }
+    }
+
+    /* faces: - phi_k H(U-, U+, n) at x = x_e -+ h/2 */
+    for (int f = 0; f < 2; ++f) {
+        double sx = 0.0, sy = 0.0;
+        long nb = neighbour(P, e, f, &sx, &sy);
+        if (nb >= 0)
+            for (int c = 0; c < 3; ++c) load_comp(P, U, nb, c, cn[c]);
+        face_quad(P, e, f, nq, fx, fy, fr, fs, fw, n);
+        double um[3], up[3], H[3];
+        for (int c = 0; c < 3; ++c) um[c] = poly_d(P, ce[c], 0, 0, fr[0], 0.0);
+        if (nb >= 0) {
+            for (int c = 0; c < 3; ++c) up[c] = poly_d(P, cn[c], 0, 0, fr[0] + sx, 0.0);
+        } else if (P->bc[f] == ORC_BC_REFLECT) {
+            up[0] = um[0]; up[1] = -um[1]; up[2] = um[2];
+        } else {
+            for (int c = 0; c < 3; ++c) up[c] = um[c];
+        }
+        euler_llf(P, um, up, n[0], H);
+        for (int k = 0; k < K; ++k) {
+            double ph = phi_d(P, k, 0, 0, fr[0], 0.0);
+            for (int c = 0; c < 3; ++c) R[c][k] -= fw[0] * ph * H[c];
+        }
+    }
+
+    /* stabilization of every component with the density sensor */
+    double gamma = 0.0;
+    if (P->stab != ORC_STAB_DG && P->p >= 1) {
+        gamma = (P->stab == ORC_STAB_LO) ? 1.0 : sensor_elem(P, U, e, NULL, NULL);
+        double lam = P->lambda_nu > 0.0 ? P->lambda_nu : euler_lambda_elem(P, e, ce);
+        double nu = lam * hx_of(P) / (2.0 * P->p);
+        for (int t = 0; t < nv; ++t)
+            for (int c = 0; c < 3; ++c) {
+                double ux = poly_d(P, ce[c], 1, 0, qr[t], 0.0);
+                for (int k = 0; k < K; ++k) R[c][k] -= gamma * nu * qw[t] * phi_d(P, k, 1, 0, qr[t], 0.0) * ux;
+            }
+    }
+    if (gamma_out) *gamma_out = gamma;
+
+    for (int k = 0; k < K; ++k) {
+        double m = 0.0;
+        for (int t = 0; t < nv; ++t) {
+            double ph = phi_d(P, k, 0, 0, qr[t], 0.0);
+            m += qw[t] * ph * ph;
+        }
+        for (int c = 0; c < 3; ++c) Le[c * K + k] = R[c][k] / m;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Public entry points (ctypes)                                               */
 /* ------------------------------------------------------------------------- */
 
@@ -624,6 +763,9 @@ int orc_check(const orc_problem* P)
         if (fabs(hx - hy) > 1e-12 * hx) return -1;
     }
     if (P->stab == ORC_STAB_ZHAO && !(P->w_nbr > 0.0 && P->theta > 0.0)) return -1;   /* lin_l > 0 */
+    for (int f = 0; f < 2 * P->dim; ++f)           /* walls are for the Euler system */
+        if (P->bc[f] == ORC_BC_REFLECT && P->flux != ORC_FLUX_EULER) return -1;
+    if (P->flux == ORC_FLUX_EULER && (P->dim != 1 || !(P->gas_gamma > 1.0))) return -1;
     return 0;
 }
 
@@ -636,9 +778,14 @@ void orc_residual(const orc_problem* P, const double* U, double* L)
 #pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
     for (long e = 0; e < E; ++e) {
-        double Le[ORC_MAXK];
-        residual_elem(P, U, e, Le, NULL);
-        for (int k = 0; k < K; ++k) L[k * E + e] = Le[k];
+        double Le[3 * ORC_MAXK];
+        if (P->flux == ORC_FLUX_EULER) {
+            euler_residual_elem(P, U, e, Le, NULL);
+            for (int k = 0; k < 3 * K; ++k) L[k * E + e] = Le[k];
+        } else {
+            residual_elem(P, U, e, Le, NULL);
+            for (int k = 0; k < K; ++k) L[k * E + e] = Le[k];
+        }
     }
 }
 
@@ -663,6 +810,12 @@ void orc_lambda(const orc_problem* P, const double* U, double* lam)
     orc_init();
     long E = nelem(P);
     for (long e = 0; e < E; ++e) {
+        if (P->flux == ORC_FLUX_EULER) {
+            double cq[3][ORC_MAXK];
+            for (int c = 0; c < 3; ++c) load_comp(P, U, e, c, cq[c]);
+            lam[e] = euler_lambda_elem(P, e, cq);
+            continue;
+        }
         double ce[ORC_MAXK];
         load_elem(P, U, e, ce);
         lam[e] = lambda_elem(P, e, ce);
@@ -672,7 +825,7 @@ void orc_lambda(const orc_problem* P, const double* U, double* lam)
 /* Optimal third-order SSP Runge-Kutta (Eq. ssp), nsteps steps of size dt, in place. */
 void orc_rk3(const orc_problem* P, double* U, double dt, int nsteps)
 {
-    long N = nelem(P) * nmodes(P);
+    long N = nstate(P);
     double* L = malloc(sizeof(double) * N);
     double* U1 = malloc(sizeof(double) * N);
     double* U2 = malloc(sizeof(double) * N);
@@ -692,7 +845,7 @@ void orc_rk3(const orc_problem* P, double* U, double dt, int nsteps)
  *   U1 = U + dt L(U),  U <- 1/2 U + 1/2 (U1 + dt L(U1)). */
 void orc_rk2(const orc_problem* P, double* U, double dt, int nsteps)
 {
-    long N = nelem(P) * nmodes(P);
+    long N = nstate(P);
     double* L = malloc(sizeof(double) * N);
     double* U1 = malloc(sizeof(double) * N);
     for (int s = 0; s < nsteps; ++s) {
@@ -711,7 +864,7 @@ void orc_rk2(const orc_problem* P, double* U, double dt, int nsteps)
  *   U <- q2 + 3/5 q1 + dt/10 L(q1). */
 void orc_rk4(const orc_problem* P, double* U, double dt, int nsteps)
 {
-    long N = nelem(P) * nmodes(P);
+    long N = nstate(P);
     double* L = malloc(sizeof(double) * N);
     double* q1 = malloc(sizeof(double) * N);
     double* q2 = malloc(sizeof(double) * N);
@@ -844,13 +997,15 @@ void orc_residual_at(const orc_problem* P, const double* U, const long* idx, lon
 {
     orc_init();
     int K = nmodes(P);
+    const int KK = K * ncomp(P);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
     for (long t = 0; t < n; ++t) {
-        double Le[ORC_MAXK];
-        residual_elem(P, U, idx[t], Le, NULL);
-        for (int k = 0; k < K; ++k) out[k * n + t] = Le[k];
+        double Le[3 * ORC_MAXK];
+        if (P->flux == ORC_FLUX_EULER) euler_residual_elem(P, U, idx[t], Le, NULL);
+        else residual_elem(P, U, idx[t], Le, NULL);
+        for (int k = 0; k < KK; ++k) out[k * n + t] = Le[k];
     }
 }
 

@@ -29,8 +29,8 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2}
-FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3}
+BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3}
+FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3, "euler": 4}
 STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 
 
@@ -62,7 +62,7 @@ class _Problem(ctypes.Structure):
         ("stab", ctypes.c_int),
         ("q", ctypes.c_double), ("b", ctypes.c_double), ("w_nbr", ctypes.c_double),
         ("eps_w", ctypes.c_double), ("eps_s", ctypes.c_double),
-        ("theta", ctypes.c_double),
+        ("theta", ctypes.c_double), ("gas_gamma", ctypes.c_double),
     ]
 
 
@@ -87,6 +87,7 @@ class Problem:
     eps_w: float = 1e-6
     eps_s: float = 1e-12
     theta: float = 1.0
+    gas_gamma: float = 1.4
 
     @property
     def E(self) -> int:
@@ -94,7 +95,8 @@ class Problem:
 
     @property
     def K(self) -> int:
-        return (self.p + 1) ** self.dim
+        """Rows of the state: modes per element, times 3 components for the Euler system."""
+        return (self.p + 1) ** self.dim * (3 if self.flux == "euler" else 1)
 
     @property
     def h(self) -> float:
@@ -113,6 +115,7 @@ class Problem:
         s.stab = STAB[self.stab]
         s.q, s.b, s.w_nbr, s.eps_w, s.eps_s = self.q, self.b, self.w_nbr, self.eps_w, self.eps_s
         s.theta = self.theta
+        s.gas_gamma = self.gas_gamma
         return s
 
 
@@ -141,6 +144,7 @@ def lib():
             L.orc_candidate.argtypes = [pp, dp, ctypes.c_long, ctypes.c_int, dp]
             L.orc_llf.argtypes = [pp] + [ctypes.c_double] * 6
             L.orc_llf.restype = ctypes.c_double
+            L.orc_euler_llf.argtypes = [pp, dp, dp, ctypes.c_double, dp]
             L.orc_wave_speed.argtypes = [pp] + [ctypes.c_double] * 6
             L.orc_wave_speed.restype = ctypes.c_double
             L.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
@@ -250,7 +254,13 @@ def gauss_legendre(n: int):
 
 
 def project(P: Problem, samples, nq: int = 8) -> np.ndarray:
-    """L2 projection of samples given at the nq-point Gauss points of every element."""
+    """L2 projection of samples given at the nq-point Gauss points of every element
+    (Euler system: samples of (rho, rho v, rho E), shape (3, E * nq), one component after
+    the other)."""
+    if P.flux == "euler":
+        f = np.asarray(samples, dtype=np.float64).reshape(3, -1)
+        Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b == "reflect" else b for b in P.bc))
+        return np.concatenate([project(Ps, f[c], nq) for c in range(3)], axis=0)
     c = _checked(P)
     f = np.ascontiguousarray(np.asarray(samples, dtype=np.float64)).reshape(-1)
     if f.size != P.E * nq ** P.dim:
@@ -294,6 +304,17 @@ def candidate(P: Problem, U, e: int, face: int):
 def llf(P: Problem, um, up, x, y, nx, ny) -> float:
     c = _checked(P)
     return lib().orc_llf(ctypes.byref(c), um, up, x, y, nx, ny)
+
+
+def euler_llf(P: Problem, um, up, n: float) -> np.ndarray:
+    """LLF flux of the Euler system between conservative states um (own) and up across a
+    face of outward normal n = +-1 (reading R15)."""
+    c = _checked(P)
+    a = np.ascontiguousarray(np.asarray(um, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(up, dtype=np.float64))
+    H = np.zeros(3)
+    lib().orc_euler_llf(ctypes.byref(c), _ptr(a), _ptr(b), float(n), _ptr(H))
+    return H
 
 
 def wave_speed(P: Problem, um, up, x, y, nx, ny) -> float:

@@ -224,3 +224,64 @@ def nsteps_to(t_end: float, dt: float):
     if last < 1e-12 * dt:
         return n, dt, 0.0
     return n, dt, last
+
+
+# --------------------------------------------------------------------------------------
+# Shock tubes of the Euler system (Sec. 5.6), primitive states (rho, v, p), gamma = 1.4
+# --------------------------------------------------------------------------------------
+# Where the paper does not give the diaphragm position it is read as the usual one of
+# each problem (Sod, Lax: the centre; modified Sod: x = 0.3; Shu-Osher: x = -4; blast
+# wave: x = 0.1 and x = 0.9).  "lam" bounds |v| + c over the solution and sets the time
+# step; an inlet is read as a zero-gradient boundary, exact here because the state at
+# the inlet stays at its initial value up to t_end.
+SHOCK_TUBES = {
+    "sod": dict(box=(0.0, 1.0), jumps=(0.5,), states=((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)),
+                bc=("reflect", "reflect"), t_end=0.231, nx=128, p=2, lam=2.5),
+    "sod_modified": dict(box=(0.0, 1.0), jumps=(0.3,), states=((1.0, 0.75, 1.0), (0.125, 0.0, 0.1)),
+                         bc=("outflow", "reflect"), t_end=0.2, nx=128, p=2, lam=2.5),
+    "lax": dict(box=(0.0, 2.0), jumps=(1.0,), states=((0.445, 0.698, 3.528), (0.5, 0.0, 0.571)),
+                bc=("outflow", "outflow"), t_end=0.14, nx=512, p=2, lam=5.0),
+    "shu_osher": dict(box=(-5.0, 5.0), jumps=(-4.0,), states=((3.857143, 2.629369, 10.3333), "sine"),
+                      bc=("outflow", "reflect"), t_end=1.8, nx=512, p=2, lam=5.0),
+    "blast": dict(box=(0.0, 1.0), jumps=(0.1, 0.9),
+                  states=((1.0, 0.0, 1000.0), (1.0, 0.0, 0.1), (1.0, 0.0, 100.0)),
+                  bc=("reflect", "reflect"), t_end=0.038, nx=512, p=2, lam=60.0),
+}
+
+GAS_GAMMA = 1.4
+
+
+def shock_tube_primitive(name: str, x):
+    """(rho, v, p) of the initial data at the points x (any shape)."""
+    d = SHOCK_TUBES[name]
+    x = np.asarray(x, dtype=np.float64)
+    region = np.zeros(x.shape, dtype=np.int64)
+    for j in d["jumps"]:
+        region += (x >= j).astype(np.int64)
+    out = np.zeros((3,) + x.shape)
+    for r, st in enumerate(d["states"]):
+        sel = region == r
+        if isinstance(st, str):        # Shu-Osher: density wave ahead of the shock
+            out[0][sel] = 1.0 + 0.2 * np.sin(5.0 * x[sel])
+            out[1][sel] = 0.0
+            out[2][sel] = 1.0
+        else:
+            for c in range(3):
+                out[c][sel] = st[c]
+    return out
+
+
+def shock_tube_samples(name: str, nx: int, nq: int = 8, gamma: float = GAS_GAMMA):
+    """Conservative samples (rho, rho v, rho E) at the projection points of a 1D mesh of
+    nx elements, shape (3, nx * nq)."""
+    d = SHOCK_TUBES[name]
+    X, _ = sample_points(1, nx, 1, (d["box"][0], d["box"][1], 0.0, 1.0), nq)
+    rho, v, p = shock_tube_primitive(name, X.reshape(-1))
+    return np.stack([rho, rho * v, p / (gamma - 1.0) + 0.5 * rho * v * v])
+
+
+def euler_cfl(p: int) -> float:
+    """Courant number of the Euler workloads, dt = cfl h / lam: inside the SSP-RK3
+    stability interval of the stabilization term for gamma = 1 (radius 6, 15, 28.3 times
+    lam dt / h for p = 1, 2, 3)."""
+    return {1: 0.2, 2: 0.1, 3: 0.05}[p]

@@ -246,3 +246,76 @@ def residual(P, U):
                 Mkk *= (m.h / 2) * 2 / (2 * j + 1)
             L[k, e] = R[k] / Mkk
     return L
+
+
+# ---------------------------------------------------------------------------------
+# 1D Euler system (Sec. 5.6): U = (rho, rho v, rho E), p = (gamma - 1)(rho E - rho v^2/2)
+# ---------------------------------------------------------------------------------
+def _euler_F(g, q):
+    rho, m, en = q
+    v = m / rho
+    pr = (g - 1.0) * (en - 0.5 * m * v)
+    return np.array([m, m * v + pr, (en + pr) * v])
+
+
+def _euler_speed(g, q):
+    rho, m, en = q
+    v = m / rho
+    pr = (g - 1.0) * (en - 0.5 * m * v)
+    return np.abs(v) + np.sqrt(g * pr / rho)
+
+
+def euler_residual(P, U):
+    """Euler residual of a 1D mesh.  The volume flux integral uses the (p+2)-point Gauss
+    rule of the scheme (the flux is not a polynomial, so the rule is part of the method);
+    every polynomial integral uses the 24-point rule.  The sensor is the scalar one
+    applied to the density."""
+    import dataclasses
+    m = Mesh(dataclasses.replace(P, flux="advect"))
+    E, n1, g = P.E, P.p + 1, P.gas_gamma
+    Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b == "reflect" else b for b in P.bc))
+    if P.stab in ("weno", "zhao"):
+        gam = sensor(Ps, U[:n1])
+    else:
+        gam = np.full(E, 1.0 if P.stab == "lo" else 0.0)
+    gq, wq = npleg.leggauss(P.p + 2)
+    L = np.zeros((3 * n1, E))
+    for e in range(E):
+        c = m.centre(e)
+        ce = [U[comp * n1:(comp + 1) * n1, e] for comp in range(3)]
+        xs = c[0] + 0.5 * m.h * gq
+        q = np.array([m.poly(ce[comp], 0, 0, c, xs, 0 * xs) for comp in range(3)])
+        F = _euler_F(g, q)
+        R = np.zeros((3, n1))
+        for k in range(n1):
+            R[:, k] = (F * m.basis(k, 1, 0, c, xs, 0 * xs) * 0.5 * m.h * wq).sum(axis=1)
+        ends = np.array([c[0] - 0.5 * m.h, c[0] + 0.5 * m.h])
+        lam = max(np.max(_euler_speed(g, q)),
+                  np.max(_euler_speed(g, np.array([m.poly(ce[comp], 0, 0, c, ends, 0 * ends)
+                                                   for comp in range(3)]))))
+        for f in range(2):
+            n = -1.0 if f == 0 else 1.0
+            fx = np.array([c[0] + 0.5 * m.h * n])
+            um = np.array([m.poly(ce[comp], 0, 0, c, fx, 0 * fx)[0] for comp in range(3)])
+            nb, cn = m.nbr(e, f)
+            if nb is not None:
+                up = np.array([m.poly(U[comp * n1:(comp + 1) * n1, nb], 0, 0, cn, fx, 0 * fx)[0]
+                               for comp in range(3)])
+            elif P.bc[f] == "reflect":
+                up = np.array([um[0], -um[1], um[2]])
+            else:
+                up = um.copy()
+            s = max(_euler_speed(g, um), _euler_speed(g, up))
+            H = 0.5 * n * (_euler_F(g, um) + _euler_F(g, up)) - 0.5 * s * (up - um)
+            for k in range(n1):
+                R[:, k] -= m.basis(k, 0, 0, c, fx, 0 * fx)[0] * H
+        if gam[e] != 0.0:
+            nu = (P.lambda_nu if P.lambda_nu > 0 else lam) * m.h / (2 * P.p)
+            X, Y, W = m.vol_pts(e)
+            for comp in range(3):
+                ux = m.poly(ce[comp], 1, 0, c, X, Y)
+                for k in range(n1):
+                    R[comp, k] -= gam[e] * nu * np.sum(W * m.basis(k, 1, 0, c, X, Y) * ux)
+        for k in range(n1):
+            L[k::n1, e] = R[:, k] / (m.h / (2 * k + 1))
+    return L
