@@ -8,13 +8,16 @@
  * (Eq. fesol; Q_p on quadrilaterals), the local Lax-Friedrichs flux (Sec. 2), the
  * dissipative stabilization gamma_e nu_e int grad(phi).grad(U_h) (Sec. 3, Eq. astab,
  * with Eq. visc for nu_e) driven by the WENO sensor of Sec. 4 (Eq. sensor / gensensor),
- * and advanced by the optimal SSP-RK3 scheme (Eq. ssp).
+ * and advanced by the optimal SSP-RK3 scheme (Eq. ssp).  In 1D also the Euler equations
+ * of gas dynamics (Sec. 5.6) with the same scheme and a density-driven sensor.
  *
  * Conventions shared by every entry point
  *  - State arrays ("U") are device arrays owned by the caller, mode-major
  *    (structure of arrays): U[k*E + e] with element e = iy*nx + ix and mode
  *    k = i + (p+1)*j (i: Legendre degree in x, j: in y; 1D: k = i).  K = (p+1)^dim
- *    modes, E = nx (1D) or nx*ny (2D) elements.  The element type is double for
+ *    modes, E = nx (1D) or nx*ny (2D) elements.  The Euler system stacks its three
+ *    components: row comp*(p+1) + k holds mode k of rho (comp 0), rho v (1) and
+ *    rho E (2), so K = 3(p+1) rows.  The element type is double for
  *    DGW_FP64 contexts and float for DGW_FP32 contexts.  Base addresses must be
  *    aligned to 16 bytes.
  *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
@@ -50,8 +53,11 @@ typedef enum {
 /* Boundary treatment of one side of the box (Sec. 2: weak inflow conditions). */
 typedef enum {
     DGW_BC_PERIODIC = 0,
-    DGW_BC_INFLOW_ZERO = 1, /* ghost U+ = 0 where F'(U-).n < 0, U+ = U- elsewhere */
-    DGW_BC_OUTFLOW = 2      /* ghost U+ = U- */
+    DGW_BC_INFLOW_ZERO = 1, /* ghost U+ = 0 where F'(U-).n < 0, U+ = U- elsewhere
+                               (scalar laws only) */
+    DGW_BC_OUTFLOW = 2,     /* ghost U+ = U- */
+    DGW_BC_REFLECT = 3      /* Euler system only: reflecting wall, ghost (rho, -rho v, rho E)
+                               (Sec. 5.6 shock tubes) */
 } dgw_bc;
 
 /* Cartesian mesh of [x0,x1] (1D) or [x0,x1]x[y0,y1] (2D) with nx (x ny) equal cells.
@@ -69,7 +75,14 @@ typedef enum {
     DGW_FLUX_ADVECT = 0,    /* F = (a0, a1) u                                  */
     DGW_FLUX_ROTATION = 1,  /* F = omega (cy - y, x - cx) u   (solid body)      */
     DGW_FLUX_BURGERS = 2,   /* F = (a0, a1) u^2 / 2                            */
-    DGW_FLUX_KPP = 3        /* F = (sin u, cos u)                              */
+    DGW_FLUX_KPP = 3,       /* F = (sin u, cos u)                              */
+    DGW_FLUX_EULER = 4      /* 1D Euler system (Sec. 5.6): U = (rho, rho v, rho E),
+                               F = (rho v, rho v^2 + p, (rho E + p) v),
+                               p = (gas_gamma - 1)(rho E - rho v^2 / 2); the LLF speed
+                               s+ is the larger |v| + c of the two states; the sensor is
+                               computed from the density and applied to all three
+                               components; no positivity safeguard: a negative density
+                               or pressure gives non-finite results (dgw_sync_status) */
 } dgw_flux_kind;
 
 typedef struct {
@@ -79,7 +92,10 @@ typedef struct {
     double omega;
     double lambda_nu;       /* > 0: fixed lambda_e in nu_e = lambda_e h / (2p) (the paper
                                uses 2.0 for KPP); 0: max |F'(U_h)|_2 over the element's
-                               volume and face Gauss points */
+                               volume and face Gauss points (Euler: max |v| + c over the
+                               p+2 Gauss points and the two end points) */
+    double gas_gamma;       /* Euler system: ratio of heat capacities (> 1; the paper and
+                               dgw_defaults use 1.4); ignored by the scalar fluxes */
 } dgw_flux;
 
 typedef enum { DGW_STAB_DG = 0, DGW_STAB_LO = 1, DGW_STAB_WENO = 2, DGW_STAB_ZHAO = 3 } dgw_stab;
@@ -117,7 +133,9 @@ typedef struct dgw_ctx dgw_ctx;
  * Any argument may be NULL. */
 void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s);
 
-/* Creates a context for degree p (1..3) on the current device: checks the arguments,
+/* Creates a context for degree p (1..3) on the current device: checks the arguments
+ * (DGW_FLUX_EULER: 1D meshes only, else DGW_EUNSUPPORTED; DGW_BC_REFLECT only with it and
+ * DGW_BC_INFLOW_ZERO only without it, else DGW_EINVAL),
  * builds the operator tables (Gauss rule of p+2 points, Legendre values, Hermite
  * shift matrices, seminorm Gram matrix, stiffness) in double, uploads them, and
  * allocates the two RK stage buffers (2*K*E elements) plus small scratch.
@@ -139,7 +157,8 @@ dgw_status dgw_set_params(dgw_ctx* ctx, const dgw_params* params);
 /* L2 projection of initial data onto V_p (Sec. 2, Eq. fesol).  samples (device,
  * double, E * nq^dim values): f at the nq-point Gauss-Legendre points of each
  * element, sample t = a + nq*b at x = xc + h/2 g_a, y = yc + h/2 g_b.  nq in 1..8.
- * U (device, context precision, K*E) receives c_k = int f phi_k / int phi_k^2. */
+ * U (device, context precision, K*E) receives c_k = int f phi_k / int phi_k^2.  Euler
+ * system: 3 * E * nq samples, those of rho, rho v and rho E one after the other. */
 dgw_status dgw_project(dgw_ctx* ctx, int nq, const double* samples, void* U, void* stream);
 
 /* Semi-discrete right-hand side L = M^{-1} R_stab(U) (Eq. weak2 with s_h^e of Sec. 3):
@@ -168,7 +187,7 @@ dgw_status dgw_rk_step(dgw_ctx* ctx, void* U, double dt, int nsteps, void* strea
 dgw_status dgw_rk_step_host(dgw_ctx* ctx, const void* U_in, void* U_out, double dt,
                             int nsteps, void* stream);
 
-/* Total mass sum_e int_{K_e} U_h dx = sum_e |K_e| c_0^e in double, by a fixed-order
+/* Total mass sum_e int_{K_e} U_h dx = sum_e |K_e| c_0^e (Euler: of the density) in double, by a fixed-order
  * tree (bitwise reproducible).  Blocks until the result is on the host. */
 dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream);
 
@@ -182,7 +201,8 @@ dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
  * other contexts return DGW_EUNSUPPORTED.  Non-smooth points use subgradients:
  * d min(1, r)/dr = [r < 1], d|x| = sign(x) (sign(0) = 0), a maximum picks its first
  * maximising argument, and the eps_s guard / b threshold are constant pieces.  The
- * context allocates 4 + 2*dim state-sized buffers on first use.
+ * context allocates 4 + 2*dim state-sized buffers on first use.  The Euler system and
+ * the ZHAO sensor return DGW_EUNSUPPORTED.
  * ---------------------------------------------------------------------------------- */
 
 /* out = J_L(U)^T lam, the transpose Jacobian of L = M^{-1} R_stab (Eq. weak2 with the
@@ -208,7 +228,8 @@ dgw_status dgw_misfit(dgw_ctx* ctx, const void* U, const void* U_target, double*
  * above.  One persistent kernel per dimension (cooperative launch) takes work items
  * (stage, instance, chunk of tiles) in order; an item waits, with a bounded spin, only
  * for its own instance's previous stage, so instances of different sizes overlap.
- * Fluxes: advection and Burgers.  Stabilization parameters and precision are common.
+ * Fluxes: advection and Burgers (others return DGW_EUNSUPPORTED; reflecting walls
+ * DGW_EINVAL).  Stabilization parameters and precision are common.
  * ---------------------------------------------------------------------------------- */
 typedef struct dgw_batch dgw_batch;
 
@@ -263,7 +284,8 @@ dgw_status dgw_batch_debug(dgw_batch* b, long long wait_limit, int unreachable);
  * enqueue kernels on the stream.  All calls share the array, so calls whose work
  * overlaps on the GPU (other streams, other threads) race and corrupt each other:
  * order them on one stream.  Non-finite results are not reported by this entry
- * point (there is no context to hold the flag). */
+ * point (there is no context to hold the flag).  Scalar laws only: the Euler system
+ * returns DGW_EUNSUPPORTED. */
 dgw_status dgw_rk_step_noalloc(const dgw_mesh* mesh, int p, const dgw_flux* flux,
                                const dgw_params* params, void* U, double dt, int nsteps,
                                void* stream);

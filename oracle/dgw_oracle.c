@@ -51,6 +51,9 @@
  *      U[(comp (p+1) + k) E + e].  s+ of the LLF flux is read as the larger of |v| + c at
  *      the two states (the maximum along the path in conservative variables has no
  *      closed form); lambda_e = max (|v| + c) over the element's volume and face points.
+ *      A state without a real sound speed (rho <= 0 or p < 0) has no wave speed: s+ and
+ *      lambda_e are then NaN, so that the step returns non-finite values rather than
+ *      finite ones built on an undefined speed.
  *      Reflecting walls mirror the state: (rho, -rho v, rho E).  The sensor uses the
  *      density alone, applied to all components; beyond a wall, as beyond any
  *      non-periodic boundary, there is no neighbour candidate.
@@ -644,7 +647,7 @@ static void euler_llf(const orc_problem* P, const double um[3], const double up[
     euler_flux(P, um, Fm);
     euler_flux(P, up, Fp);
     double sm = euler_speed(P, um), sp = euler_speed(P, up);
-    double s = sm > sp ? sm : sp;
+    double s = (isnan(sm) || isnan(sp)) ? NAN : (sm > sp ? sm : sp);
     for (int c = 0; c < 3; ++c) H[c] = n * 0.5 * (Fm[c] + Fp[c]) - 0.5 * s * (up[c] - um[c]);
 }
 
@@ -670,7 +673,8 @@ static double euler_lambda_elem(const orc_problem* P, long e, double ce[3][ORC_M
         double r = t < nv ? qr[t] : (t == nv ? -1.0 : 1.0), q[3];
         for (int c = 0; c < 3; ++c) q[c] = poly_d(P, ce[c], 0, 0, r, 0.0);
         double sp = euler_speed(P, q);
-        if (sp > lam) lam = sp;
+        if (isnan(sp) || isnan(lam)) lam = NAN;
+        else if (sp > lam) lam = sp;
     }
     return lam;
 }

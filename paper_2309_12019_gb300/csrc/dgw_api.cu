@@ -100,7 +100,7 @@ extern "C" void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s)
     if (f) {
         std::memset(f, 0, sizeof *f);
         f->kind = DGW_FLUX_ADVECT; f->a[0] = 1.0; f->a[1] = 0.0;
-        f->center[0] = f->center[1] = 0.5; f->omega = 1.0; f->lambda_nu = 0.0;
+        f->center[0] = f->center[1] = 0.5; f->omega = 1.0; f->lambda_nu = 0.0; f->gas_gamma = 1.4;
     }
     if (s) {
         std::memset(s, 0, sizeof *s);
@@ -135,7 +135,7 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
     if (m.nx < 1 || (m.dim == 2 && m.ny < 1)) return fail(DGW_EINVAL, "nx, ny must be >= 1");
     if (!(m.x1 > m.x0) || (m.dim == 2 && !(m.y1 > m.y0))) return fail(DGW_EINVAL, "empty box");
     for (int f = 0; f < 2 * m.dim; ++f)
-        if (m.bc[f] < DGW_BC_PERIODIC || m.bc[f] > DGW_BC_OUTFLOW) return fail(DGW_EINVAL, "bad bc[%d]", f);
+        if (m.bc[f] < DGW_BC_PERIODIC || m.bc[f] > DGW_BC_REFLECT) return fail(DGW_EINVAL, "bad bc[%d]", f);
     for (int a = 0; a < m.dim; ++a)
         if ((m.bc[2 * a] == DGW_BC_PERIODIC) != (m.bc[2 * a + 1] == DGW_BC_PERIODIC))
             return fail(DGW_EINVAL, "periodic sides must come in pairs");
@@ -145,8 +145,16 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
         if (std::fabs(hx - hy) > 1e-12 * hx) return fail(DGW_EUNSUPPORTED, "2D cells must be square");
     }
     if (p < 1 || p > kMaxP) return fail(DGW_EUNSUPPORTED, "degree p=%d not built (1..3)", p);
-    if (flux->kind < DGW_FLUX_ADVECT || flux->kind > DGW_FLUX_KPP) return fail(DGW_EINVAL, "bad flux kind");
+    if (flux->kind < DGW_FLUX_ADVECT || flux->kind > DGW_FLUX_EULER) return fail(DGW_EINVAL, "bad flux kind");
     if (!(flux->lambda_nu >= 0.0)) return fail(DGW_EINVAL, "lambda_nu must be >= 0");
+    const bool euler = flux->kind == DGW_FLUX_EULER;
+    for (int f = 0; f < 2 * m.dim; ++f) {
+        if (m.bc[f] == DGW_BC_REFLECT && !euler) return fail(DGW_EINVAL, "bc[%d]: reflecting walls are for the Euler system", f);
+        if (m.bc[f] == DGW_BC_INFLOW_ZERO && euler) return fail(DGW_EINVAL, "bc[%d]: inflow_zero is for scalar laws", f);
+    }
+    if (euler && m.dim != 1) return fail(DGW_EUNSUPPORTED, "the Euler system is built for 1D meshes");
+    if (euler && !(flux->gas_gamma > 1.0 && std::isfinite(flux->gas_gamma)))
+        return fail(DGW_EINVAL, "gas_gamma must be a finite number > 1");
     dgw_status st = check_params(params, m.dim);
     if (st != DGW_OK) return st;
     const int64_t E = m.dim == 1 ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
@@ -158,7 +166,7 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
     c->p = p;
     c->flux = *flux;
     c->params = *params;
-    c->K = m.dim == 1 ? p + 1 : (p + 1) * (p + 1);
+    c->K = (m.dim == 1 ? p + 1 : (p + 1) * (p + 1)) * (euler ? 3 : 1);
     c->E = E;
     c->eb = params->prec == DGW_FP64 ? 8 : 4;
     c->h = hx;
@@ -319,6 +327,7 @@ static StageArgs base_args(const dgw_ctx* c)
     a.eps_w = c->params.eps_w;
     a.eps_s = c->params.eps_s;
     a.theta = c->params.theta;
+    a.gas_gamma = c->flux.gas_gamma;
     a.flag = c->flag;
     return a;
 }
@@ -740,8 +749,15 @@ extern "C" dgw_status dgw_project(dgw_ctx* c, int nq, const double* samples, voi
     for (int i = 0; i <= c->p; ++i) a.minv[i] = (2 * i + 1) / 2.0;
     const int threads = 128;
     const int64_t blocks = (c->E + threads - 1) / threads;
-    project_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(a);
-    DGW_CUDA(cudaGetLastError());
+    // the Euler system: one projection per component (samples and rows component-major)
+    const int ncomp = c->flux.kind == DGW_FLUX_EULER ? 3 : 1;
+    const int64_t npt = c->mesh.dim == 1 ? nq : nq * nq;
+    for (int comp = 0; comp < ncomp; ++comp) {
+        a.f = samples + comp * c->E * npt;
+        a.U = static_cast<char*>(U) + (size_t)comp * (c->K / ncomp) * c->E * c->eb;
+        project_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(a);
+        DGW_CUDA(cudaGetLastError());
+    }
     return DGW_OK;
 }
 
@@ -1356,6 +1372,7 @@ extern "C" dgw_status dgw_rk_step_noalloc(const dgw_mesh* mesh, int p, const dgw
     if (m.dim == 2 && std::fabs(hx - (m.y1 - m.y0) / m.ny) > 1e-12 * hx)
         return fail(DGW_EUNSUPPORTED, "2D cells must be square");
     if (p < 1 || p > kMaxP) return fail(DGW_EUNSUPPORTED, "degree p=%d not built (1..3)", p);
+    if (flux->kind == DGW_FLUX_EULER) return fail(DGW_EUNSUPPORTED, "dgw_rk_step_noalloc is built for the scalar laws");
     if (flux->kind < DGW_FLUX_ADVECT || flux->kind > DGW_FLUX_KPP) return fail(DGW_EINVAL, "bad flux kind");
     if (!(flux->lambda_nu >= 0.0)) return fail(DGW_EINVAL, "lambda_nu must be >= 0");
     dgw_status st = check_params(params, m.dim);

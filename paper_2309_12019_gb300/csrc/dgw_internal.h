@@ -26,8 +26,8 @@ constexpr int stage_lanes(bool f64) { return f64 ? 1 : 2; }
 constexpr int stage_thread_rows(bool f64) { return f64 ? kTileY2 : 2 * kTileY2; }
 constexpr int stage_rows(bool f64) { return stage_thread_rows(f64) * stage_lanes(f64); }
 
-enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2 };
-enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3 };
+enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2, BC_REFLECT = 3 };
+enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3, FLUX_EULER = 4 };
 enum : int { STAB_DG = 0, STAB_LO = 1, STAB_WENO = 2, STAB_ZHAO = 3 };
 
 // Operator tables of degree p, built once in double on the host (dgw_tables.cu) and
@@ -64,6 +64,7 @@ struct StageArgs {
     double a0, a1, cx, cy, omega, lambda_nu;
     int stab;
     double q, b, w_nbr, eps_w, eps_s, theta;
+    double gas_gamma;      // Euler system: ratio of heat capacities
     double* gamma_out;     // optional per-element gamma (double)
     unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x (stage_rows + 2) x K), or null

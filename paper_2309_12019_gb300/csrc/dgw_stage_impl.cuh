@@ -130,6 +130,7 @@ struct alignas(64) KParams {
     Real q, b, w_nbr, eps_w, eps_s;
     Real theta;          // exponent of the Zhao et al. sensor (stab == STAB_ZHAO)
     int theta_one;       // theta == 1
+    Real gam, gm1;       // Euler system: gamma and gamma - 1
     Real cn, ck, cl;
 };
 
@@ -1005,6 +1006,8 @@ static KParams make_params(const StageArgs& s)
     a.eps_s = (Real)s.eps_s;
     a.theta = (Real)s.theta;
     a.theta_one = s.theta == 1.0;
+    a.gam = (Real)s.gas_gamma;
+    a.gm1 = (Real)(s.gas_gamma - 1.0);
     a.cn = (Real)s.cn; a.ck = (Real)s.ck; a.cl = (Real)s.cl;
     return a;
 }
@@ -1221,6 +1224,10 @@ static cudaError_t launch_gather(const GatherArgs& g, int p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+#if DGW_DIM == 1
+#include "dgw_euler_impl.cuh"
+#endif
+
 template <int P, int FLUX>
 static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
 {
@@ -1263,6 +1270,11 @@ static cudaError_t launch_p(const StageArgs& a, int flux, int mode, cudaStream_t
 
 static cudaError_t launch(const StageArgs& a, int p, int flux, int mode, cudaStream_t s)
 {
+#if DGW_DIM == 1
+    if (flux == FLUX_EULER) return launch_euler(a, p, mode, s);
+#else
+    if (flux == FLUX_EULER) return cudaErrorInvalidValue;
+#endif
     switch (p) {
     case 1: return launch_p<1>(a, flux, mode, s);
     case 2: return launch_p<2>(a, flux, mode, s);

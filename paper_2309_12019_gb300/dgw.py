@@ -17,8 +17,8 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2}
-FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3}
+BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3}
+FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3, "euler": 4}
 STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 PREC = {"fp64": 0, "fp32": 1}
 
@@ -41,7 +41,7 @@ class Mesh(ctypes.Structure):
 
 class Flux(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double * 2), ("center", ctypes.c_double * 2),
-                ("omega", ctypes.c_double), ("lambda_nu", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("lambda_nu", ctypes.c_double), ("gas_gamma", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -127,7 +127,8 @@ def _ptr(t):
 
 @dataclasses.dataclass
 class Problem:
-    """Mesh, degree, flux and stabilization of one scalar conservation law (host side)."""
+    """Mesh, degree, flux and stabilization of one scalar conservation law, or of the 1D
+    Euler system (flux "euler"), host side."""
     dim: int
     nx: int
     p: int
@@ -148,14 +149,20 @@ class Problem:
     prec: str = "fp64"
     theta: float = 1.0
     rk_order: int = 3
+    gas_gamma: float = 1.4
 
     @property
     def E(self) -> int:
         return self.nx * (self.ny if self.dim == 2 else 1)
 
     @property
+    def ncomp(self) -> int:
+        return 3 if self.flux == "euler" else 1
+
+    @property
     def K(self) -> int:
-        return (self.p + 1) ** self.dim
+        """Rows of the state: modes per element (times 3 components for the Euler system)."""
+        return (self.p + 1) ** self.dim * self.ncomp
 
     def c_structs(self):
         m = Mesh()
@@ -168,6 +175,7 @@ class Problem:
         f.a[0], f.a[1] = self.a
         f.center[0], f.center[1] = self.center
         f.omega, f.lambda_nu = self.omega, self.lambda_nu
+        f.gas_gamma = self.gas_gamma
         s = Params()
         s.stab, s.q, s.b, s.w_nbr = STAB[self.stab], self.q, self.b, self.w_nbr
         s.eps_w, s.eps_s, s.prec, s.theta = self.eps_w, self.eps_s, PREC[self.prec], self.theta
@@ -219,6 +227,9 @@ class Context:
         import torch
         if samples.dtype != torch.float64 or not samples.is_cuda or not samples.is_contiguous():
             raise ValueError("samples must be a contiguous CUDA float64 tensor")
+        P = self.problem
+        if samples.numel() != P.ncomp * self.E * nq ** P.dim:
+            raise ValueError(f"expected {P.ncomp} x {self.E} x {nq ** P.dim} samples")
         _check(load().dgw_project(self._h, nq, _ptr(samples), self._state(U), _stream(stream)))
 
     def residual(self, U, L, stream=None):

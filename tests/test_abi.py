@@ -46,6 +46,12 @@ def _create(**kw):
     (dict(bc=("periodic", "outflow", "periodic", "periodic")), -1),
     (dict(b=1.5), -1), (dict(q=0.0), -1), (dict(w_nbr=0.3), -1), (dict(eps_w=0.0), -1),
     (dict(lambda_nu=-1.0), -1),
+    # the Euler system: 1D only, reflecting walls only with it, inflow_zero only without
+    (dict(flux="euler"), -4),
+    (dict(dim=1, bc=("reflect", "reflect", "periodic", "periodic")), -1),
+    (dict(dim=1, flux="euler", bc=("inflow_zero", "outflow", "periodic", "periodic")), -1),
+    (dict(dim=1, flux="euler", gas_gamma=1.0), -1),
+    (dict(dim=1, flux="euler", gas_gamma=float("nan")), -1),
 ])
 def test_bad_arguments_rejected(kw, status):
     rc, msg = _create(**kw)
@@ -64,3 +70,4 @@ def test_defaults():
     m, f, s = dgw.Mesh(), dgw.Flux(), dgw.Params()
     L.dgw_defaults(ctypes.byref(m), ctypes.byref(f), ctypes.byref(s))
     assert (m.dim, s.stab, s.q, s.b, s.w_nbr, s.eps_w) == (1, 2, 1.0, 0.0, 1e-2, 1e-6)
+    assert f.gas_gamma == 1.4

@@ -1,0 +1,224 @@
+"""Parity of the 1D Euler kernel (Sec. 5.6) with the FP64 oracle, through the C ABI.
+
+Bars (written in each test): FP64 residuals, sensors and short RK3 runs to 1e-12
+relative L2 (|d gamma| <= 1e-12); the full Sod run (about 2200 stages) to 1e-9, the
+rounding differences of that many nonlinear stages; FP32 residuals on float-rounded
+input to 1e-5 relative L2 per component, FP32 RK3 runs to 2e-5.  Meshes of 300 cells
+span three 128-cell tiles and a ragged tail.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import helpers as H
+from paper_2309_12019_gb300 import dgw
+from paper_2309_12019_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+BCS = {"periodic": ("periodic", "periodic"), "reflect": ("reflect", "reflect"),
+       "wall_out": ("reflect", "outflow"), "outflow": ("outflow", "outflow")}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dgw.load()
+
+
+def spec(p, nx=300, stab="weno", bc="wall_out", box=None, **kw):
+    box = box or (0.0, 1.0)
+    return dict(dim=1, nx=nx, p=p, box=(box[0], box[1], 0.0, 1.0), bc=BCS[bc] + ("periodic", "periodic"),
+                flux="euler", stab=stab, **kw)
+
+
+def ctx_for(s, prec="fp64"):
+    return dgw.Context(dgw.Problem(**s, prec=prec))
+
+
+def dev(U, prec):
+    return torch.tensor(U, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda").contiguous()
+
+
+def residual(ctx, U):
+    Ud = dev(U, ctx.problem.prec)
+    L = torch.empty_like(Ud)
+    ctx.residual(Ud, L)
+    torch.cuda.synchronize()
+    return L.double().cpu().numpy()
+
+
+def per_comp_rel(got, ref, p):
+    n1 = p + 1
+    return max(H.rel_l2(got[c * n1:(c + 1) * n1], ref[c * n1:(c + 1) * n1]) for c in range(3))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "lo", "weno", "zhao"])
+@pytest.mark.parametrize("bc", sorted(BCS))
+def test_residual_fp64(oracle_mod, p, stab, bc):
+    s = spec(p, stab=stab, bc=bc)
+    U = I.random_euler_state(p, s["nx"], seed=10 * p + len(stab) + len(bc), amp=0.1)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    assert per_comp_rel(residual(ctx_for(s), U), ref, p) <= 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["weno", "zhao"])
+def test_sensor_fp64(oracle_mod, p, stab):
+    s = spec(p, stab=stab, bc="reflect")
+    U = I.random_euler_state(p, s["nx"], seed=40 + p, amp=0.1)
+    ref = oracle_mod.sensor(oracle_mod.Problem(**s), U)[0]
+    ctx = ctx_for(s)
+    g = torch.empty(ctx.E, dtype=torch.float64, device="cuda")
+    ctx.sensor(dev(U, "fp64"), g)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(g.cpu().numpy() - ref)) <= 1e-12
+    assert np.mean(ref > 1e-3) > 0.05
+
+
+def test_fixed_lambda_fp64(oracle_mod):
+    s = spec(2, stab="lo", bc="periodic", lambda_nu=3.0)
+    U = I.random_euler_state(2, s["nx"], seed=3, amp=0.1)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    assert per_comp_rel(residual(ctx_for(s), U), ref, 2) <= 1e-12
+
+
+@pytest.mark.parametrize("p,bc,rk", [(1, "reflect", 3), (2, "wall_out", 3), (3, "periodic", 3),
+                                      (2, "reflect", 2), (2, "outflow", 4)])
+def test_rk_fp64_random(oracle_mod, p, bc, rk):
+    s = spec(p, stab="weno", bc=bc)
+    U = I.random_euler_state(p, s["nx"], seed=60 + p, amp=0.05)
+    dt = I.euler_cfl(p) / s["nx"] / 3.0
+    ref = oracle_mod.rk(oracle_mod.Problem(**s), U, dt, 6, rk)
+    ctx = dgw.Context(dgw.Problem(**s, prec="fp64", rk_order=rk))
+    Ud = dev(U, "fp64")
+    ctx.rk_step(Ud, dt, 6)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert per_comp_rel(Ud.cpu().numpy(), ref, p) <= 1e-12
+
+
+def _shock_tube(name, nx, p):
+    d = I.SHOCK_TUBES[name]
+    s = spec(p, nx=nx, stab="weno", bc="reflect", box=d["box"])
+    s["bc"] = tuple(d["bc"]) + ("periodic", "periodic")
+    n, dt, last = I.nsteps_to(d["t_end"], I.euler_cfl(p) * (d["box"][1] - d["box"][0]) / nx / d["lam"])
+    return s, n, dt, last
+
+
+def test_sod_fp64_full_run(oracle_mod):
+    """Sod's problem at the paper's size (128 cells, p = 2) to t = 0.231: device
+    projection and every step against the oracle."""
+    s, n, dt, last = _shock_tube("sod", 128, 2)
+    f = I.shock_tube_samples("sod", 128, 8)
+    P = oracle_mod.Problem(**s)
+    U0 = oracle_mod.project(P, f, 8)
+    ctx = ctx_for(s)
+    Ud = torch.empty((ctx.K, ctx.E), dtype=torch.float64, device="cuda")
+    ctx.project(torch.tensor(f, device="cuda").contiguous(), Ud, 8)
+    torch.cuda.synchronize()
+    assert H.rel_l2(Ud.cpu().numpy(), U0) <= 1e-14
+    ref = oracle_mod.rk3(P, U0, dt, n)
+    ctx.rk_step(Ud, dt, n)
+    if last > 0:
+        ref = oracle_mod.rk3(P, ref, last, 1)
+        ctx.rk_step(Ud, last, 1)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert per_comp_rel(Ud.cpu().numpy(), ref, 2) <= 1e-9
+    # between reflecting walls the mass is conserved
+    assert abs(ctx.mass(Ud) - oracle_mod.mass(P, U0)) <= 1e-13
+
+
+@pytest.mark.parametrize("p,stab", [(1, "weno"), (2, "zhao"), (3, "weno"), (2, "lo")])
+def test_residual_fp32(oracle_mod, p, stab):
+    s = spec(p, stab=stab, bc="wall_out")
+    U = I.random_euler_state(p, s["nx"], seed=80 + p, amp=0.1).astype(np.float32).astype(np.float64)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    assert per_comp_rel(residual(ctx_for(s, "fp32"), U), ref, p) <= 1e-5
+
+
+@pytest.mark.parametrize("name,p", [("sod", 1), ("sod", 3), ("lax", 2)])
+def test_shock_tube_fp32_steps(oracle_mod, name, p):
+    """Twenty FP32 steps of a shock tube from its projected initial data."""
+    d = I.SHOCK_TUBES[name]
+    s, _, dt, _ = _shock_tube(name, 300, p)
+    f = I.shock_tube_samples(name, 300, 8)
+    P = oracle_mod.Problem(**s)
+    U0 = oracle_mod.project(P, f, 8).astype(np.float32).astype(np.float64)
+    ref = oracle_mod.rk3(P, U0, dt, 20)
+    ctx = ctx_for(s, "fp32")
+    Ud = dev(U0, "fp32")
+    ctx.rk_step(Ud, dt, 20)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert per_comp_rel(Ud.double().cpu().numpy(), ref, p) <= 2e-5
+    assert d["t_end"] > 20 * dt
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_host_entry_matches_device_entry(prec):
+    s = spec(2, nx=1000, bc="reflect")
+    U = I.random_euler_state(2, s["nx"], seed=5).astype(np.float64 if prec == "fp64" else np.float32)
+    ctx = ctx_for(s, prec)
+    dt = 0.02 / s["nx"]
+    Ud = dev(U, prec)
+    ctx.rk_step(Ud, dt, 4)
+    Uh = torch.tensor(U).pin_memory()
+    out = torch.empty_like(Uh).pin_memory()
+    ctx.rk_step_host(Uh, out, dt, 4)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy(), Ud.cpu().numpy())
+
+
+def test_negative_pressure_is_reported():
+    """No positivity safeguard: a state with negative pressure gives non-finite results,
+    which the stage kernel flags (a NaN from a square root, no fault)."""
+    s = spec(1, nx=200, stab="dg", bc="periodic")
+    U = I.random_euler_state(1, s["nx"], seed=9)
+    U[4, 17] = -5.0                     # rho E < rho v^2 / 2 in cell 17
+    ctx = ctx_for(s)
+    Ud = dev(U, "fp64")
+    ctx.rk_step(Ud, 1e-4, 1)
+    with pytest.raises(dgw.DGWError) as e:
+        ctx.sync_status()
+    assert e.value.status == -6
+    ctx.sync_status()                   # the flag was cleared
+
+
+def test_other_paths_refuse_the_euler_system():
+    s = spec(2, nx=64, bc="periodic")
+    ctx = ctx_for(s)
+    U = dev(I.random_euler_state(2, 64, seed=1), "fp64")
+    with pytest.raises(dgw.DGWError) as e:
+        ctx.residual_vjp(U, U.clone(), torch.empty_like(U))
+    assert e.value.status == -4
+    with pytest.raises(dgw.DGWError) as e:
+        dgw.Batch([dgw.Problem(**s)])
+    assert e.value.status == -4
+    with pytest.raises(dgw.DGWError) as e:
+        dgw.rk_step_noalloc(dgw.Problem(**s, prec="fp64"), U, 1e-3, 1)
+    assert e.value.status == -4
+
+
+@pytest.mark.parametrize("prec,p,stab", [("fp64", 2, "weno"), ("fp32", 2, "zhao"), ("fp32", 3, "weno")])
+def test_sod_train_steps(oracle_mod, prec, p, stab):
+    """Fifty steps of the Sod-train workload (a shock tube every 64 cells, periodic) on
+    4160 cells: 32 full 128-cell tiles and a ragged one of 64."""
+    nx = 4160
+    s = spec(p, nx=nx, stab=stab, bc="periodic")
+    P = oracle_mod.Problem(**s)
+    U0 = oracle_mod.project(P, I.sod_train_samples(nx), 8)
+    if prec == "fp32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    dt = I.euler_cfl(p) / nx / 2.5
+    ref = oracle_mod.rk3(P, U0, dt, 50)
+    ctx = ctx_for(s, prec)
+    Ud = dev(U0, prec)
+    ctx.rk_step(Ud, dt, 50)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert per_comp_rel(Ud.double().cpu().numpy(), ref, p) <= (1e-12 if prec == "fp64" else 2e-5)
