@@ -48,6 +48,15 @@ WORKLOADS = {
 # and with the ten-stage SSP Runge-Kutta of order 4 (order p + 1, as in Sec. 5's studies)
 WORKLOADS["kpp_1024x1024_q3_zhao"] = dict(WORKLOADS["kpp_1024x1024_q3"], stab="zhao")
 WORKLOADS["kpp_1024x1024_q3_rk4"] = dict(WORKLOADS["kpp_1024x1024_q3"], rk_order=4)
+# the 1D Euler system (Sec. 5.6): Sod's shock tube at the paper's size (128 cells, p = 2,
+# reflecting walls, to t = 0.231), and a periodic train of Sod tubes (one every 64 cells)
+# on 2^22 cells as the large-mesh workload; |v| + c <= 2.5 sets the step
+WORKLOADS["sod_128_q2"] = dict(dim=1, nx=128, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0),
+                               bc=("reflect", "reflect", "periodic", "periodic"), flux="euler", stab="weno",
+                               cfl=I.euler_cfl(2), speeds=(2.5,), u0="sod", t_end=I.SHOCK_TUBES["sod"]["t_end"])
+WORKLOADS["sod_train_4194304_q2"] = dict(dim=1, nx=1 << 22, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0),
+                                         bc=("periodic",) * 4, flux="euler", stab="weno",
+                                         cfl=I.euler_cfl(2), speeds=(2.5,), u0="sod_train")
 STAGES_PER_STEP = {2: 2, 3: 3, 4: 10}
 
 SPEC_KEYS = ("dim", "nx", "ny", "p", "box", "bc", "flux", "lambda_nu", "stab", "center", "omega", "a", "rk_order")
@@ -63,9 +72,18 @@ def initial_samples(w):
         f = I.u0_kpp(X, Y)
     elif w["u0"] == "rotation":
         f = I.u0_rotation(X, Y)
+    elif w["u0"] == "sod":
+        f = I.shock_tube_samples("sod", w["nx"], 8)
+    elif w["u0"] == "sod_train":
+        f = I.sod_train_samples(w["nx"], nq=8)
     else:
         f = I.u0_mixed_1d(X)
     return np.ascontiguousarray(f.reshape(-1))
+
+
+def dofs_of(w):
+    """State rows times cells: (p+1)^dim modes, three components for the Euler system."""
+    return w["nx"] * w["ny"] * (w["p"] + 1) ** w["dim"] * (3 if w["flux"] == "euler" else 1)
 
 
 def dt_of(w):
@@ -363,13 +381,26 @@ def run_adjoint(local, n=512, steps=200, every=20):
 
 
 def run_small(name, prec, steps, warmup, local):
-    """Throughput of one of the smaller configurations through dgw_rk_step."""
+    """Throughput of one of the smaller configurations through dgw_rk_step.  Euler
+    workloads add the stage kernel's HBM roofline: 8/3 state passes per stage launch
+    (read Uk and write Uout in every stage, read Un in two of three)."""
     w = WORKLOADS[name]
     r = run_gpu(w, prec, steps, warmup, 1, local, measure_e2e=False)
     stages = STAGES_PER_STEP[w.get("rk_order", 3)]
-    return {"workload": name, "dtype": "f64" if prec == "fp64" else "f32", "value": stages * r["N"] * steps / r["t"],
-            "unit": "DOF-updates/s", "steps": steps, "ms_per_step": 1e3 * r["t"] / steps,
-            "cell_mean_range_after": r["mean_range"]}
+    out = {"workload": name, "dtype": "f64" if prec == "fp64" else "f32", "value": stages * r["N"] * steps / r["t"],
+           "unit": "DOF-updates/s", "steps": steps, "ms_per_step": 1e3 * r["t"] / steps,
+           "cell_mean_range_after": r["mean_range"]}
+    if w["flux"] == "euler":
+        hbm, src = peaks()
+        per_launch = r["t"] / (stages * steps)
+        alg = 8.0 / 3.0 * r["N"] * (8 if prec == "fp64" else 4)
+        out["roofline"] = {"bound": "hbm", "kernel": "euler_kernel", "achieved": alg / per_launch / 1e9,
+                           "peak": hbm, "unit": "GB/s", "frac": alg / per_launch / 1e9 / hbm,
+                           "peak_source": src, "bytes_per_launch": alg, "us_per_launch": 1e6 * per_launch}
+        out["mass_after"] = r["mass"]
+    if "t_end" in w:
+        out["time_to_t_end_ms"] = 1e3 * r["t"] / steps * math.ceil(w["t_end"] / dt_of(w) - 1e-9)
+    return out
 
 
 def run_reference(w, steps, warmup, budget_s=12.0):
@@ -420,7 +451,7 @@ def main():
         args.warmup = 3
     metric = "DOF-updates/sec per SSP-RK3 stage"
     config = {"workload": args.workload, "mesh": f"{w['nx']}x{w['ny']}", "p": w["p"], "flux": w["flux"],
-              "stab": w["stab"], "dofs": w["nx"] * w["ny"] * (w["p"] + 1) ** 2,
+              "stab": w["stab"], "dofs": dofs_of(w),
               "l2": "inputs larger than L2 (three 67 MB FP32 state arrays per stage)",
               "parallelism": f"replicas{world}" if world > 1 else "single"}
 
@@ -467,7 +498,10 @@ def main():
                             run_small("kpp_1024x1024_q3_rk4", "fp32", 40, 3, local),
                             run_small("rotation_256x256_q2", "fp64", 100, 5, local),
                             run_small("rotation_256x256_q2", "fp32", 100, 5, local),
-                            run_small("advect1d_128_p2", "fp64", 1280, 10, local)]
+                            run_small("advect1d_128_p2", "fp64", 1280, 10, local),
+                            run_small("sod_train_4194304_q2", "fp32", 200, 5, local),
+                            run_small("sod_train_4194304_q2", "fp64", 100, 5, local),
+                            run_small("sod_128_q2", "fp64", 739, 10, local)]
     if rank != 0:
         return
     hbm, src = peaks()
@@ -492,6 +526,11 @@ def main():
                     "d2h_bytes_per_step": r32.get("bytes")} if "t_e2e" in r32 else None,
             "gpu_launches": r32["launches"], "clocks": r32["clocks"], "mass_after": r32["mass"],
             "cell_mean_range_after": r32["mean_range"]}
+    if w["flux"] == "euler":      # the Euler kernel is bound by HBM, not by FP32 issue
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                            "bytes_per_launch": alg_bytes, "kernel": "euler_kernel (3 launches per step)"}
+        line["config"]["l2"] = f"inputs larger than L2 (three {N * 4 / 1e6:.0f} MB FP32 state arrays per stage)"
     if r64 is not None:
         line["fp64"] = {"value": stages * N * r64["steps"] / r64["t"], "unit": "DOF-updates/s",
                         "ms_per_step": 1e3 * r64["t"] / r64["steps"], "steps": r64["steps"]}

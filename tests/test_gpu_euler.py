@@ -222,3 +222,28 @@ def test_sod_train_steps(oracle_mod, prec, p, stab):
     torch.cuda.synchronize()
     ctx.sync_status()
     assert per_comp_rel(Ud.double().cpu().numpy(), ref, p) <= (1e-12 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_sod_train_full_size_sampled(oracle_mod, prec):
+    """The large-mesh workload as the bench runs it (2^22 cells, p = 2, dgw_project, then
+    ten steps): the residual of the stepped state at sampled cells (both ends, tile
+    borders and a seeded random sample) against the oracle evaluated cell by cell."""
+    import bench
+    w = bench.WORKLOADS["sod_train_4194304_q2"]
+    s = bench.spec_of(w)
+    ctx = ctx_for(s, prec)
+    U = torch.empty((ctx.K, ctx.E), dtype=ctx.dtype, device="cuda")
+    ctx.project(torch.tensor(bench.initial_samples(w), device="cuda").contiguous(), U)
+    ctx.rk_step(U, bench.dt_of(w), 10)
+    L = torch.empty_like(U)
+    ctx.residual(U, L)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    E = ctx.E
+    rng = np.random.default_rng(77)
+    idx = np.unique(np.concatenate([[0, 1, 127, 128, E // 2 - 1, E // 2, E - 129, E - 128, E - 2, E - 1],
+                                    rng.integers(0, E, 3000)]))
+    ref = oracle_mod.residual_at(oracle_mod.Problem(**s), U.double().cpu().numpy(), idx)
+    got = L.double().cpu().numpy()[:, idx]
+    assert per_comp_rel(got, ref, 2) <= (1e-12 if prec == "fp64" else 1e-5)
