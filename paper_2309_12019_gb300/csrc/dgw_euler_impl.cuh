@@ -25,8 +25,28 @@ struct EulerSmem {
     Real rho[N1][TX + 2];     // density coefficients, column lx + 1; halo cells 0 and nt + 1
     Real tr[2][3][TX + 2];    // values at xi = -1 (0) and xi = +1 (1), same columns
     Real hf[3][TX + 1];       // LLF flux of face f, between columns f and f + 1
+    Real sp[2][TX + 1];       // |v| + c of the left (0) and right (1) state of face f
     int has[2];               // the halo cell on the left / right exists
 };
+
+// Reciprocal and square root of the Euler kernel.  float: the approximate instructions
+// rcp.approx and sqrt.approx of the PTX ISA (relative error of a few ulp, far inside the
+// float path's tolerance; a negative argument of the square root gives NaN);
+// double: the correctly rounded operations.
+__device__ __forceinline__ float rcp_e(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_e(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_e(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double sqrt_e(double x) { return sqrt(x); }
 
 struct EulerState {
     Real v, pr, inv_rho;
@@ -35,7 +55,7 @@ struct EulerState {
 __device__ __forceinline__ EulerState euler_prim(const KParams& A, Real rho, Real m, Real en)
 {
     EulerState s;
-    s.inv_rho = Real(1) / rho;
+    s.inv_rho = rcp_e(rho);
     s.v = m * s.inv_rho;
     s.pr = A.gm1 * (en - Real(0.5) * m * s.v);
     return s;
@@ -43,7 +63,7 @@ __device__ __forceinline__ EulerState euler_prim(const KParams& A, Real rho, Rea
 
 __device__ __forceinline__ Real euler_speed(const KParams& A, const EulerState& s)
 {
-    return fabs(s.v) + sqrt_r(A.gam * s.pr * s.inv_rho);
+    return fabs(s.v) + sqrt_e(A.gam * s.pr * s.inv_rho);
 }
 
 // max(a, b) that returns NaN when either is NaN (fmax drops a NaN operand): a state
@@ -109,19 +129,21 @@ __device__ __forceinline__ Real sensor_1d(const KParams& A, const Tab<P>& T, con
         for (int f = 0; f < 2; ++f)
             if (has[f]) dev += zpow(A, fabs(wnb[f] * inv / A.w_nbr - Real(1)));
         const Real minlin = lin0 < A.w_nbr ? lin0 : A.w_nbr;
-        return dev / (zpow(A, fabs(Real(1) / minlin - Real(1))) + Real(me));
+        return dev * rcp_e(zpow(A, fabs(rcp_e(minlin) - Real(1))) + Real(me));
     }
-    // U - U* = sum_l w_l (c - c_l)
+    // U - U* = sum_l w_l (c - c_l); the ratio r = ||U - U*|| / ||U|| is taken through
+    // its square: r <= 1 iff qd <= beta0, r < b iff r^2 < b^2, ||U - U*|| <= eps_s iff
+    // qd <= eps_s^2
 #pragma unroll
     for (int k = 1; k < N1; ++k) dacc[k] *= inv;
     dacc[0] = Real(0);
-    const Real num = sqrt_r(fmax(qform<P>(T, dacc), Real(0)));
-    if (num <= A.eps_s) return Real(0);
+    const Real qd = fmax(qform<P>(T, dacc), Real(0));
+    if (qd <= A.eps_s * A.eps_s) return Real(0);
     if (beta0 <= Real(0)) return Real(1);
-    const Real r = num / sqrt_r(beta0);
-    Real g = r < Real(1) ? r : Real(1);
+    const Real r2 = qd * rcp_e(beta0);
+    Real g = r2 < Real(1) ? sqrt_e(r2) : Real(1);
     if (!A.q_one) g = pow(g, A.q);
-    if (r < A.b) g = Real(0);
+    if (r2 < A.b * A.b) g = Real(0);
     return g;
 }
 
@@ -160,12 +182,25 @@ __global__ void __launch_bounds__(TX, kF32 ? 8 : 4) euler_kernel(const __grid_co
             S.tr[1][comp][col] = xp;
         }
     };
+    // Un is read only by the final combination: its loads are issued here, so that their
+    // latency hides behind the sensor, volume and face work
+    Real un[3][N1];
     if (in) {
         const Real* src = A.Uk + gx;
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp)
 #pragma unroll
             for (int k = 0; k < N1; ++k) c[comp][k] = src[(int64_t)(comp * N1 + k) * E];
+        if (MODE == 0 && A.has_un) {
+            const Real* usrc = A.Un + gx;
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    const Real* a = usrc + (int64_t)(comp * N1 + k) * E;
+                    un[comp][k] = A.cg_loads ? __ldcg(a) : *a;
+                }
+        }
         put(c, tid + 1);
     }
     if (tid < 2) {
@@ -226,13 +261,6 @@ __global__ void __launch_bounds__(TX, kF32 ? 8 : 4) euler_kernel(const __grid_co
 #pragma unroll
                 for (int k = 0; k < N1; ++k) acc[comp][k] = fma(T.WD[q][k], F[comp], acc[comp][k]);
         }
-        if (need_lam) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const EulerState st = euler_prim(A, S.tr[s][0][tid + 1], S.tr[s][1][tid + 1], S.tr[s][2][tid + 1]);
-                lam = max_nan(lam, euler_speed(A, st));
-            }
-        }
     }
 
     // ---- 2. faces f = 0 .. nt of the tile ----
@@ -257,7 +285,10 @@ __global__ void __launch_bounds__(TX, kF32 ? 8 : 4) euler_kernel(const __grid_co
         Real FL[3], FR[3];
         euler_flux(sl, uL[1], uL[2], FL);
         euler_flux(sr, uR[1], uR[2], FR);
-        const Real s = max_nan(euler_speed(A, sl), euler_speed(A, sr));
+        const Real spl = euler_speed(A, sl), spr = euler_speed(A, sr);
+        S.sp[0][f] = spl;
+        S.sp[1][f] = spr;
+        const Real s = max_nan(spl, spr);
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp)
             S.hf[comp][f] = Real(0.5) * ((FL[comp] + FR[comp]) - s * (uR[comp] - uL[comp]));
@@ -266,6 +297,8 @@ __global__ void __launch_bounds__(TX, kF32 ? 8 : 4) euler_kernel(const __grid_co
     if (!in) return;
 
     // ---- 3. face terms, stabilization, M^{-1}, Runge-Kutta combination ----
+    // lambda_e: also |v| + c at the cell's two ends, its own states at faces tid, tid + 1
+    if (need_lam) lam = max_nan(lam, max_nan(S.sp[1][tid], S.sp[0][tid + 1]));
     const Real ngs = A.stab == STAB_DG ? Real(0) : -(gamma * (A.lam_fixed ? A.lambda_nu : lam) * Real(1.0 / P));
     Real chk = Real(0);
 #pragma unroll
@@ -285,7 +318,7 @@ __global__ void __launch_bounds__(TX, kF32 ? 8 : 4) euler_kernel(const __grid_co
             const Real Lk = (A.two_h * T.minv[k]) * r;
             const int64_t idx = (int64_t)(comp * N1 + k) * E + gx;
             Real out = fma(A.cl, Lk, A.ck * c[comp][k]);
-            if (A.has_un) out = fma(A.cn, A.cg_loads ? __ldcg(A.Un + idx) : A.Un[idx], out);
+            if (A.has_un) out = fma(A.cn, un[comp][k], out);
             chk = fma(out, Real(0), chk);
             A.Uout[idx] = out;
         }
