@@ -51,9 +51,12 @@ WORKLOADS["kpp_1024x1024_q3_rk4"] = dict(WORKLOADS["kpp_1024x1024_q3"], rk_order
 # the 1D Euler system (Sec. 5.6): Sod's shock tube at the paper's size (128 cells, p = 2,
 # reflecting walls, to t = 0.231), and a periodic train of Sod tubes (one every 64 cells)
 # on 2^22 cells as the large-mesh workload; |v| + c <= 2.5 sets the step
-WORKLOADS["sod_128_q2"] = dict(dim=1, nx=128, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0),
-                               bc=("reflect", "reflect", "periodic", "periodic"), flux="euler", stab="weno",
-                               cfl=I.euler_cfl(2), speeds=(2.5,), u0="sod", t_end=I.SHOCK_TUBES["sod"]["t_end"])
+for _name, _nx, _p in (("sod", 128, 2), ("shu_osher", 512, 3)):
+    _d = I.SHOCK_TUBES[_name]
+    WORKLOADS[f"{_name}_{_nx}_q{_p}"] = dict(dim=1, nx=_nx, ny=1, p=_p, box=(_d["box"][0], _d["box"][1], 0.0, 1.0),
+                                             bc=tuple(_d["bc"]) + ("periodic", "periodic"), flux="euler",
+                                             stab="weno", cfl=I.euler_cfl(_p), speeds=(_d["lam"],),
+                                             u0="tube:" + _name, t_end=_d["t_end"])
 WORKLOADS["sod_train_4194304_q2"] = dict(dim=1, nx=1 << 22, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0),
                                          bc=("periodic",) * 4, flux="euler", stab="weno",
                                          cfl=I.euler_cfl(2), speeds=(2.5,), u0="sod_train")
@@ -72,8 +75,8 @@ def initial_samples(w):
         f = I.u0_kpp(X, Y)
     elif w["u0"] == "rotation":
         f = I.u0_rotation(X, Y)
-    elif w["u0"] == "sod":
-        f = I.shock_tube_samples("sod", w["nx"], 8)
+    elif w["u0"].startswith("tube:"):
+        f = I.shock_tube_samples(w["u0"][5:], w["nx"], 8)
     elif w["u0"] == "sod_train":
         f = I.sod_train_samples(w["nx"], nq=8)
     else:
@@ -501,7 +504,8 @@ def main():
                             run_small("advect1d_128_p2", "fp64", 1280, 10, local),
                             run_small("sod_train_4194304_q2", "fp32", 200, 5, local),
                             run_small("sod_train_4194304_q2", "fp64", 100, 5, local),
-                            run_small("sod_128_q2", "fp64", 739, 10, local)]
+                            run_small("sod_128_q2", "fp64", 739, 10, local),
+                            run_small("shu_osher_512_q3", "fp64", 9216, 10, local)]
     if rank != 0:
         return
     hbm, src = peaks()

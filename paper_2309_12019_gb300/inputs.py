@@ -229,13 +229,21 @@ def nsteps_to(t_end: float, dt: float):
 # --------------------------------------------------------------------------------------
 # Shock tubes of the Euler system (Sec. 5.6), primitive states (rho, v, p), gamma = 1.4
 # --------------------------------------------------------------------------------------
-# Sod's and Lax's shock tubes: the diaphragm at the centre, on a cell face for the even
-# cell counts used here.  "lam" bounds |v| + c over the solution and sets the time step.
+# Shock tubes of Sec. 5.6.  Where the paper gives no diaphragm position it is read as
+# the usual one of each problem (Sod, Lax: the centre; modified Sod: x = 0.3;
+# Shu-Osher: x = -4).  An inlet is read as a zero-gradient side: the state there stays at
+# its initial value up to t_end (supersonic inflow for Shu-Osher; for the modified Sod
+# problem the rarefaction's head reaches x = 0 only at t = 0.7).  "lam" bounds |v| + c
+# over the solution and sets the time step.
 SHOCK_TUBES = {
     "sod": dict(box=(0.0, 1.0), jumps=(0.5,), states=((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)),
                 bc=("reflect", "reflect"), t_end=0.231, nx=128, p=2, lam=2.5),
+    "sod_modified": dict(box=(0.0, 1.0), jumps=(0.3,), states=((1.0, 0.75, 1.0), (0.125, 0.0, 0.1)),
+                         bc=("outflow", "reflect"), t_end=0.2, nx=128, p=2, lam=2.8),
     "lax": dict(box=(0.0, 2.0), jumps=(1.0,), states=((0.445, 0.698, 3.528), (0.5, 0.0, 0.571)),
                 bc=("outflow", "outflow"), t_end=0.14, nx=512, p=2, lam=5.0),
+    "shu_osher": dict(box=(-5.0, 5.0), jumps=(-4.0,), states=((3.857143, 2.629369, 10.3333), "sine"),
+                      bc=("outflow", "reflect"), t_end=1.8, nx=512, p=2, lam=5.0),
 }
 
 GAS_GAMMA = 1.4
@@ -251,18 +259,33 @@ def shock_tube_primitive(name: str, x):
     out = np.zeros((3,) + x.shape)
     for r, st in enumerate(d["states"]):
         sel = region == r
-        for c in range(3):
-            out[c][sel] = st[c]
+        if isinstance(st, str):        # Shu-Osher: a density wave ahead of the shock
+            out[0][sel] = 1.0 + 0.2 * np.sin(5.0 * x[sel])
+            out[1][sel] = 0.0
+            out[2][sel] = 1.0
+        else:
+            for c in range(3):
+                out[c][sel] = st[c]
     return out
 
 
 def shock_tube_samples(name: str, nx: int, nq: int = 8, gamma: float = GAS_GAMMA):
     """Conservative samples (rho, rho v, rho E) at the projection points of a 1D mesh of
-    nx elements, shape (3, nx * nq)."""
+    nx elements, shape (3, nx * nq).  In a cell that a diaphragm cuts, every sample is
+    the cell's Gauss mean of the data, so that the projection there is the cell mean (the
+    L2 projection of a jump inside a cell overshoots, here into negative pressure)."""
     d = SHOCK_TUBES[name]
     X, _ = sample_points(1, nx, 1, (d["box"][0], d["box"][1], 0.0, 1.0), nq)
-    rho, v, p = shock_tube_primitive(name, X.reshape(-1))
-    return np.stack([rho, rho * v, p / (gamma - 1.0) + 0.5 * rho * v * v])
+    rho, v, p = shock_tube_primitive(name, X)
+    q = np.stack([rho, rho * v, p / (gamma - 1.0) + 0.5 * rho * v * v])    # (3, nx, nq)
+    w = np.polynomial.legendre.leggauss(nq)[1] / 2.0
+    h = (d["box"][1] - d["box"][0]) / nx
+    left = d["box"][0] + np.arange(nx) * h
+    cut = np.zeros(nx, dtype=bool)
+    for j in d["jumps"]:
+        cut |= (left < j) & (j < left + h)
+    q = np.where(cut[None, :, None], (q * w).sum(axis=2, keepdims=True), q)
+    return q.reshape(3, -1)
 
 
 def euler_cfl(p: int) -> float:

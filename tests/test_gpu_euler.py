@@ -109,11 +109,20 @@ def _shock_tube(name, nx, p):
     return s, n, dt, last
 
 
-def test_sod_fp64_full_run(oracle_mod):
-    """Sod's problem at the paper's size (128 cells, p = 2) to t = 0.231: device
-    projection and every step against the oracle."""
-    s, n, dt, last = _shock_tube("sod", 128, 2)
-    f = I.shock_tube_samples("sod", 128, 8)
+@pytest.mark.parametrize("name,nx,p,nmax", [("sod", 128, 2, None), ("sod_modified", 128, 2, None),
+                                            ("shu_osher", 512, 2, 400), ("shu_osher", 512, 3, 50),
+                                            ("lax", 512, 2, 300)])
+def test_shock_tube_fp64_runs(oracle_mod, name, nx, p, nmax):
+    """Shock tubes at the paper's sizes: device projection, then every step to t_end (Sod,
+    modified Sod) or the first nmax steps, against the oracle.  The sensor ratio is
+    scale-free: in a cell whose slopes are at rounding level it takes O(1) values set by
+    the rounding, so the two sides' different summation orders seed differences that a
+    strong shock amplifies.  Shu-Osher at p = 3 agrees to 2e-12 after 50 steps and
+    drifts apart beyond (2e-7 after 100 steps on GB300), hence its shorter horizon."""
+    s, n, dt, last = _shock_tube(name, nx, p)
+    if nmax is not None:
+        n, last = min(n, nmax), 0.0
+    f = I.shock_tube_samples(name, nx, 8)
     P = oracle_mod.Problem(**s)
     U0 = oracle_mod.project(P, f, 8)
     ctx = ctx_for(s)
@@ -128,9 +137,9 @@ def test_sod_fp64_full_run(oracle_mod):
         ctx.rk_step(Ud, last, 1)
     torch.cuda.synchronize()
     ctx.sync_status()
-    assert per_comp_rel(Ud.cpu().numpy(), ref, 2) <= 1e-9
-    # between reflecting walls the mass is conserved
-    assert abs(ctx.mass(Ud) - oracle_mod.mass(P, U0)) <= 1e-13
+    assert per_comp_rel(Ud.cpu().numpy(), ref, p) <= 1e-9
+    if name == "sod":      # between reflecting walls the mass is conserved
+        assert abs(ctx.mass(Ud) - oracle_mod.mass(P, U0)) <= 1e-13
 
 
 @pytest.mark.parametrize("p,stab", [(1, "weno"), (2, "zhao"), (3, "weno"), (2, "lo")])
@@ -141,7 +150,7 @@ def test_residual_fp32(oracle_mod, p, stab):
     assert per_comp_rel(residual(ctx_for(s, "fp32"), U), ref, p) <= 1e-5
 
 
-@pytest.mark.parametrize("name,p", [("sod", 1), ("sod", 3), ("lax", 2)])
+@pytest.mark.parametrize("name,p", [("sod", 1), ("sod", 3), ("lax", 2), ("sod_modified", 2), ("shu_osher", 3)])
 def test_shock_tube_fp32_steps(oracle_mod, name, p):
     """Twenty FP32 steps of a shock tube from its projected initial data."""
     d = I.SHOCK_TUBES[name]

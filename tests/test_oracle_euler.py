@@ -150,10 +150,11 @@ def test_exact_riemann_solver_star_state():
     assert abs(rl - 0.42632) < 1e-5 and abs(rr - 0.26557) < 1e-5
 
 
-def _sod(nx, p, stab, nq=8):
-    d = I.SHOCK_TUBES["sod"]
+def _tube(name, nx, p, stab, nq=8):
+    """L1 density error at t_end against the exact Riemann solution, and the state."""
+    d = I.SHOCK_TUBES[name]
     P = _problem(nx, p, stab, d["bc"], d["box"])
-    U = O.project(P, I.shock_tube_samples("sod", nx, nq), nq)
+    U = O.project(P, I.shock_tube_samples(name, nx, nq), nq)
     n, dt, last = I.nsteps_to(d["t_end"], I.euler_cfl(p) * P.h / d["lam"])
     U = O.rk3(P, U, dt, n)
     if last > 0:
@@ -163,6 +164,10 @@ def _sod(nx, p, stab, nq=8):
     exact = X.sample(a, b, (Xs.reshape(-1) - d["jumps"][0]) / d["t_end"])
     Pd = dataclasses.replace(P, flux="advect", bc=("outflow",) * 2 + P.bc[2:])
     return O.l1_error(Pd, U[:p + 1], exact[0], nq), U
+
+
+def _sod(nx, p, stab):
+    return _tube("sod", nx, p, stab)
 
 
 def test_sod_shock_tube_against_exact_solution():
@@ -182,3 +187,31 @@ def test_sod_shock_tube_against_exact_solution():
     ez, _ = _sod(64, 2, "zhao")
     assert elo > 2.0 * e64
     assert ez > e64
+
+
+@pytest.mark.parametrize("name,n0,bound", [("sod_modified", 32, 1.5e-2), ("lax", 128, 4e-2)])
+def test_shock_tubes_against_exact_solutions(name, n0, bound):
+    """The modified Sod problem (a sonic point inside the rarefaction; its diaphragm cuts a
+    cell) and Lax's problem, p = 2, WENO: the L1 density error against the exact Riemann
+    solution is below the bound on 2 n0 cells and falls under refinement, and the LO
+    scheme's is at least 1.5 times larger."""
+    e1, _ = _tube(name, n0, 2, "weno")
+    e2, U = _tube(name, 2 * n0, 2, "weno")
+    assert e2 < bound and e2 < 0.7 * e1
+    elo, _ = _tube(name, 2 * n0, 2, "lo")
+    assert elo > 1.5 * e2
+
+
+def test_cut_cells_start_from_their_mean():
+    """A diaphragm inside a cell: the samples there are the cell's Gauss mean, so the
+    projection is the constant mean (no overshoot); elsewhere the data are sampled."""
+    d = I.SHOCK_TUBES["sod_modified"]
+    f = I.shock_tube_samples("sod_modified", 128, 8).reshape(3, 128, 8)
+    cut = int(0.3 * 128)                       # x = 0.3 lies inside cell 38
+    assert np.all(f[:, cut] == f[:, cut, :1])
+    w = np.polynomial.legendre.leggauss(8)[1] / 2
+    x = (cut + 0.5 + 0.5 * np.polynomial.legendre.leggauss(8)[0]) / 128
+    rho = np.where(x < 0.3, 1.0, 0.125)
+    assert abs(f[0, cut, 0] - np.sum(w * rho)) < 1e-15
+    assert np.all(f[0, :cut] == 1.0) and np.all(f[0, cut + 1:] == 0.125)
+    assert d["jumps"] == (0.3,)
