@@ -57,6 +57,12 @@
  *      Reflecting walls mirror the state: (rho, -rho v, rho E).  The sensor uses the
  *      density alone, applied to all components; beyond a wall, as beyond any
  *      non-periodic boundary, there is no neighbour candidate.
+ *   R17 Euler system in 2D (Sec. 5.6, its 2D problems): U = (rho, rho vx, rho vy, rho E),
+ *      F(U) n = (rho v.n, rho v (v.n) + p n, (rho E + p) v.n); layout
+ *      U[(comp (p+1)^2 + k) E + e].  LLF at each face Gauss point with s+ the larger
+ *      |v.n| + c of the two states; lambda_e = max (|v| + c) over the volume Gauss points
+ *      and the element's own values at the face Gauss points.  A reflecting wall mirrors
+ *      the normal momentum: m+ = m- - 2 (m-.n) n.  Stabilization and sensor as in R15.
  *   R13 the comparison sensor of Zhao et al. (restated in Sec. 5.6), stab = ZHAO:
  *      gamma^Z = sum_l |w_l / lin_l - 1|^theta / (|1 / min_l lin_l - 1|^theta + m_e) with
  *      the weights of R3; with no neighbour candidate (m_e = 0) the weights are the linear
@@ -191,7 +197,7 @@ void orc_gauss_legendre(int n, double* x, double* w)
 static int nmodes1(const orc_problem* P) { return P->p + 1; }
 static int nmodes(const orc_problem* P) { return P->dim == 1 ? P->p + 1 : (P->p + 1) * (P->p + 1); }
 static long nelem(const orc_problem* P) { return P->dim == 1 ? (long)P->nx : (long)P->nx * P->ny; }
-static int ncomp(const orc_problem* P) { return P->flux == ORC_FLUX_EULER ? 3 : 1; }
+static int ncomp(const orc_problem* P) { return P->flux == ORC_FLUX_EULER ? P->dim + 2 : 1; }
 static long nstate(const orc_problem* P) { return nelem(P) * nmodes(P) * ncomp(P); }
 static double hx_of(const orc_problem* P) { return (P->x1 - P->x0) / P->nx; }
 static double hy_of(const orc_problem* P) { return P->dim == 1 ? 1.0 : (P->y1 - P->y0) / P->ny; }
@@ -620,40 +626,66 @@ static void residual_elem(const orc_problem* P, const double* U, long e, double*
 }
 
 /* ------------------------------------------------------------------------- */
-/* Euler system in 1D (Sec. 5.6; reading R15)                                */
+/* Euler system in 1D and 2D (Sec. 5.6; readings R15, R17)                    */
 /* ------------------------------------------------------------------------- */
 
-static void euler_flux(const orc_problem* P, const double q[3], double F[3])
+#define ORC_MAXC 4     /* conserved variables: rho, rho v (dim components), rho E */
+
+/* velocity, pressure and sound speed squared of a conservative state */
+static void euler_prim(const orc_problem* P, const double* q, double v[2], double* pr, double* c2)
 {
-    double v = q[1] / q[0];
-    double pr = (P->gas_gamma - 1.0) * (q[2] - 0.5 * q[1] * v);
-    F[0] = q[1];
-    F[1] = q[1] * v + pr;
-    F[2] = (q[2] + pr) * v;
+    int d = P->dim;
+    v[0] = q[1] / q[0];
+    v[1] = d == 2 ? q[2] / q[0] : 0.0;
+    double mv = q[1] * v[0] + (d == 2 ? q[2] * v[1] : 0.0);
+    *pr = (P->gas_gamma - 1.0) * (q[d + 1] - 0.5 * mv);
+    *c2 = P->gas_gamma * *pr / q[0];
 }
 
-/* |v| + c, the spectral radius of the flux Jacobian */
-static double euler_speed(const orc_problem* P, const double q[3])
+/* F(U) n = (rho v.n, rho v (v.n) + p n, (rho E + p) v.n) */
+static void euler_flux_n(const orc_problem* P, const double* q, double nx, double ny, double* F)
 {
-    double v = q[1] / q[0];
-    double pr = (P->gas_gamma - 1.0) * (q[2] - 0.5 * q[1] * v);
-    return fabs(v) + sqrt(P->gas_gamma * pr / q[0]);
+    int d = P->dim;
+    double v[2], pr, c2;
+    euler_prim(P, q, v, &pr, &c2);
+    double vn = v[0] * nx + v[1] * ny;
+    F[0] = q[0] * vn;
+    F[1] = q[1] * vn + pr * nx;
+    if (d == 2) F[2] = q[2] * vn + pr * ny;
+    F[d + 1] = (q[d + 1] + pr) * vn;
 }
 
-/* LLF flux for the normal n = +-1 (R15: s+ = the larger endpoint speed) */
-static void euler_llf(const orc_problem* P, const double um[3], const double up[3], double n, double H[3])
+/* |v.n| + c (the spectral radius of F'(U) n); |v| + c when n is NULL */
+static double euler_speed(const orc_problem* P, const double* q, const double* n)
 {
-    double Fm[3], Fp[3];
-    euler_flux(P, um, Fm);
-    euler_flux(P, up, Fp);
-    double sm = euler_speed(P, um), sp = euler_speed(P, up);
+    double v[2], pr, c2;
+    euler_prim(P, q, v, &pr, &c2);
+    double vn = n ? fabs(v[0] * n[0] + v[1] * n[1]) : sqrt(v[0] * v[0] + v[1] * v[1]);
+    return vn + sqrt(c2);
+}
+
+/* LLF flux across a face of outward unit normal n (R15: s+ = the larger |v.n| + c) */
+static void euler_llf(const orc_problem* P, const double* um, const double* up, const double n[2], double* H)
+{
+    int m = P->dim + 2;
+    double Fm[ORC_MAXC], Fp[ORC_MAXC];
+    euler_flux_n(P, um, n[0], n[1], Fm);
+    euler_flux_n(P, up, n[0], n[1], Fp);
+    double sm = euler_speed(P, um, n), sp = euler_speed(P, up, n);
     double s = (isnan(sm) || isnan(sp)) ? NAN : (sm > sp ? sm : sp);
-    for (int c = 0; c < 3; ++c) H[c] = n * 0.5 * (Fm[c] + Fp[c]) - 0.5 * s * (up[c] - um[c]);
+    for (int c = 0; c < m; ++c) H[c] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * s * (up[c] - um[c]);
 }
 
+/* For tests: the LLF flux in 1D (normal n = +-1) and in 2D (normal (nx, ny)). */
 void orc_euler_llf(const orc_problem* P, const double* um, const double* up, double n, double* H)
 {
-    euler_llf(P, um, up, n, H);
+    double nn[2] = {n, 0.0};
+    euler_llf(P, um, up, nn, H);
+}
+void orc_euler_llf2(const orc_problem* P, const double* um, const double* up, double nx, double ny, double* H)
+{
+    double nn[2] = {nx, ny};
+    euler_llf(P, um, up, nn, H);
 }
 
 static void load_comp(const orc_problem* P, const double* U, long e, int comp, double* c)
@@ -663,88 +695,121 @@ static void load_comp(const orc_problem* P, const double* U, long e, int comp, d
     for (int k = 0; k < K; ++k) c[k] = U[((long)comp * K + k) * E + e];
 }
 
-/* lambda_e of R15: max (|v| + c) over the p+2 Gauss points and the two end points */
-static double euler_lambda_elem(const orc_problem* P, long e, double ce[3][ORC_MAXK])
+/* state at reference point (r, s) of an element with coefficients ce */
+static void euler_state(const orc_problem* P, double ce[ORC_MAXC][ORC_MAXK], double r, double s, double* q)
 {
-    double qx[ORC_MAXNQ], qy[ORC_MAXNQ], qr[ORC_MAXNQ], qs[ORC_MAXNQ], qw[ORC_MAXNQ];
-    int nv = elem_quad(P, e, P->p + 2, qx, qy, qr, qs, qw);
-    double lam = 0.0;
-    for (int t = 0; t < nv + 2; ++t) {
-        double r = t < nv ? qr[t] : (t == nv ? -1.0 : 1.0), q[3];
-        for (int c = 0; c < 3; ++c) q[c] = poly_d(P, ce[c], 0, 0, r, 0.0);
-        double sp = euler_speed(P, q);
-        if (isnan(sp) || isnan(lam)) lam = NAN;
+    for (int c = 0; c < P->dim + 2; ++c) q[c] = poly_d(P, ce[c], 0, 0, r, s);
+}
+
+/* lambda_e of R15/R17: max (|v| + c) over the (p+2)^d volume Gauss points and the
+ * element's own values at the face Gauss points (1D: the two end points); NaN if any
+ * of them has no real sound speed */
+static double euler_lambda_elem(const orc_problem* P, long e, double ce[ORC_MAXC][ORC_MAXK])
+{
+    int nq = P->p + 2;
+    double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qr[ORC_MAXNQ * ORC_MAXNQ];
+    double qs[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ], n[2];
+    double lam = 0.0, q[ORC_MAXC];
+    int bad = 0;
+    int nv = elem_quad(P, e, nq, qx, qy, qr, qs, qw);
+    for (int t = 0; t < nv; ++t) {
+        euler_state(P, ce, qr[t], qs[t], q);
+        double sp = euler_speed(P, q, NULL);
+        if (isnan(sp)) bad = 1;
         else if (sp > lam) lam = sp;
     }
-    return lam;
+    for (int f = 0; f < nfaces(P); ++f) {
+        int nf = face_quad(P, e, f, nq, qx, qy, qr, qs, qw, n);
+        for (int t = 0; t < nf; ++t) {
+            euler_state(P, ce, qr[t], qs[t], q);
+            double sp = euler_speed(P, q, NULL);
+            if (isnan(sp)) bad = 1;
+            else if (sp > lam) lam = sp;
+        }
+    }
+    return bad ? NAN : lam;
 }
 
 static void euler_residual_elem(const orc_problem* P, const double* U, long e, double* Le, double* gamma_out)
 {
-    int K = nmodes(P);
+    int K = nmodes(P), m = P->dim + 2;
     int nq = P->p + 2;
-    double ce[3][ORC_MAXK], cn[3][ORC_MAXK], R[3][ORC_MAXK];
-    double qx[ORC_MAXNQ], qy[ORC_MAXNQ], qr[ORC_MAXNQ], qs[ORC_MAXNQ], qw[ORC_MAXNQ];
+    double ce[ORC_MAXC][ORC_MAXK], cn[ORC_MAXC][ORC_MAXK], R[ORC_MAXC][ORC_MAXK];
+    double qx[ORC_MAXNQ * ORC_MAXNQ], qy[ORC_MAXNQ * ORC_MAXNQ], qr[ORC_MAXNQ * ORC_MAXNQ];
+    double qs[ORC_MAXNQ * ORC_MAXNQ], qw[ORC_MAXNQ * ORC_MAXNQ];
     double fx[ORC_MAXNQ], fy[ORC_MAXNQ], fr[ORC_MAXNQ], fs[ORC_MAXNQ], fw[ORC_MAXNQ], n[2];
     memset(R, 0, sizeof R);
-    for (int c = 0; c < 3; ++c) load_comp(P, U, e, c, ce[c]);
+    for (int c = 0; c < m; ++c) load_comp(P, U, e, c, ce[c]);
 
-    /* volume: + int phi_k' F(U_h) dx */
+    /* volume: + int grad(phi_k) . F(U_h) dx, component by component */
     int nv = elem_quad(P, e, nq, qx, qy, qr, qs, qw);
     for (int t = 0; t < nv; ++t) {
-        double q[3], F[3];
-        for (int c = 0; c < 3; ++c) q[c] = poly_d(P, ce[c], 0, 0, qr[t], 0.0);
-        euler_flux(P, q, F);
+        double q[ORC_MAXC], Fx[ORC_MAXC], Fy[ORC_MAXC];
+        euler_state(P, ce, qr[t], qs[t], q);
+        euler_flux_n(P, q, 1.0, 0.0, Fx);
+        if (P->dim == 2) euler_flux_n(P, q, 0.0, 1.0, Fy);
         for (int k = 0; k < K; ++k) {
-            double d = phi_d(P, k, 1, 0, qr[t], 0.0);
-            for (int c = 0; c < 3; ++c) R[c][k] += qw[t] * d * F[c];
+            double dx = phi_d(P, k, 1, 0, qr[t], qs[t]);
+            double dy = P->dim == 2 ? phi_d(P, k, 0, 1, qr[t], qs[t]) : 0.0;
+            for (int c = 0; c < m; ++c) R[c][k] += qw[t] * (dx * Fx[c] + (P->dim == 2 ? dy * Fy[c] : 0.0));
         }
     }
 
-    /* faces: - phi_k H(U-, U+, n) at x = x_e -+ h/2 */
-    for (int f = 0; f < 2; ++f) {
+    /* faces: - int_{dK} phi_k H(U-, U+, n) ds */
+    for (int f = 0; f < nfaces(P); ++f) {
         double sx = 0.0, sy = 0.0;
         long nb = neighbour(P, e, f, &sx, &sy);
         if (nb >= 0)
-            for (int c = 0; c < 3; ++c) load_comp(P, U, nb, c, cn[c]);
-        face_quad(P, e, f, nq, fx, fy, fr, fs, fw, n);
-        double um[3], up[3], H[3];
-        for (int c = 0; c < 3; ++c) um[c] = poly_d(P, ce[c], 0, 0, fr[0], 0.0);
-        if (nb >= 0) {
-            for (int c = 0; c < 3; ++c) up[c] = poly_d(P, cn[c], 0, 0, fr[0] + sx, 0.0);
-        } else if (P->bc[f] == ORC_BC_REFLECT) {
-            up[0] = um[0]; up[1] = -um[1]; up[2] = um[2];
-        } else {
-            for (int c = 0; c < 3; ++c) up[c] = um[c];
-        }
-        euler_llf(P, um, up, n[0], H);
-        for (int k = 0; k < K; ++k) {
-            double ph = phi_d(P, k, 0, 0, fr[0], 0.0);
-            for (int c = 0; c < 3; ++c) R[c][k] -= fw[0] * ph * H[c];
+            for (int c = 0; c < m; ++c) load_comp(P, U, nb, c, cn[c]);
+        int nf = face_quad(P, e, f, nq, fx, fy, fr, fs, fw, n);
+        for (int t = 0; t < nf; ++t) {
+            double um[ORC_MAXC], up[ORC_MAXC], H[ORC_MAXC];
+            euler_state(P, ce, fr[t], fs[t], um);
+            if (nb >= 0) {
+                euler_state(P, cn, fr[t] + sx, fs[t] + sy, up);
+            } else {
+                for (int c = 0; c < m; ++c) up[c] = um[c];
+                if (P->bc[f] == ORC_BC_REFLECT) {
+                    /* mirror the normal momentum: m+ = m- - 2 (m-.n) n */
+                    double mn = um[1] * n[0] + (P->dim == 2 ? um[2] * n[1] : 0.0);
+                    up[1] = um[1] - 2.0 * mn * n[0];
+                    if (P->dim == 2) up[2] = um[2] - 2.0 * mn * n[1];
+                }
+            }
+            euler_llf(P, um, up, n, H);
+            for (int k = 0; k < K; ++k) {
+                double ph = phi_d(P, k, 0, 0, fr[t], fs[t]);
+                for (int c = 0; c < m; ++c) R[c][k] -= fw[t] * ph * H[c];
+            }
         }
     }
 
-    /* stabilization of every component with the density sensor */
+    /* stabilization of every component with the density's gamma */
     double gamma = 0.0;
     if (P->stab != ORC_STAB_DG && P->p >= 1) {
         gamma = (P->stab == ORC_STAB_LO) ? 1.0 : sensor_elem(P, U, e, NULL, NULL);
         double lam = P->lambda_nu > 0.0 ? P->lambda_nu : euler_lambda_elem(P, e, ce);
         double nu = lam * hx_of(P) / (2.0 * P->p);
         for (int t = 0; t < nv; ++t)
-            for (int c = 0; c < 3; ++c) {
-                double ux = poly_d(P, ce[c], 1, 0, qr[t], 0.0);
-                for (int k = 0; k < K; ++k) R[c][k] -= gamma * nu * qw[t] * phi_d(P, k, 1, 0, qr[t], 0.0) * ux;
+            for (int c = 0; c < m; ++c) {
+                double ux = poly_d(P, ce[c], 1, 0, qr[t], qs[t]);
+                double uy = P->dim == 2 ? poly_d(P, ce[c], 0, 1, qr[t], qs[t]) : 0.0;
+                for (int k = 0; k < K; ++k) {
+                    double g = phi_d(P, k, 1, 0, qr[t], qs[t]) * ux;
+                    if (P->dim == 2) g += phi_d(P, k, 0, 1, qr[t], qs[t]) * uy;
+                    R[c][k] -= gamma * nu * qw[t] * g;
+                }
             }
     }
     if (gamma_out) *gamma_out = gamma;
 
     for (int k = 0; k < K; ++k) {
-        double m = 0.0;
+        double mk = 0.0;
         for (int t = 0; t < nv; ++t) {
-            double ph = phi_d(P, k, 0, 0, qr[t], 0.0);
-            m += qw[t] * ph * ph;
+            double ph = phi_d(P, k, 0, 0, qr[t], qs[t]);
+            mk += qw[t] * ph * ph;
         }
-        for (int c = 0; c < 3; ++c) Le[c * K + k] = R[c][k] / m;
+        for (int c = 0; c < m; ++c) Le[c * K + k] = R[c][k] / mk;
     }
 }
 
@@ -769,7 +834,7 @@ int orc_check(const orc_problem* P)
     if (P->stab == ORC_STAB_ZHAO && !(P->w_nbr > 0.0 && P->theta > 0.0)) return -1;   /* lin_l > 0 */
     for (int f = 0; f < 2 * P->dim; ++f)           /* walls are for the Euler system */
         if (P->bc[f] == ORC_BC_REFLECT && P->flux != ORC_FLUX_EULER) return -1;
-    if (P->flux == ORC_FLUX_EULER && (P->dim != 1 || !(P->gas_gamma > 1.0))) return -1;
+    if (P->flux == ORC_FLUX_EULER && !(P->gas_gamma > 1.0)) return -1;
     return 0;
 }
 
@@ -782,10 +847,10 @@ void orc_residual(const orc_problem* P, const double* U, double* L)
 #pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
     for (long e = 0; e < E; ++e) {
-        double Le[3 * ORC_MAXK];
+        double Le[ORC_MAXC * ORC_MAXK];
         if (P->flux == ORC_FLUX_EULER) {
             euler_residual_elem(P, U, e, Le, NULL);
-            for (int k = 0; k < 3 * K; ++k) L[k * E + e] = Le[k];
+            for (int k = 0; k < ncomp(P) * K; ++k) L[k * E + e] = Le[k];
         } else {
             residual_elem(P, U, e, Le, NULL);
             for (int k = 0; k < K; ++k) L[k * E + e] = Le[k];
@@ -815,8 +880,8 @@ void orc_lambda(const orc_problem* P, const double* U, double* lam)
     long E = nelem(P);
     for (long e = 0; e < E; ++e) {
         if (P->flux == ORC_FLUX_EULER) {
-            double cq[3][ORC_MAXK];
-            for (int c = 0; c < 3; ++c) load_comp(P, U, e, c, cq[c]);
+            double cq[ORC_MAXC][ORC_MAXK];
+            for (int c = 0; c < ncomp(P); ++c) load_comp(P, U, e, c, cq[c]);
             lam[e] = euler_lambda_elem(P, e, cq);
             continue;
         }
@@ -1006,7 +1071,7 @@ void orc_residual_at(const orc_problem* P, const double* U, const long* idx, lon
 #pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
     for (long t = 0; t < n; ++t) {
-        double Le[3 * ORC_MAXK];
+        double Le[ORC_MAXC * ORC_MAXK];
         if (P->flux == ORC_FLUX_EULER) euler_residual_elem(P, U, idx[t], Le, NULL);
         else residual_elem(P, U, idx[t], Le, NULL);
         for (int k = 0; k < KK; ++k) out[k * n + t] = Le[k];

@@ -95,8 +95,12 @@ class Problem:
 
     @property
     def K(self) -> int:
-        """Rows of the state: modes per element, times 3 components for the Euler system."""
-        return (self.p + 1) ** self.dim * (3 if self.flux == "euler" else 1)
+        """Rows of the state: modes per element, times dim + 2 components for the Euler system."""
+        return (self.p + 1) ** self.dim * self.ncomp
+
+    @property
+    def ncomp(self) -> int:
+        return self.dim + 2 if self.flux == "euler" else 1
 
     @property
     def h(self) -> float:
@@ -145,6 +149,7 @@ def lib():
             L.orc_llf.argtypes = [pp] + [ctypes.c_double] * 6
             L.orc_llf.restype = ctypes.c_double
             L.orc_euler_llf.argtypes = [pp, dp, dp, ctypes.c_double, dp]
+            L.orc_euler_llf2.argtypes = [pp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
             L.orc_wave_speed.argtypes = [pp] + [ctypes.c_double] * 6
             L.orc_wave_speed.restype = ctypes.c_double
             L.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
@@ -255,12 +260,12 @@ def gauss_legendre(n: int):
 
 def project(P: Problem, samples, nq: int = 8) -> np.ndarray:
     """L2 projection of samples given at the nq-point Gauss points of every element
-    (Euler system: samples of (rho, rho v, rho E), shape (3, E * nq), one component after
-    the other)."""
+    (Euler system: samples of the dim + 2 conserved variables, shape (dim + 2, E nq^dim),
+    one component after the other)."""
     if P.flux == "euler":
-        f = np.asarray(samples, dtype=np.float64).reshape(3, -1)
+        f = np.asarray(samples, dtype=np.float64).reshape(P.ncomp, -1)
         Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b == "reflect" else b for b in P.bc))
-        return np.concatenate([project(Ps, f[c], nq) for c in range(3)], axis=0)
+        return np.concatenate([project(Ps, f[c], nq) for c in range(P.ncomp)], axis=0)
     c = _checked(P)
     f = np.ascontiguousarray(np.asarray(samples, dtype=np.float64)).reshape(-1)
     if f.size != P.E * nq ** P.dim:
@@ -306,14 +311,17 @@ def llf(P: Problem, um, up, x, y, nx, ny) -> float:
     return lib().orc_llf(ctypes.byref(c), um, up, x, y, nx, ny)
 
 
-def euler_llf(P: Problem, um, up, n: float) -> np.ndarray:
+def euler_llf(P: Problem, um, up, n) -> np.ndarray:
     """LLF flux of the Euler system between conservative states um (own) and up across a
-    face of outward normal n = +-1 (reading R15)."""
+    face of outward unit normal n: +-1 in 1D (reading R15), (nx, ny) in 2D (R17)."""
     c = _checked(P)
     a = np.ascontiguousarray(np.asarray(um, dtype=np.float64))
     b = np.ascontiguousarray(np.asarray(up, dtype=np.float64))
-    H = np.zeros(3)
-    lib().orc_euler_llf(ctypes.byref(c), _ptr(a), _ptr(b), float(n), _ptr(H))
+    H = np.zeros(P.ncomp)
+    if P.dim == 1:
+        lib().orc_euler_llf(ctypes.byref(c), _ptr(a), _ptr(b), float(n), _ptr(H))
+    else:
+        lib().orc_euler_llf2(ctypes.byref(c), _ptr(a), _ptr(b), float(n[0]), float(n[1]), _ptr(H))
     return H
 
 

@@ -288,28 +288,78 @@ def shock_tube_samples(name: str, nx: int, nq: int = 8, gamma: float = GAS_GAMMA
     return q.reshape(3, -1)
 
 
-def euler_cfl(p: int) -> float:
+def euler_cfl(p: int, dim: int = 1) -> float:
     """Courant number of the Euler workloads, dt = cfl h / lam: inside the SSP-RK3
     stability interval of the stabilization term for gamma = 1 (radius 6, 15, 28.3 times
-    lam dt / h for p = 1, 2, 3)."""
-    return {1: 0.1, 2: 0.1, 3: 0.05}[p]
+    lam dt / h per direction for p = 1, 2, 3; the directions add in 2D)."""
+    return {1: 0.1, 2: 0.1, 3: 0.05}[p] / dim
 
 
-def random_euler_state(p: int, E: int, seed: int, amp: float = 0.05, gamma: float = GAS_GAMMA) -> np.ndarray:
-    """Seeded random modal state of the 1D Euler system, shape (3 (p+1), E), rows
-    comp (p+1) + k: cell means from random primitive states (rho in [1, 1.4], v normal
-    with deviation 0.5, p in [1, 1.5]) and small random higher modes (amp, 2 amp, 3 amp
-    for the three components), so that density and pressure stay positive."""
+def random_euler_state(p: int, E: int, seed: int, amp: float = 0.05, gamma: float = GAS_GAMMA,
+                       dim: int = 1) -> np.ndarray:
+    """Seeded random modal state of the Euler system, shape ((dim + 2) K, E) with
+    K = (p+1)^dim, rows comp K + k: cell means from random primitive states (rho in
+    [1, 1.4], each velocity component normal with deviation 0.5, p in [1, 1.5]) and small
+    random higher modes (amp (1 + comp)), so that density and pressure stay positive."""
     rng = np.random.default_rng(seed)
-    n1 = p + 1
-    U = np.zeros((3 * n1, E))
+    K = (p + 1) ** dim
+    U = np.zeros(((dim + 2) * K, E))
     rho = 1.0 + 0.4 * rng.random(E)
-    v = 0.5 * rng.standard_normal(E)
+    v = 0.5 * rng.standard_normal((dim, E))
     pr = 1.0 + 0.5 * rng.random(E)
-    U[0], U[n1], U[2 * n1] = rho, rho * v, pr / (gamma - 1.0) + 0.5 * rho * v * v
-    for c in range(3):
-        U[c * n1 + 1:(c + 1) * n1] = amp * (1 + c) * rng.standard_normal((p, E))
+    U[0] = rho
+    for a in range(dim):
+        U[(1 + a) * K] = rho * v[a]
+    U[(dim + 1) * K] = pr / (gamma - 1.0) + 0.5 * rho * (v * v).sum(axis=0)
+    for c in range(dim + 2):
+        U[c * K + 1:(c + 1) * K] = amp * (1 + c) * rng.standard_normal((K - 1, E))
     return U
+
+
+# 2D problems of Sec. 5.6 whose data jump along cell faces at the paper's mesh sizes.
+# Kelvin-Helmholtz: the denser, left-moving state fills the strip |y - 0.5| < 0.25 and
+# the boundaries are periodic (the paper gives neither; this is the usual set-up of the
+# cited problem).  Triple point: three states in the subdomains the paper names, walls
+# all round.
+EULER_2D = {
+    "kelvin_helmholtz": dict(box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4, t_end=1.0, nx=512, ny=512, p=2,
+                             lam=3.0),
+    "triple_point": dict(box=(0.0, 7.0, 0.0, 3.0), bc=("reflect",) * 4, t_end=4.0, nx=896, ny=384, p=2, lam=3.0),
+}
+
+
+def euler2d_primitive(name: str, x, y):
+    """(rho, vx, vy, p) of the initial data and the region label at the points (x, y)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if name == "kelvin_helmholtz":
+        inner = np.abs(y - 0.5) < 0.25
+        rho = np.where(inner, 2.0, 1.0)
+        vx = np.where(inner, -0.5, 0.5)
+        vy = 0.01 * np.sin(2.0 * np.pi * (x - 0.5))
+        pr = np.full(x.shape, 2.5)
+        return np.stack([rho, vx, vy, pr]), inner.astype(np.int64)
+    if name == "triple_point":
+        region = np.where(x <= 1.0, 0, np.where(y <= 1.5, 1, 2))
+        rho = np.array([1.0, 0.125, 1.0])[region]
+        pr = np.array([1.0, 0.1, 0.1])[region]
+        return np.stack([rho, 0.0 * rho, 0.0 * rho, pr]), region
+    raise ValueError(name)
+
+
+def euler2d_samples(name: str, nx: int, ny: int, nq: int = 8, gamma: float = GAS_GAMMA):
+    """Conservative samples (rho, rho vx, rho vy, rho E) at the projection points of an
+    nx x ny mesh, shape (4, E nq^2); a cell whose samples straddle two regions gets its
+    Gauss mean in every sample (as for the shock tubes)."""
+    d = EULER_2D[name]
+    X, Y = sample_points(2, nx, ny, d["box"], nq)
+    (rho, vx, vy, pr), region = euler2d_primitive(name, X, Y)
+    q = np.stack([rho, rho * vx, rho * vy, pr / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy)])
+    g, w = np.polynomial.legendre.leggauss(nq)
+    w2 = (np.tile(w, nq) * np.repeat(w, nq)) / 4.0           # sample t = a + nq b
+    cut = region.min(axis=1) != region.max(axis=1)
+    q = np.where(cut[None, :, None], (q * w2).sum(axis=2, keepdims=True), q)
+    return q.reshape(4, -1)
 
 
 def sod_train_samples(nx: int, period: int = 64, nq: int = 8, gamma: float = GAS_GAMMA):

@@ -249,73 +249,106 @@ def residual(P, U):
 
 
 # ---------------------------------------------------------------------------------
-# 1D Euler system (Sec. 5.6): U = (rho, rho v, rho E), p = (gamma - 1)(rho E - rho v^2/2)
+# Euler system (Sec. 5.6), 1D and 2D: U = (rho, rho v, rho E), p = (gamma - 1)(rho E -
+# rho |v|^2 / 2)
 # ---------------------------------------------------------------------------------
-def _euler_F(g, q):
-    rho, m, en = q
-    v = m / rho
-    pr = (g - 1.0) * (en - 0.5 * m * v)
-    return np.array([m, m * v + pr, (en + pr) * v])
+def _euler_Fn(g, q, n):
+    """F(U) n for states q of shape (d + 2, npts) and a unit normal n = (nx, ny)."""
+    d = q.shape[0] - 2
+    rho, en = q[0], q[d + 1]
+    v = [q[1 + a] / rho for a in range(d)]
+    pr = (g - 1.0) * (en - 0.5 * sum(q[1 + a] * v[a] for a in range(d)))
+    vn = sum(v[a] * n[a] for a in range(d))
+    out = [rho * vn] + [q[1 + a] * vn + pr * n[a] for a in range(d)] + [(en + pr) * vn]
+    return np.array(out)
 
 
-def _euler_speed(g, q):
-    rho, m, en = q
-    v = m / rho
-    pr = (g - 1.0) * (en - 0.5 * m * v)
-    return np.abs(v) + np.sqrt(g * pr / rho)
+def _euler_speed(g, q, n=None):
+    d = q.shape[0] - 2
+    rho, en = q[0], q[d + 1]
+    v = [q[1 + a] / rho for a in range(d)]
+    pr = (g - 1.0) * (en - 0.5 * sum(q[1 + a] * v[a] for a in range(d)))
+    vv = np.abs(sum(v[a] * n[a] for a in range(d))) if n is not None else np.sqrt(sum(x * x for x in v))
+    return vv + np.sqrt(g * pr / rho)
 
 
 def euler_residual(P, U):
-    """Euler residual of a 1D mesh.  The volume flux integral uses the (p+2)-point Gauss
-    rule of the scheme (the flux is not a polynomial, so the rule is part of the method);
-    every polynomial integral uses the 24-point rule.  The sensor is the scalar one
-    applied to the density."""
+    """Euler residual on a 1D or 2D mesh.  The flux integrals use the (p+2)-point Gauss
+    rule per direction of the scheme (the flux is not a polynomial, so the rule is part
+    of the method); the polynomial integrals of the stabilization use the 24-point rule.
+    The sensor is the scalar one applied to the density."""
     import dataclasses
+    d = P.dim
     m = Mesh(dataclasses.replace(P, flux="advect"))
-    E, n1, g = P.E, P.p + 1, P.gas_gamma
+    E, g, K = P.E, P.gas_gamma, (P.p + 1) ** d
+    nc = d + 2
     Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b == "reflect" else b for b in P.bc))
     if P.stab in ("weno", "zhao"):
-        gam = sensor(Ps, U[:n1])
+        gam = sensor(Ps, U[:K])
     else:
         gam = np.full(E, 1.0 if P.stab == "lo" else 0.0)
     gq, wq = npleg.leggauss(P.p + 2)
-    L = np.zeros((3 * n1, E))
+    L = np.zeros((nc * K, E))
     for e in range(E):
         c = m.centre(e)
-        ce = [U[comp * n1:(comp + 1) * n1, e] for comp in range(3)]
-        xs = c[0] + 0.5 * m.h * gq
-        q = np.array([m.poly(ce[comp], 0, 0, c, xs, 0 * xs) for comp in range(3)])
-        F = _euler_F(g, q)
-        R = np.zeros((3, n1))
-        for k in range(n1):
-            R[:, k] = (F * m.basis(k, 1, 0, c, xs, 0 * xs) * 0.5 * m.h * wq).sum(axis=1)
-        ends = np.array([c[0] - 0.5 * m.h, c[0] + 0.5 * m.h])
-        lam = max(np.max(_euler_speed(g, q)),
-                  np.max(_euler_speed(g, np.array([m.poly(ce[comp], 0, 0, c, ends, 0 * ends)
-                                                   for comp in range(3)]))))
-        for f in range(2):
-            n = -1.0 if f == 0 else 1.0
-            fx = np.array([c[0] + 0.5 * m.h * n])
-            um = np.array([m.poly(ce[comp], 0, 0, c, fx, 0 * fx)[0] for comp in range(3)])
+        ce = [U[comp * K:(comp + 1) * K, e] for comp in range(nc)]
+        state = lambda X, Y, cc=ce, ctr=c: np.array([m.poly(cc[comp], 0, 0, ctr, X, Y) for comp in range(nc)])
+        if d == 1:
+            X = c[0] + 0.5 * m.h * gq
+            Y = 0 * X
+            W = 0.5 * m.h * wq
+        else:
+            X, Y = np.meshgrid(c[0] + 0.5 * m.h * gq, c[1] + 0.5 * m.h * gq, indexing="xy")
+            X, Y = X.ravel(), Y.ravel()
+            W = np.outer(wq, wq).ravel() * 0.25 * m.h ** 2
+        q = state(X, Y)
+        Fx = _euler_Fn(g, q, (1.0, 0.0))
+        Fy = _euler_Fn(g, q, (0.0, 1.0)) if d == 2 else 0 * Fx
+        R = np.zeros((nc, K))
+        for k in range(K):
+            bx = m.basis(k, 1, 0, c, X, Y)
+            by = m.basis(k, 0, 1, c, X, Y) if d == 2 else 0 * X
+            R[:, k] = ((Fx * bx + Fy * by) * W).sum(axis=1)
+        lam = np.max(_euler_speed(g, q))
+        for f in range(2 * d):
+            n = [(-1.0, 0.0), (1.0, 0.0), (0.0, -1.0), (0.0, 1.0)][f]
+            if d == 1:
+                fx, fy, fw = np.array([c[0] + 0.5 * m.h * n[0]]), np.zeros(1), np.ones(1)
+            elif f < 2:
+                fx, fy, fw = np.full(P.p + 2, c[0] + 0.5 * m.h * n[0]), c[1] + 0.5 * m.h * gq, 0.5 * m.h * wq
+            else:
+                fx, fy, fw = c[0] + 0.5 * m.h * gq, np.full(P.p + 2, c[1] + 0.5 * m.h * n[1]), 0.5 * m.h * wq
+            um = state(fx, fy)
+            lam = max(lam, np.max(_euler_speed(g, um)))
             nb, cn = m.nbr(e, f)
             if nb is not None:
-                up = np.array([m.poly(U[comp * n1:(comp + 1) * n1, nb], 0, 0, cn, fx, 0 * fx)[0]
-                               for comp in range(3)])
+                up = np.array([m.poly(U[comp * K:(comp + 1) * K, nb], 0, 0, cn, fx, fy) for comp in range(nc)])
             elif P.bc[f] == "reflect":
-                up = np.array([um[0], -um[1], um[2]])
+                up = um.copy()
+                mn = sum(um[1 + a] * n[a] for a in range(d))
+                for a in range(d):
+                    up[1 + a] = um[1 + a] - 2.0 * mn * n[a]
             else:
                 up = um.copy()
-            s = max(_euler_speed(g, um), _euler_speed(g, up))
-            H = 0.5 * n * (_euler_F(g, um) + _euler_F(g, up)) - 0.5 * s * (up - um)
-            for k in range(n1):
-                R[:, k] -= m.basis(k, 0, 0, c, fx, 0 * fx)[0] * H
+            s = np.maximum(_euler_speed(g, um, n), _euler_speed(g, up, n))
+            H = 0.5 * (_euler_Fn(g, um, n) + _euler_Fn(g, up, n)) - 0.5 * s * (up - um)
+            for k in range(K):
+                R[:, k] -= (H * m.basis(k, 0, 0, c, fx, fy) * fw).sum(axis=1)
         if gam[e] != 0.0:
             nu = (P.lambda_nu if P.lambda_nu > 0 else lam) * m.h / (2 * P.p)
-            X, Y, W = m.vol_pts(e)
-            for comp in range(3):
-                ux = m.poly(ce[comp], 1, 0, c, X, Y)
-                for k in range(n1):
-                    R[comp, k] -= gam[e] * nu * np.sum(W * m.basis(k, 1, 0, c, X, Y) * ux)
-        for k in range(n1):
-            L[k::n1, e] = R[:, k] / (m.h / (2 * k + 1))
+            X2, Y2, W2 = m.vol_pts(e)
+            for comp in range(nc):
+                ux = m.poly(ce[comp], 1, 0, c, X2, Y2)
+                uy = m.poly(ce[comp], 0, 1, c, X2, Y2) if d == 2 else 0 * X2
+                for k in range(K):
+                    gk = m.basis(k, 1, 0, c, X2, Y2) * ux
+                    if d == 2:
+                        gk = gk + m.basis(k, 0, 1, c, X2, Y2) * uy
+                    R[comp, k] -= gam[e] * nu * np.sum(W2 * gk)
+        for k in range(K):
+            i, j = k % (P.p + 1), k // (P.p + 1)
+            Mkk = m.h / (2 * i + 1)
+            if d == 2:
+                Mkk *= m.h / (2 * j + 1)
+            L[k::K, e] = R[:, k] / Mkk
     return L

@@ -215,3 +215,131 @@ def test_cut_cells_start_from_their_mean():
     assert abs(f[0, cut, 0] - np.sum(w * rho)) < 1e-15
     assert np.all(f[0, :cut] == 1.0) and np.all(f[0, cut + 1:] == 0.125)
     assert d["jumps"] == (0.3,)
+
+
+# ---------------------------------------------------------------------------------
+# 2D Euler system (reading R17)
+# ---------------------------------------------------------------------------------
+def _problem2(nx, ny, p, stab="weno", bc=("periodic",) * 4, box=None, **kw):
+    box = box or (0.0, nx / 8.0, 0.0, ny / 8.0)
+    return O.Problem(dim=2, nx=nx, ny=ny, p=p, flux="euler", stab=stab, bc=tuple(bc), box=box, **kw)
+
+
+def _state2(P, seed, amp=0.02):
+    U = I.random_euler_state(P.p, P.E, seed, amp=amp, dim=2)
+    assert np.isfinite(O.residual(dataclasses.replace(P, stab="lo"), U)).all()   # p > 0, rho > 0 throughout
+    return U
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "lo", "weno", "zhao"])
+@pytest.mark.parametrize("bc", [("periodic",) * 4, ("reflect", "outflow", "reflect", "reflect"),
+                                ("outflow", "outflow", "periodic", "periodic")])
+def test_2d_residual_matches_brute_force(p, stab, bc):
+    P = _problem2(4, 3, p, stab, bc)
+    U = _state2(P, 7 * p + len(stab))
+    a, b = O.residual(P, U), B.euler_residual(P, U)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "lo", "weno"])
+def test_2d_free_stream_and_conservation(p, stab):
+    """A constant state is steady (moving, periodic; at rest, between walls); the total
+    rates of all four components vanish with periodic sides, and of mass and energy
+    between walls."""
+    K = (p + 1) ** 2
+    for bc, v in ((("periodic",) * 4, (0.4, -0.3)), (("reflect",) * 4, (0.0, 0.0))):
+        P = _problem2(5, 4, p, stab, bc)
+        U = np.zeros((P.K, P.E))
+        rho, pr = 1.2, 0.8
+        U[0], U[K], U[2 * K] = rho, rho * v[0], rho * v[1]
+        U[3 * K] = pr / (G - 1) + 0.5 * rho * (v[0] ** 2 + v[1] ** 2)
+        assert np.abs(O.residual(P, U)).max() < 1e-12
+    L = O.residual(_problem2(5, 4, p, stab), _state2(_problem2(5, 4, p, stab), 3 + p))
+    for c in range(4):
+        assert abs(L[c * K].sum()) < 1e-12 * np.abs(L[c * K]).max()
+    P = _problem2(5, 4, p, stab, ("reflect",) * 4)
+    L = O.residual(P, _state2(P, 9 + p))
+    for c in (0, 3):
+        assert abs(L[c * K].sum()) < 1e-12 * np.abs(L[c * K]).max()
+
+
+def test_2d_wall_flux_and_llf():
+    """At a wall of normal n the LLF flux of the mirrored pair is (0, (rho (v.n)^2 + p +
+    s rho v.n) n, 0); H(u, u, n) = F(u) n written out; H(a, b, n) = -H(b, a, -n)."""
+    P = _problem2(4, 4, 1, "dg", ("reflect",) * 4)
+    rho, vx, vy, pr = 1.1, 0.3, -0.2, 0.9
+    q = np.array([rho, rho * vx, rho * vy, pr / (G - 1) + 0.5 * rho * (vx * vx + vy * vy)])
+    c = np.sqrt(G * pr / rho)
+    for n in ((1.0, 0.0), (0.0, -1.0), (0.6, 0.8)):
+        vn = vx * n[0] + vy * n[1]
+        mn = rho * vn
+        ghost = q.copy()
+        ghost[1:3] -= 2 * mn * np.array(n)
+        H = O.euler_llf(P, q, ghost, n)
+        s = abs(vn) + c
+        assert abs(H[0]) < 1e-15 and abs(H[3]) < 1e-14
+        assert np.allclose(H[1:3], (rho * vn * vn + pr + s * rho * vn) * np.array(n), rtol=1e-14, atol=1e-15)
+        F = np.array([rho * vn, rho * vx * vn + pr * n[0], rho * vy * vn + pr * n[1], (q[3] + pr) * vn])
+        assert np.allclose(O.euler_llf(P, q, q, n), F, rtol=1e-14, atol=1e-15)
+        b = np.array([0.9, 0.1, 0.2, 2.0])
+        assert np.allclose(O.euler_llf(P, q, b, n), -O.euler_llf(P, b, q, (-n[0], -n[1])), rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "lo"])
+def test_2d_reduces_to_1d(p, stab):
+    """A state independent of y with vy = 0 on a mesh periodic in y: the y-mean modes
+    of the 2D residual are the 1D residual and every other mode is zero (DG and LO; the
+    WENO sensor sees four candidates in 2D and two in 1D)."""
+    n1, K = p + 1, (p + 1) ** 2
+    P1 = _problem(9, p, stab, ("reflect", "outflow"), box=(0.0, 9 / 8.0))
+    U1 = _random_state(P1, 31 + p)
+    P2 = _problem2(9, 3, p, stab, ("reflect", "outflow", "periodic", "periodic"))
+    U2 = np.zeros((P2.K, P2.E))
+    for comp2, comp1 in ((0, 0), (1, 1), (3, 2)):
+        for i in range(n1):
+            U2[comp2 * K + i] = np.tile(U1[comp1 * n1 + i], 3)
+    L1, L2 = O.residual(P1, U1), O.residual(P2, U2)
+    for comp2, comp1 in ((0, 0), (1, 1), (3, 2)):
+        for i in range(n1):
+            assert np.allclose(L2[comp2 * K + i], np.tile(L1[comp1 * n1 + i], 3), rtol=1e-12, atol=1e-12)
+        assert np.abs(L2[comp2 * K + n1:(comp2 + 1) * K]).max() < 1e-11
+    assert np.abs(L2[2 * K:3 * K]).max() < 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "weno", "zhao"])
+def test_2d_transpose_symmetry(p, stab):
+    """Swapping x and y (a square mesh, the two momenta exchanged, mode (i, j) -> (j, i))
+    maps residuals onto residuals: the y-direction code agrees with the x-direction
+    code."""
+    n1, K = p + 1, (p + 1) ** 2
+    bc = ("reflect", "reflect", "outflow", "outflow")
+    P = _problem2(6, 6, p, stab, bc)
+    Pt = _problem2(6, 6, p, stab, ("outflow", "outflow", "reflect", "reflect"))
+    U = _state2(P, 41 + p)
+
+    def transpose(V):
+        W = np.zeros_like(V)
+        for comp in range(4):
+            ct = {0: 0, 1: 2, 2: 1, 3: 3}[comp]
+            for k in range(K):
+                i, j = k % n1, k // n1
+                W[ct * K + j + n1 * i] = V[comp * K + k].reshape(6, 6).T.reshape(-1)
+        return W
+
+    assert np.allclose(O.residual(Pt, transpose(U)), transpose(O.residual(P, U)), rtol=1e-11, atol=1e-11)
+
+
+def test_2d_inputs_are_face_aligned_at_the_paper_sizes():
+    """The Kelvin-Helmholtz strip and the triple point's subdomains end on cell faces at
+    the paper's meshes, so no cell starts from a mean there; the samples carry the
+    stated states."""
+    for name in ("kelvin_helmholtz", "triple_point"):
+        d = I.EULER_2D[name]
+        f = I.euler2d_samples(name, d["nx"], d["ny"], 4).reshape(4, d["nx"] * d["ny"], 16)
+        rho = f[0]
+        assert np.all((rho.max(axis=1) == rho.min(axis=1)) | (name == "kelvin_helmholtz"))
+        assert set(np.unique(rho)) <= {1.0, 2.0, 0.125}
