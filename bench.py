@@ -57,6 +57,13 @@ for _name, _nx, _p in (("sod", 128, 2), ("shu_osher", 512, 3)):
                                              bc=tuple(_d["bc"]) + ("periodic", "periodic"), flux="euler",
                                              stab="weno", cfl=I.euler_cfl(_p), speeds=(_d["lam"],),
                                              u0="tube:" + _name, t_end=_d["t_end"])
+# the 2D Euler problems of Sec. 5.6: Kelvin-Helmholtz at the paper's 512^2 cells (p = 2, to
+# t = 1.0) and on 2048^2 cells (state arrays above L2), the triple point at 896 x 384
+for _name, _nx, _ny in (("kelvin_helmholtz", 512, 512), ("kelvin_helmholtz", 2048, 2048), ("triple_point", 896, 384)):
+    _d = I.EULER_2D[_name]
+    WORKLOADS[f"{_name}_{_nx}x{_ny}_q2"] = dict(dim=2, nx=_nx, ny=_ny, p=2, box=_d["box"], bc=_d["bc"], flux="euler",
+                                                stab="weno", cfl=I.euler_cfl(2, 2), speeds=(_d["lam"], _d["lam"]),
+                                                u0="euler2d:" + _name, t_end=_d["t_end"])
 WORKLOADS["sod_train_4194304_q2"] = dict(dim=1, nx=1 << 22, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0),
                                          bc=("periodic",) * 4, flux="euler", stab="weno",
                                          cfl=I.euler_cfl(2), speeds=(2.5,), u0="sod_train")
@@ -75,6 +82,8 @@ def initial_samples(w):
         f = I.u0_kpp(X, Y)
     elif w["u0"] == "rotation":
         f = I.u0_rotation(X, Y)
+    elif w["u0"].startswith("euler2d:"):
+        f = I.euler2d_samples(w["u0"][8:], w["nx"], w["ny"], 8)
     elif w["u0"].startswith("tube:"):
         f = I.shock_tube_samples(w["u0"][5:], w["nx"], 8)
     elif w["u0"] == "sod_train":
@@ -85,12 +94,14 @@ def initial_samples(w):
 
 
 def dofs_of(w):
-    """State rows times cells: (p+1)^dim modes, three components for the Euler system."""
-    return w["nx"] * w["ny"] * (w["p"] + 1) ** w["dim"] * (3 if w["flux"] == "euler" else 1)
+    """State rows times cells: (p+1)^dim modes, dim + 2 components for the Euler system."""
+    return w["nx"] * w["ny"] * (w["p"] + 1) ** w["dim"] * (w["dim"] + 2 if w["flux"] == "euler" else 1)
 
 
 def dt_of(w):
     h = (w["box"][1] - w["box"][0]) / w["nx"]
+    if w["flux"] == "euler":        # dt = CFL h / lam, the CFL already halved in 2D
+        return w["cfl"] * h / w["speeds"][0]
     return I.cfl_dt(w["cfl"], w["speeds"], [h] * w["dim"])
 
 
@@ -505,7 +516,11 @@ def main():
                             run_small("sod_train_4194304_q2", "fp32", 200, 5, local),
                             run_small("sod_train_4194304_q2", "fp64", 100, 5, local),
                             run_small("sod_128_q2", "fp64", 739, 10, local),
-                            run_small("shu_osher_512_q3", "fp64", 9216, 10, local)]
+                            run_small("shu_osher_512_q3", "fp64", 9216, 10, local),
+                            run_small("kelvin_helmholtz_512x512_q2", "fp32", 200, 5, local),
+                            run_small("kelvin_helmholtz_512x512_q2", "fp64", 20, 3, local),
+                            run_small("kelvin_helmholtz_2048x2048_q2", "fp32", 50, 3, local),
+                            run_small("triple_point_896x384_q2", "fp32", 200, 5, local)]
     if rank != 0:
         return
     hbm, src = peaks()

@@ -8,16 +8,16 @@
  * (Eq. fesol; Q_p on quadrilaterals), the local Lax-Friedrichs flux (Sec. 2), the
  * dissipative stabilization gamma_e nu_e int grad(phi).grad(U_h) (Sec. 3, Eq. astab,
  * with Eq. visc for nu_e) driven by the WENO sensor of Sec. 4 (Eq. sensor / gensensor),
- * and advanced by the optimal SSP-RK3 scheme (Eq. ssp).  In 1D also the Euler equations
- * of gas dynamics (Sec. 5.6) with the same scheme and a density-driven sensor.
+ * and advanced by the optimal SSP-RK3 scheme (Eq. ssp).  Also the Euler equations of gas
+ * dynamics (Sec. 5.6) in 1D and 2D with the same scheme and a density-driven sensor.
  *
  * Conventions shared by every entry point
  *  - State arrays ("U") are device arrays owned by the caller, mode-major
  *    (structure of arrays): U[k*E + e] with element e = iy*nx + ix and mode
  *    k = i + (p+1)*j (i: Legendre degree in x, j: in y; 1D: k = i).  K = (p+1)^dim
- *    modes, E = nx (1D) or nx*ny (2D) elements.  The Euler system stacks its three
- *    components: row comp*(p+1) + k holds mode k of rho (comp 0), rho v (1) and
- *    rho E (2), so K = 3(p+1) rows.  The element type is double for
+ *    modes, E = nx (1D) or nx*ny (2D) elements.  The Euler system stacks its dim + 2
+ *    components: row comp*(p+1)^dim + k holds mode k of rho (comp 0), the momentum
+ *    components (1 .. dim) and rho E (dim + 1), so K = (dim + 2)(p+1)^dim rows.  The element type is double for
  *    DGW_FP64 contexts and float for DGW_FP32 contexts.  Base addresses must be
  *    aligned to 16 bytes.
  *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
@@ -56,8 +56,8 @@ typedef enum {
     DGW_BC_INFLOW_ZERO = 1, /* ghost U+ = 0 where F'(U-).n < 0, U+ = U- elsewhere
                                (scalar laws only) */
     DGW_BC_OUTFLOW = 2,     /* ghost U+ = U- */
-    DGW_BC_REFLECT = 3      /* Euler system only: reflecting wall, ghost (rho, -rho v, rho E)
-                               (Sec. 5.6 shock tubes) */
+    DGW_BC_REFLECT = 3      /* Euler system only: reflecting wall, ghost state with the
+                               normal momentum mirrored, (rho, m - 2 (m.n) n, rho E) */
 } dgw_bc;
 
 /* Cartesian mesh of [x0,x1] (1D) or [x0,x1]x[y0,y1] (2D) with nx (x ny) equal cells.
@@ -76,13 +76,13 @@ typedef enum {
     DGW_FLUX_ROTATION = 1,  /* F = omega (cy - y, x - cx) u   (solid body)      */
     DGW_FLUX_BURGERS = 2,   /* F = (a0, a1) u^2 / 2                            */
     DGW_FLUX_KPP = 3,       /* F = (sin u, cos u)                              */
-    DGW_FLUX_EULER = 4      /* 1D Euler system (Sec. 5.6): U = (rho, rho v, rho E),
-                               F = (rho v, rho v^2 + p, (rho E + p) v),
-                               p = (gas_gamma - 1)(rho E - rho v^2 / 2); the LLF speed
-                               s+ is the larger |v| + c of the two states; the sensor is
-                               computed from the density and applied to all three
-                               components; no positivity safeguard: a negative density
-                               or pressure gives non-finite results (dgw_sync_status) */
+    DGW_FLUX_EULER = 4      /* Euler system (Sec. 5.6), 1D or 2D: U = (rho, rho v, rho E),
+                               F(U) n = (rho v.n, rho v (v.n) + p n, (rho E + p) v.n),
+                               p = (gas_gamma - 1)(rho E - rho |v|^2 / 2); the LLF speed
+                               s+ is the larger |v.n| + c of the two states; the sensor is
+                               computed from the density and applied to every component;
+                               no positivity safeguard: a negative density or pressure
+                               gives non-finite results (dgw_sync_status) */
 } dgw_flux_kind;
 
 typedef struct {
@@ -93,7 +93,7 @@ typedef struct {
     double lambda_nu;       /* > 0: fixed lambda_e in nu_e = lambda_e h / (2p) (the paper
                                uses 2.0 for KPP); 0: max |F'(U_h)|_2 over the element's
                                volume and face Gauss points (Euler: max |v| + c over the
-                               p+2 Gauss points and the two end points) */
+                               same points, the element's own values on its faces) */
     double gas_gamma;       /* Euler system: ratio of heat capacities (> 1; the paper and
                                dgw_defaults use 1.4); ignored by the scalar fluxes */
 } dgw_flux;
@@ -134,8 +134,8 @@ typedef struct dgw_ctx dgw_ctx;
 void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s);
 
 /* Creates a context for degree p (1..3) on the current device: checks the arguments
- * (DGW_FLUX_EULER: 1D meshes only, else DGW_EUNSUPPORTED; DGW_BC_REFLECT only with it and
- * DGW_BC_INFLOW_ZERO only without it, else DGW_EINVAL),
+ * (DGW_BC_REFLECT only with DGW_FLUX_EULER and DGW_BC_INFLOW_ZERO only without it, else
+ * DGW_EINVAL),
  * builds the operator tables (Gauss rule of p+2 points, Legendre values, Hermite
  * shift matrices, seminorm Gram matrix, stiffness) in double, uploads them, and
  * allocates the two RK stage buffers (2*K*E elements) plus small scratch.
@@ -158,7 +158,8 @@ dgw_status dgw_set_params(dgw_ctx* ctx, const dgw_params* params);
  * double, E * nq^dim values): f at the nq-point Gauss-Legendre points of each
  * element, sample t = a + nq*b at x = xc + h/2 g_a, y = yc + h/2 g_b.  nq in 1..8.
  * U (device, context precision, K*E) receives c_k = int f phi_k / int phi_k^2.  Euler
- * system: 3 * E * nq samples, those of rho, rho v and rho E one after the other. */
+ * system: (dim + 2) * E * nq^dim samples, those of each conserved variable one after
+ * the other. */
 dgw_status dgw_project(dgw_ctx* ctx, int nq, const double* samples, void* U, void* stream);
 
 /* Semi-discrete right-hand side L = M^{-1} R_stab(U) (Eq. weak2 with s_h^e of Sec. 3):
@@ -187,8 +188,9 @@ dgw_status dgw_rk_step(dgw_ctx* ctx, void* U, double dt, int nsteps, void* strea
 dgw_status dgw_rk_step_host(dgw_ctx* ctx, const void* U_in, void* U_out, double dt,
                             int nsteps, void* stream);
 
-/* Total mass sum_e int_{K_e} U_h dx = sum_e |K_e| c_0^e (Euler: of the density) in double, by a fixed-order
- * tree (bitwise reproducible).  Blocks until the result is on the host. */
+/* Total mass sum_e int_{K_e} U_h dx = sum_e |K_e| c_0^e (Euler: of the density) in
+ * double, by a fixed-order tree (bitwise reproducible).  Blocks until the result is on
+ * the host. */
 dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream);
 
 /* Reads and clears the context's device-side error flag (non-finite stage output).

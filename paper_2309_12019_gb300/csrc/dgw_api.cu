@@ -152,7 +152,6 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
         if (m.bc[f] == DGW_BC_REFLECT && !euler) return fail(DGW_EINVAL, "bc[%d]: reflecting walls are for the Euler system", f);
         if (m.bc[f] == DGW_BC_INFLOW_ZERO && euler) return fail(DGW_EINVAL, "bc[%d]: inflow_zero is for scalar laws", f);
     }
-    if (euler && m.dim != 1) return fail(DGW_EUNSUPPORTED, "the Euler system is built for 1D meshes");
     if (euler && !(flux->gas_gamma > 1.0 && std::isfinite(flux->gas_gamma)))
         return fail(DGW_EINVAL, "gas_gamma must be a finite number > 1");
     dgw_status st = check_params(params, m.dim);
@@ -166,7 +165,7 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
     c->p = p;
     c->flux = *flux;
     c->params = *params;
-    c->K = (m.dim == 1 ? p + 1 : (p + 1) * (p + 1)) * (euler ? 3 : 1);
+    c->K = (m.dim == 1 ? p + 1 : (p + 1) * (p + 1)) * (euler ? m.dim + 2 : 1);
     c->E = E;
     c->eb = params->prec == DGW_FP64 ? 8 : 4;
     c->h = hx;
@@ -273,7 +272,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U, int kind = 0)
 {
     dgw_ctx* c = const_cast<dgw_ctx*>(cc);
-    if (c->mesh.dim != 2 || !U) return nullptr;
+    if (c->mesh.dim != 2 || !U || c->flux.kind == DGW_FLUX_EULER) return nullptr;   // the Euler kernel stages by plain loads
     const auto key = std::make_pair(U, kind);
     auto it = c->tmaps.find(key);
     if (it != c->tmaps.end()) return &it->second;
@@ -664,7 +663,7 @@ extern "C" dgw_status dgw_rk_step_host(dgw_ctx* c, const void* U_in, void* U_out
     cudaStream_t s = (cudaStream_t)stream;
     const int rows = stage_rows(c->eb == 8);
     const bool pipelined = c->mesh.dim == 2 && c->mesh.bc[2] != DGW_BC_PERIODIC && c->mesh.ny >= 2 * rows &&
-                           c->params.rk_order == 3;
+                           c->params.rk_order == 3 && c->flux.kind != DGW_FLUX_EULER;
     if (!pipelined) {
         DGW_CUDA(cudaMemcpyAsync(c->Uhost_dev, U_in, bytes, cudaMemcpyHostToDevice, s));
         st = dgw_rk_step(c, c->Uhost_dev, dt, nsteps, stream);
@@ -750,7 +749,7 @@ extern "C" dgw_status dgw_project(dgw_ctx* c, int nq, const double* samples, voi
     const int threads = 128;
     const int64_t blocks = (c->E + threads - 1) / threads;
     // the Euler system: one projection per component (samples and rows component-major)
-    const int ncomp = c->flux.kind == DGW_FLUX_EULER ? 3 : 1;
+    const int ncomp = c->flux.kind == DGW_FLUX_EULER ? c->mesh.dim + 2 : 1;
     const int64_t npt = c->mesh.dim == 1 ? nq : nq * nq;
     for (int comp = 0; comp < ncomp; ++comp) {
         a.f = samples + comp * c->E * npt;

@@ -1,0 +1,441 @@
+// Stage kernel of the 2D Euler system (Sec. 5.6, its 2D problems), included by the 2D
+// stage translation units after the scalar kernel (it shares the tables, the launch
+// scalars and the math helpers of dgw_stage_impl.cuh).
+//
+// State U = (rho, rho vx, rho vy, rho E), p = (gamma - 1)(rho E - rho |v|^2 / 2); mode
+// k = i + (p+1) j of component comp of cell e at row comp K + k, K = (p+1)^2.
+// One CTA of EX x EY = 32 x 4 threads owns a tile of as many cells, one per thread:
+//   0. the tile's coefficients and a one-cell face halo (all four components) are
+//      staged in shared memory by coalesced row loads; halo cells beyond a periodic side
+//      are its images, beyond a wall or an outflow side they are absent
+//   1. per cell: the sensor of Sec. 4 on the density, the volume term at the (p+2)^2
+//      Gauss points by sum factorisation, lambda_e over those points
+//   2. every face of the tile once: both traces at the p+2 Gauss points, the ghost
+//      state at a boundary (a wall mirrors the normal momentum), the LLF flux with s+
+//      the larger |v.n| + c, lifted onto the face's Legendre modes; the largest own-side
+//      |v| + c of each face for lambda_e
+//   3. per cell: face terms, the stabilization of every component with the density's
+//      gamma, M^{-1} and the Runge-Kutta combination Uout = cn Un + ck Uk + cl L(Uk)
+// Constants are folded as in the scalar kernel:
+//   L_k = (2/h) minv(i) minv(j) [acc_k - gamma lambda / p (K_ref c)_k].
+
+constexpr int EX = kTileX2, EY = kTileY2, ENT = EX * EY;
+constexpr int EHX = EX + 2, EHY = EY + 2;          // staged columns / rows (one halo cell)
+
+template <int P>
+struct Euler2Smem {
+    static constexpr int N1 = P + 1, K = N1 * N1;
+    Real u[4][K][EHY][EHX];         // coefficients; tile cell (lx, ly) at [ly + 1][lx + 1]
+    Real hx[4][N1][EY][EX + 1];     // lifted LLF flux of x-face f of row r (cells f - 1, f)
+    Real hy[4][N1][EY + 1][EX];     // lifted LLF flux of y-face r of column c (cells r - 1, r)
+    Real sx[2][EY][EX + 1];         // max |v| + c of the minus (0) / plus (1) cell's own values on x-face f
+    Real sy[2][EY + 1][EX];         // the same on y-face r
+    int has[EHY][EHX];              // the staged cell exists
+};
+
+struct Euler2State {
+    Real vx, vy, pr, inv_rho;
+};
+
+__device__ __forceinline__ Euler2State euler2_prim(const KParams& A, const Real* q)
+{
+    Euler2State s;
+    s.inv_rho = rcp_e(q[0]);
+    s.vx = q[1] * s.inv_rho;
+    s.vy = q[2] * s.inv_rho;
+    s.pr = A.gm1 * (q[3] - Real(0.5) * (q[1] * s.vx + q[2] * s.vy));
+    return s;
+}
+
+// |v.n| + c for an axis normal (axis 0: x, 1: y), or |v| + c for axis < 0
+__device__ __forceinline__ Real euler2_speed(const KParams& A, const Euler2State& s, int axis)
+{
+    const Real c = sqrt_e(A.gam * s.pr * s.inv_rho);
+    const Real v = axis == 0 ? fabs(s.vx) : (axis == 1 ? fabs(s.vy) : sqrt_e(s.vx * s.vx + s.vy * s.vy));
+    return v + c;
+}
+
+// F(U) e_axis
+__device__ __forceinline__ void euler2_flux(const Euler2State& s, const Real* q, int axis, Real* F)
+{
+    const Real vn = axis == 0 ? s.vx : s.vy;
+    F[0] = q[0] * vn;
+    F[1] = q[1] * vn + (axis == 0 ? s.pr : Real(0));
+    F[2] = q[2] * vn + (axis == 1 ? s.pr : Real(0));
+    F[3] = (q[3] + s.pr) * vn;
+}
+
+// Sensor of Sec. 4 (or Zhao et al.'s, stab = ZHAO) of a 2D cell from the density
+// coefficients of the cell (c) and of its face neighbours at staged position (r, col).
+template <int P>
+__device__ __forceinline__ Real sensor_2d(const KParams& A, const Tab<P>& T, const Real* c,
+                                          const Euler2Smem<P>& S, int r, int col)
+{
+    constexpr int N1 = P + 1, K = N1 * N1;
+    bool has[4];
+    int me = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const int rr = r + (f == 2 ? -1 : (f == 3 ? 1 : 0)), cc = col + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+        has[f] = S.has[rr][cc] != 0;
+        me += has[f] ? 1 : 0;
+    }
+    const Real beta0 = qform<P>(T, c);
+    const Real d0 = A.eps_w + beta0;
+    const Real w0 = div_w(Real(1) - Real(me) * A.w_nbr, d0 * d0);
+    Real wsum = w0;
+    Real wnb[4];
+    Real dacc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) dacc[k] = Real(0);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        wnb[f] = Real(0);
+        if (!has[f]) continue;
+        const int axis = f >> 1, side = f & 1;
+        const int rr = r + (f == 2 ? -1 : (f == 3 ? 1 : 0)), cc = col + (f == 0 ? -1 : (f == 1 ? 1 : 0));
+        // Hermite candidate: the neighbour's polynomial continued into this cell (its
+        // mean does not enter the seminorms)
+        Real cl[K];
+        cl[0] = Real(0);
+#pragma unroll
+        for (int k = 1; k < K; ++k) {
+            const int i = k % N1, j = k / N1;
+            const int a = axis == 0 ? i : j;
+            Real s = Real(0);
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                if (m < a) continue;
+                const int km = axis == 0 ? m + N1 * j : i + N1 * m;
+                s = fma(T.T[side][a][m], S.u[0][km][rr][cc], s);
+            }
+            cl[k] = s;
+        }
+        const Real dl = A.eps_w + qform<P>(T, cl);
+        const Real wl = div_w(A.w_nbr, dl * dl);
+        wsum += wl;
+        wnb[f] = wl;
+#pragma unroll
+        for (int k = 1; k < K; ++k) dacc[k] = fma(wl, c[k] - cl[k], dacc[k]);
+    }
+    const Real inv = div_w(Real(1), wsum);
+    if (A.stab == STAB_ZHAO) {
+        if (me == 0) return Real(0);
+        const Real lin0 = Real(1) - Real(me) * A.w_nbr;
+        Real dev = zpow(A, fabs(w0 * inv / lin0 - Real(1)));
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+            if (has[f]) dev += zpow(A, fabs(wnb[f] * inv / A.w_nbr - Real(1)));
+        const Real minlin = lin0 < A.w_nbr ? lin0 : A.w_nbr;
+        return dev * rcp_e(zpow(A, fabs(rcp_e(minlin) - Real(1))) + Real(me));
+    }
+#pragma unroll
+    for (int k = 1; k < K; ++k) dacc[k] *= inv;
+    dacc[0] = Real(0);
+    const Real qd = fmax(qform<P>(T, dacc), Real(0));
+    if (qd <= A.eps_s * A.eps_s) return Real(0);
+    if (beta0 <= Real(0)) return Real(1);
+    const Real r2 = qd * rcp_e(beta0);
+    Real g = r2 < Real(1) ? sqrt_e(r2) : Real(1);
+    if (!A.q_one) g = pow(g, A.q);
+    if (r2 < A.b * A.b) g = Real(0);
+    return g;
+}
+
+// MODE 0: stage / residual; MODE 1: sensor only (writes gamma_out).
+template <int P, int MODE>
+__global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __grid_constant__ KParams A)
+{
+    constexpr int N1 = P + 1, NQ = P + 2, K = N1 * N1;
+    extern __shared__ __align__(16) unsigned char smem_e2[];
+    Euler2Smem<P>& S = *reinterpret_cast<Euler2Smem<P>*>(smem_e2);
+    const Tab<P>& T = tab<P>();
+    const int tid = threadIdx.x;
+    const int64_t E = A.E;
+    const int tx0 = blockIdx.x * EX, ty0 = blockIdx.y * EY;
+    // ---- 0. stage the tile and its face halo ----
+    for (int idx = tid; idx < EHY * EHX; idx += ENT) {
+        const int r = idx / EHX, cc = idx - r * EHX;
+        const bool corner = (r == 0 || r == EHY - 1) && (cc == 0 || cc == EHX - 1);
+        const int gx = wrap_x(A, tx0 - 1 + cc), gy = wrap_y(A, ty0 - 1 + r);
+        const bool ok = !corner && gx >= 0 && gy >= 0;
+        S.has[r][cc] = ok;
+        const Real* src = A.Uk + (ok ? (int64_t)gy * A.nx + gx : 0);
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+            for (int k = 0; k < K; ++k) S.u[comp][k][r][cc] = ok ? src[(int64_t)(comp * K + k) * E] : Real(0);
+    }
+    const int lx = tid % EX, ly = tid / EX;
+    const int gx = tx0 + lx, gy = ty0 + ly;
+    const bool in = gx < A.nx && gy < A.ny;
+    const int64_t e = (int64_t)gy * A.nx + gx;
+    // Un is read only at the end: issue its loads now where registers allow (p <= 2)
+    constexpr bool kPrefetch = K <= 9;
+    Real un[4][kPrefetch ? K : 1];
+    if (kPrefetch && MODE == 0 && A.has_un && in) {
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const Real* a = A.Un + e + (int64_t)(comp * K + k) * E;
+                un[comp][k] = A.cg_loads ? __ldcg(a) : *a;
+            }
+    }
+    __syncthreads();
+
+    // ---- 1. sensor of the density; volume term; lambda_e over the volume points ----
+    const int r0 = ly + 1, c0 = lx + 1;
+    Real gamma = (MODE == 0 && A.stab == STAB_LO) ? Real(1) : Real(0);
+    if (in && (MODE == 1 || A.stab >= STAB_WENO)) {
+        Real c[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) c[k] = S.u[0][k][r0][c0];
+        gamma = sensor_2d<P>(A, T, c, S, r0, c0);
+        if (MODE == 1) A.gamma_out[e] = (double)gamma;
+    }
+    if (MODE == 1) return;
+
+    const bool need_lam = A.stab != STAB_DG && !A.lam_fixed;
+    Real acc[4][K];
+#pragma unroll
+    for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[comp][k] = Real(0);
+    Real lam = Real(0);
+    if (in) {
+#pragma unroll
+        for (int qy = 0; qy < NQ; ++qy) {
+            // row[comp][i] = sum_j B[qy][j] c_comp[i + N1 j]: the polynomial on the line y = g_qy
+            Real row[4][N1];
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+                for (int i = 0; i < N1; ++i) {
+                    Real s = Real(0);
+#pragma unroll
+                    for (int j = 0; j < N1; ++j) s = fma(T.B[qy][j], S.u[comp][i + N1 * j][r0][c0], s);
+                    row[comp][i] = s;
+                }
+            Real px[4][N1], py[4][N1];
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+                for (int i = 0; i < N1; ++i) { px[comp][i] = Real(0); py[comp][i] = Real(0); }
+#pragma unroll
+            for (int qx = 0; qx < NQ; ++qx) {
+                Real q[4];
+#pragma unroll
+                for (int comp = 0; comp < 4; ++comp) {
+                    Real s = Real(0);
+#pragma unroll
+                    for (int i = 0; i < N1; ++i) s = fma(T.B[qx][i], row[comp][i], s);
+                    q[comp] = s;
+                }
+                const Euler2State st = euler2_prim(A, q);
+                Real Fx[4], Fy[4];
+                euler2_flux(st, q, 0, Fx);
+                euler2_flux(st, q, 1, Fy);
+                if (need_lam) lam = max_nan(lam, euler2_speed(A, st, -1));
+#pragma unroll
+                for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+                    for (int i = 0; i < N1; ++i) {
+                        px[comp][i] = fma(T.WD[qx][i], Fx[comp], px[comp][i]);
+                        py[comp][i] = fma(T.WB[qx][i], Fy[comp], py[comp][i]);
+                    }
+            }
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+                for (int j = 0; j < N1; ++j)
+#pragma unroll
+                    for (int i = 0; i < N1; ++i)
+                        acc[comp][i + N1 * j] =
+                            fma(T.WB[qy][j], px[comp][i], fma(T.WD[qy][j], py[comp][i], acc[comp][i + N1 * j]));
+        }
+    }
+
+    // ---- 2. faces: x-faces f = 0..EX of each row, y-faces r = 0..EY of each column ----
+    constexpr int NFX = (EX + 1) * EY, NFY = EX * (EY + 1);
+    for (int item = tid; item < NFX + NFY; item += ENT) {
+        const bool xf = item < NFX;
+        int rm, cm, rp, cp, fr, fc;       // staged positions of the minus / plus cell; face index
+        if (xf) {
+            fr = item / (EX + 1);
+            fc = item - fr * (EX + 1);
+            rm = rp = fr + 1;
+            cm = fc;
+            cp = fc + 1;
+        } else {
+            const int it = item - NFX;
+            fr = it / EX;
+            fc = it - fr * EX;
+            cm = cp = fc + 1;
+            rm = fr;
+            rp = fr + 1;
+        }
+        // the face exists if the cell on either side is a cell of this tile in the mesh
+        const int gxm = tx0 + cm - 1, gym = ty0 + rm - 1, gxp = tx0 + cp - 1, gyp = ty0 + rp - 1;
+        const bool tile_m = (xf ? cm >= 1 : rm >= 1) && gxm < A.nx && gym < A.ny && gxm >= 0 && gym >= 0;
+        const bool tile_p = (xf ? cp <= EX : rp <= EY) && gxp < A.nx && gyp < A.ny;
+        if (!(tile_m && (xf ? cm <= EX : rm <= EY)) && !tile_p) continue;
+        const bool has_m = S.has[rm][cm] != 0, has_p = S.has[rp][cp] != 0;
+        const int axis = xf ? 0 : 1;
+        // trace coefficients along the face (Legendre index t), both sides, all components
+        Real tm[4][N1], tp[4][N1];
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+            for (int t = 0; t < N1; ++t) {
+                Real sm = Real(0), sp = Real(0);
+#pragma unroll
+                for (int n = 0; n < N1; ++n) {
+                    const int k = xf ? n + N1 * t : t + N1 * n;
+                    sm += S.u[comp][k][rm][cm];                                    // xi = +1 of the minus cell
+                    sp += (n & 1) ? -S.u[comp][k][rp][cp] : S.u[comp][k][rp][cp];  // xi = -1 of the plus cell
+                }
+                tm[comp][t] = sm;
+                tp[comp][t] = sp;
+            }
+        Real hq[4][N1];
+#pragma unroll
+        for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+            for (int t = 0; t < N1; ++t) hq[comp][t] = Real(0);
+        Real spm = Real(0), spp = Real(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            Real um[4], up[4];
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp) {
+                Real a = Real(0), b = Real(0);
+#pragma unroll
+                for (int t = 0; t < N1; ++t) { a = fma(T.B[q][t], tm[comp][t], a); b = fma(T.B[q][t], tp[comp][t], b); }
+                um[comp] = a;
+                up[comp] = b;
+            }
+            if (!has_m) {          // ghost for the plus cell (outward normal -e_axis)
+                const bool refl = A.bc[xf ? 0 : 2] == BC_REFLECT;
+#pragma unroll
+                for (int comp = 0; comp < 4; ++comp) um[comp] = up[comp];
+                if (refl) um[1 + axis] = -up[1 + axis];
+            } else if (!has_p) {   // ghost for the minus cell (outward normal +e_axis)
+                const bool refl = A.bc[xf ? 1 : 3] == BC_REFLECT;
+#pragma unroll
+                for (int comp = 0; comp < 4; ++comp) up[comp] = um[comp];
+                if (refl) up[1 + axis] = -um[1 + axis];
+            }
+            const Euler2State sl = euler2_prim(A, um), sr = euler2_prim(A, up);
+            Real Fl[4], Fr[4];
+            euler2_flux(sl, um, axis, Fl);
+            euler2_flux(sr, up, axis, Fr);
+            const Real snl = euler2_speed(A, sl, axis), snr = euler2_speed(A, sr, axis);
+            const Real s = max_nan(snl, snr);
+            if (need_lam) {
+                spm = max_nan(spm, euler2_speed(A, sl, -1));
+                spp = max_nan(spp, euler2_speed(A, sr, -1));
+            }
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp) {
+                const Real H = Real(0.5) * ((Fl[comp] + Fr[comp]) - s * (up[comp] - um[comp]));
+#pragma unroll
+                for (int t = 0; t < N1; ++t) hq[comp][t] = fma(T.WB[q][t], H, hq[comp][t]);
+            }
+        }
+        if (xf) {
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+                for (int t = 0; t < N1; ++t) S.hx[comp][t][fr][fc] = hq[comp][t];
+            S.sx[0][fr][fc] = spm;
+            S.sx[1][fr][fc] = spp;
+        } else {
+#pragma unroll
+            for (int comp = 0; comp < 4; ++comp)
+#pragma unroll
+                for (int t = 0; t < N1; ++t) S.hy[comp][t][fr][fc] = hq[comp][t];
+            S.sy[0][fr][fc] = spm;
+            S.sy[1][fr][fc] = spp;
+        }
+    }
+    __syncthreads();
+    if (!in) return;
+
+    // ---- 3. face terms, stabilization, M^{-1}, Runge-Kutta combination ----
+    if (need_lam)
+        lam = max_nan(lam, max_nan(max_nan(S.sx[1][ly][lx], S.sx[0][ly][lx + 1]),
+                                   max_nan(S.sy[1][ly][lx], S.sy[0][ly + 1][lx])));
+    const Real ngs = A.stab == STAB_DG ? Real(0) : -(gamma * (A.lam_fixed ? A.lambda_nu : lam) * Real(1.0 / P));
+    Real chk = Real(0);
+#pragma unroll
+    for (int comp = 0; comp < 4; ++comp) {
+#pragma unroll
+        for (int t = 0; t < N1; ++t) {
+            // even n: += (m - p); odd n: -= (m + p)
+            const Real xm = S.hx[comp][t][ly][lx], xp = S.hx[comp][t][ly][lx + 1];
+            const Real ym = S.hy[comp][t][ly][lx], yp = S.hy[comp][t][ly + 1][lx];
+#pragma unroll
+            for (int n = 0; n < N1; ++n) {
+                acc[comp][n + N1 * t] += (n & 1) ? -(xm + xp) : (xm - xp);
+                acc[comp][t + N1 * n] += (n & 1) ? -(ym + yp) : (ym - yp);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = k % N1, j = k / N1;
+            Real r = acc[comp][k];
+            Real s1 = Real(0), s2 = Real(0);
+#pragma unroll
+            for (int m = 1; m < N1; ++m) {
+                if (((i + m) & 1) == 0 && i > 0) s1 = fma(T.A1[i][m], S.u[comp][m + N1 * j][r0][c0], s1);
+                if (((j + m) & 1) == 0 && j > 0) s2 = fma(T.A1[j][m], S.u[comp][i + N1 * m][r0][c0], s2);
+            }
+            r = fma(ngs, fma(T.A0[i], s2, T.A0[j] * s1), r);
+            const Real Lk = (A.two_h * (T.minv[i] * T.minv[j])) * r;
+            Real out = fma(A.cl, Lk, A.ck * S.u[comp][k][r0][c0]);
+            if (A.has_un) {
+                Real unk;
+                if constexpr (kPrefetch) {
+                    unk = un[comp][k];
+                } else {
+                    const Real* a = A.Un + e + (int64_t)(comp * K + k) * E;
+                    unk = A.cg_loads ? __ldcg(a) : *a;
+                }
+                out = fma(A.cn, unk, out);
+            }
+            chk = fma(out, Real(0), chk);
+            A.Uout[e + (int64_t)(comp * K + k) * E] = out;
+        }
+    }
+    if (chk != chk) atomicOr(A.flag, 1u);
+}
+
+template <int P>
+static cudaError_t launch_euler2d_p(const StageArgs& s, int mode, cudaStream_t st)
+{
+    const KParams a = make_params(s);
+    dim3 grid((s.nx + EX - 1) / EX, (s.ny + EY - 1) / EY);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    const size_t smem = sizeof(Euler2Smem<P>);
+    static bool opted[2] = {false, false};
+    if (!opted[mode]) {
+        const void* fn = mode == 0 ? (const void*)euler2d_kernel<P, 0> : (const void*)euler2d_kernel<P, 1>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        opted[mode] = true;
+    }
+    if (mode == 0) euler2d_kernel<P, 0><<<grid, ENT, smem, st>>>(a);
+    else euler2d_kernel<P, 1><<<grid, ENT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_euler2d(const StageArgs& s, int p, int mode, cudaStream_t st)
+{
+    switch (p) {
+    case 1: return launch_euler2d_p<1>(s, mode, st);
+    case 2: return launch_euler2d_p<2>(s, mode, st);
+    case 3: return launch_euler2d_p<3>(s, mode, st);
+    default: return cudaErrorInvalidValue;
+    }
+}

@@ -29,25 +29,6 @@ struct EulerSmem {
     int has[2];               // the halo cell on the left / right exists
 };
 
-// Reciprocal and square root of the Euler kernel.  float: the approximate instructions
-// rcp.approx and sqrt.approx of the PTX ISA (relative error of a few ulp, far inside the
-// float path's tolerance; a negative argument of the square root gives NaN);
-// double: the correctly rounded operations.
-__device__ __forceinline__ float rcp_e(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ double rcp_e(double x) { return 1.0 / x; }
-__device__ __forceinline__ float sqrt_e(float x)
-{
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ double sqrt_e(double x) { return sqrt(x); }
-
 struct EulerState {
     Real v, pr, inv_rho;
 };
@@ -64,14 +45,6 @@ __device__ __forceinline__ EulerState euler_prim(const KParams& A, Real rho, Rea
 __device__ __forceinline__ Real euler_speed(const KParams& A, const EulerState& s)
 {
     return fabs(s.v) + sqrt_e(A.gam * s.pr * s.inv_rho);
-}
-
-// max(a, b) that returns NaN when either is NaN (fmax drops a NaN operand): a state
-// without a real sound speed (rho <= 0 or p < 0) has no wave speed, and the step then
-// returns non-finite values, which the stage's check reports
-__device__ __forceinline__ Real max_nan(Real a, Real b)
-{
-    return fmax(a, b) + ((a - a) + (b - b));
 }
 
 // F(U) = (rho v, rho v^2 + p, (rho E + p) v)

@@ -1224,8 +1224,40 @@ static cudaError_t launch_gather(const GatherArgs& g, int p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// Euler system (Sec. 5.6): shared helpers, then the kernel of this unit's dimension
+// ------------------------------------------------------------------------------------
+// Reciprocal and square root of the Euler kernels.  float: the approximate instructions
+// rcp.approx and sqrt.approx of the PTX ISA (relative error of a few ulp, far inside the
+// float path's tolerance; a negative argument of the square root gives NaN);
+// double: the correctly rounded operations.
+__device__ __forceinline__ float rcp_e(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_e(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_e(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double sqrt_e(double x) { return sqrt(x); }
+
+// max(a, b) that returns NaN when either is NaN (fmax drops a NaN operand): a state
+// without a real sound speed (rho <= 0 or p < 0) has no wave speed, and the step then
+// returns non-finite values, which the stage's check reports
+__device__ __forceinline__ Real max_nan(Real a, Real b)
+{
+    return fmax(a, b) + ((a - a) + (b - b));
+}
+
 #if DGW_DIM == 1
 #include "dgw_euler_impl.cuh"
+#else
+#include "dgw_euler2d_impl.cuh"
 #endif
 
 template <int P, int FLUX>
@@ -1273,7 +1305,7 @@ static cudaError_t launch(const StageArgs& a, int p, int flux, int mode, cudaStr
 #if DGW_DIM == 1
     if (flux == FLUX_EULER) return launch_euler(a, p, mode, s);
 #else
-    if (flux == FLUX_EULER) return cudaErrorInvalidValue;
+    if (flux == FLUX_EULER) return launch_euler2d(a, p, mode, s);
 #endif
     switch (p) {
     case 1: return launch_p<1>(a, flux, mode, s);

@@ -157,7 +157,7 @@ class Problem:
 
     @property
     def ncomp(self) -> int:
-        return 3 if self.flux == "euler" else 1
+        return self.dim + 2 if self.flux == "euler" else 1
 
     @property
     def K(self) -> int:

@@ -46,8 +46,8 @@ def _create(**kw):
     (dict(bc=("periodic", "outflow", "periodic", "periodic")), -1),
     (dict(b=1.5), -1), (dict(q=0.0), -1), (dict(w_nbr=0.3), -1), (dict(eps_w=0.0), -1),
     (dict(lambda_nu=-1.0), -1),
-    # the Euler system: 1D only, reflecting walls only with it, inflow_zero only without
-    (dict(flux="euler"), -4),
+    # the Euler system: reflecting walls only with it, inflow_zero only without it
+    (dict(flux="euler", bc=("periodic", "periodic", "inflow_zero", "outflow")), -1),
     (dict(dim=1, bc=("reflect", "reflect", "periodic", "periodic")), -1),
     (dict(dim=1, flux="euler", bc=("inflow_zero", "outflow", "periodic", "periodic")), -1),
     (dict(dim=1, flux="euler", gas_gamma=1.0), -1),
