@@ -31,6 +31,9 @@ struct Euler2Smem {
     Real sx[2][EY][EX + 1];         // max |v| + c of the minus (0) / plus (1) cell's own values on x-face f
     Real sy[2][EY + 1][EX];         // the same on y-face r
     int has[EHY][EHX];              // the staged cell exists
+    // float: Un of the tile's cells, brought in by cp.async (in double this would halve
+    // the CTAs per SM; double reads Un at the end)
+    Real un[kF32 ? 4 : 1][kF32 ? K : 1][EY][EX];
 };
 
 struct Euler2State {
@@ -170,17 +173,21 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
     const int gx = tx0 + lx, gy = ty0 + ly;
     const bool in = gx < A.nx && gy < A.ny;
     const int64_t e = (int64_t)gy * A.nx + gx;
-    // Un is read only at the end: issue its loads now where registers allow (p <= 2)
-    constexpr bool kPrefetch = K <= 9;
-    Real un[4][kPrefetch ? K : 1];
-    if (kPrefetch && MODE == 0 && A.has_un && in) {
+    // Un is read only by the final combination: each thread starts asynchronous copies
+    // of its cell's Un coefficients into shared memory now (cp.async holds no
+    // registers) and waits for them just before that combination
+    const bool copy_un = kF32 && MODE == 0 && A.has_un && in;
+    if (copy_un) {
 #pragma unroll
         for (int comp = 0; comp < 4; ++comp)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const Real* a = A.Un + e + (int64_t)(comp * K + k) * E;
-                un[comp][k] = A.cg_loads ? __ldcg(a) : *a;
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.un[kF32 ? comp : 0][kF32 ? k : 0][ly][lx]);
+                const Real* src = A.Un + e + (int64_t)(comp * K + k) * E;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" :: "r"(dst), "l"(src), "n"((int)sizeof(Real))
+                             : "memory");
             }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     __syncthreads();
 
@@ -319,12 +326,14 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
                 const bool refl = A.bc[xf ? 0 : 2] == BC_REFLECT;
 #pragma unroll
                 for (int comp = 0; comp < 4; ++comp) um[comp] = up[comp];
-                if (refl) um[1 + axis] = -up[1 + axis];
+                if (refl && axis == 0) um[1] = -up[1];     // constant indices keep um in registers
+                if (refl && axis == 1) um[2] = -up[2];
             } else if (!has_p) {   // ghost for the minus cell (outward normal +e_axis)
                 const bool refl = A.bc[xf ? 1 : 3] == BC_REFLECT;
 #pragma unroll
                 for (int comp = 0; comp < 4; ++comp) up[comp] = um[comp];
-                if (refl) up[1 + axis] = -um[1 + axis];
+                if (refl && axis == 0) up[1] = -um[1];
+                if (refl && axis == 1) up[2] = -um[2];
             }
             const Euler2State sl = euler2_prim(A, um), sr = euler2_prim(A, up);
             Real Fl[4], Fr[4];
@@ -368,6 +377,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
                                    max_nan(S.sy[1][ly][lx], S.sy[0][ly + 1][lx])));
     const Real ngs = A.stab == STAB_DG ? Real(0) : -(gamma * (A.lam_fixed ? A.lambda_nu : lam) * Real(1.0 / P));
     Real chk = Real(0);
+    if (copy_un) asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's own copies
 #pragma unroll
     for (int comp = 0; comp < 4; ++comp) {
 #pragma unroll
@@ -396,8 +406,8 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
             Real out = fma(A.cl, Lk, A.ck * S.u[comp][k][r0][c0]);
             if (A.has_un) {
                 Real unk;
-                if constexpr (kPrefetch) {
-                    unk = un[comp][k];
+                if constexpr (kF32) {
+                    unk = S.un[comp][k][ly][lx];
                 } else {
                     const Real* a = A.Un + e + (int64_t)(comp * K + k) * E;
                     unk = A.cg_loads ? __ldcg(a) : *a;
