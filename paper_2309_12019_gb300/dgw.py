@@ -127,8 +127,8 @@ def _ptr(t):
 
 @dataclasses.dataclass
 class Problem:
-    """Mesh, degree, flux and stabilization of one scalar conservation law, or of the 1D
-    Euler system (flux "euler"), host side."""
+    """Mesh, degree, flux and stabilization of one scalar conservation law, or of the
+    Euler system in 1D or 2D (flux "euler"), host side."""
     dim: int
     nx: int
     p: int

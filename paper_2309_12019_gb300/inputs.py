@@ -1,4 +1,5 @@
-"""Seeded synthetic inputs for the scalar conservation laws of the paper's Sec. 5.
+"""Seeded synthetic inputs for the scalar conservation laws and the Euler problems of the
+paper's Sec. 5.
 
 This module holds no arithmetic of the method itself: it only places sample points,
 evaluates initial data (closed-form functions of x), draws seeded random states and
