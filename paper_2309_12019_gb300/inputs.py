@@ -318,6 +318,7 @@ def random_euler_state(p: int, E: int, seed: int, amp: float = 0.05, gamma: floa
 
 
 # 2D problems of Sec. 5.6 whose data jump along cell faces at the paper's mesh sizes.
+# Outflow boundaries for the rarefaction problems, as the paper states.
 # Kelvin-Helmholtz: the denser, left-moving state fills the strip |y - 0.5| < 0.25 and
 # the boundaries are periodic (the paper gives neither; this is the usual set-up of the
 # cited problem).  Triple point: three states in the subdomains the paper names, walls
@@ -326,6 +327,14 @@ EULER_2D = {
     "kelvin_helmholtz": dict(box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4, t_end=1.0, nx=512, ny=512, p=2,
                              lam=3.0),
     "triple_point": dict(box=(0.0, 7.0, 0.0, 3.0), bc=("reflect",) * 4, t_end=4.0, nx=896, ny=384, p=2, lam=3.0),
+    # the two four-quadrant rarefaction problems, the paper's first and second initial
+    # conditions; quadrants numbered counterclockwise from x > 1/2, y > 1/2
+    "rarefaction_1": dict(box=(0.0, 1.0, 0.0, 1.0), bc=("outflow",) * 4, t_end=0.2, nx=256, ny=256, p=2, lam=3.0,
+                          states=((1.0, 0.6233, 0.6233, 1.5), (0.389, -0.6233, 0.6233, 0.4),
+                                  (1.0, -0.6233, -0.6233, 1.5), (0.389, 0.6233, -0.6233, 0.4))),
+    "rarefaction_2": dict(box=(0.0, 1.0, 0.0, 1.0), bc=("outflow",) * 4, t_end=0.25, nx=256, ny=256, p=2, lam=3.0,
+                          states=((1.0, 0.0312, 0.0312, 0.5), (0.927, -0.0312, 0.0312, 0.45),
+                                  (1.0, -0.0312, -0.0312, 0.5), (0.927, 0.0312, -0.0312, 0.45))),
 }
 
 
@@ -340,6 +349,10 @@ def euler2d_primitive(name: str, x, y):
         vy = 0.01 * np.sin(2.0 * np.pi * (x - 0.5))
         pr = np.full(x.shape, 2.5)
         return np.stack([rho, vx, vy, pr]), inner.astype(np.int64)
+    if name.startswith("rarefaction_"):
+        region = np.where(x > 0.5, np.where(y > 0.5, 0, 3), np.where(y > 0.5, 1, 2))
+        st = np.asarray(EULER_2D[name]["states"])[region]
+        return np.moveaxis(st, -1, 0), region
     if name == "triple_point":
         region = np.where(x <= 1.0, 0, np.where(y <= 1.5, 1, 2))
         rho = np.array([1.0, 0.125, 1.0])[region]

@@ -344,7 +344,8 @@ def rel_to_state(got, ref, p):
     return max(np.linalg.norm(got[c * K:(c + 1) * K] - ref[c * K:(c + 1) * K]) for c in range(4)) / scale
 
 
-@pytest.mark.parametrize("name,nx,ny", [("kelvin_helmholtz", 32, 32), ("triple_point", 56, 24)])
+@pytest.mark.parametrize("name,nx,ny", [("kelvin_helmholtz", 32, 32), ("triple_point", 56, 24),
+                                        ("rarefaction_1", 32, 32), ("rarefaction_2", 32, 32)])
 @pytest.mark.parametrize("prec,stab,bar", [("fp64", "lo", 1e-12), ("fp64", "weno", 1e-9), ("fp32", "weno", 2e-5)])
 def test_2d_problems_steps(oracle_mod, name, nx, ny, prec, stab, bar):
     """The paper's 2D problems on reduced meshes: device projection, then 20 steps.  With
@@ -415,3 +416,38 @@ def test_2d_host_entry_and_negative_pressure():
     with pytest.raises(dgw.DGWError) as e:
         ctx.sync_status()
     assert e.value.status == -6
+
+
+def _golden_ranges():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "euler2d_density_ranges.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, stab, lo, hi = line.split()
+            rows[(name, stab)] = (float(lo), float(hi))
+    return rows
+
+
+@pytest.mark.parametrize("name", ["rarefaction_1", "rarefaction_2"])
+@pytest.mark.parametrize("stab", ["lo", "weno"])
+def test_2d_rarefaction_density_ranges_match_the_paper(name, stab):
+    """The rarefaction interactions at the paper's 256^2 cells, p = 2, FP64, run to the
+    paper's final times on the GPU: the range of the density cell means matches the range
+    the paper prints for its LO and WENO solutions to 0.003 (its values are taken on its
+    own nodes; the unstabilized DG extremes depend on them and are not compared)."""
+    lo, hi = _golden_ranges()[(name, stab)]
+    d = I.EULER_2D[name]
+    s = dict(dim=2, nx=256, ny=256, p=2, box=d["box"], bc=d["bc"], flux="euler", stab=stab)
+    ctx = ctx_for(s)
+    U = torch.empty((ctx.K, ctx.E), dtype=torch.float64, device="cuda")
+    ctx.project(torch.tensor(I.euler2d_samples(name, 256, 256, 8), device="cuda").contiguous(), U, 8)
+    n, dt, last = I.nsteps_to(d["t_end"], I.euler_cfl(2, 2) / 256 / d["lam"])
+    ctx.rk_step(U, dt, n)
+    if last > 0:
+        ctx.rk_step(U, last, 1)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    rho = U[0].cpu().numpy()
+    assert abs(rho.min() - lo) <= 3e-3 and abs(rho.max() - hi) <= 3e-3, (rho.min(), rho.max(), lo, hi)

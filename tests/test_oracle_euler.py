@@ -334,12 +334,12 @@ def test_2d_transpose_symmetry(p, stab):
 
 
 def test_2d_inputs_are_face_aligned_at_the_paper_sizes():
-    """The Kelvin-Helmholtz strip and the triple point's subdomains end on cell faces at
-    the paper's meshes, so no cell starts from a mean there; the samples carry the
-    stated states."""
-    for name in ("kelvin_helmholtz", "triple_point"):
+    """The Kelvin-Helmholtz strip, the triple point's subdomains and the rarefaction
+    quadrants end on cell faces at the paper's meshes, so no cell starts from a mean
+    there; the density samples are constant per cell and carry the stated states."""
+    for name in ("kelvin_helmholtz", "triple_point", "rarefaction_1", "rarefaction_2"):
         d = I.EULER_2D[name]
         f = I.euler2d_samples(name, d["nx"], d["ny"], 4).reshape(4, d["nx"] * d["ny"], 16)
         rho = f[0]
-        assert np.all((rho.max(axis=1) == rho.min(axis=1)) | (name == "kelvin_helmholtz"))
-        assert set(np.unique(rho)) <= {1.0, 2.0, 0.125}
+        assert np.all(rho.max(axis=1) == rho.min(axis=1))
+        assert set(np.unique(rho)) <= {1.0, 2.0, 0.125, 0.389, 0.927}
