@@ -40,7 +40,7 @@ WORKLOADS = {
                              cfl=0.02, speeds=(1.0, 1.0), u0="kpp"),
     "rotation_256x256_q2": dict(dim=2, nx=256, ny=256, p=2, box=(0.0, 1.0, 0.0, 1.0),
                                 bc=("inflow_zero",) * 4, flux="rotation", center=(0.5, 0.5), omega=1.0,
-                                stab="weno", cfl=0.1, speeds=(0.5, 0.5), u0="rotation"),
+                                stab="weno", cfl=0.05, speeds=(0.5, 0.5), u0="rotation"),
     "advect1d_128_p2": dict(dim=1, nx=128, ny=1, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4,
                             flux="advect", a=(1.0, 0.0), stab="weno", cfl=0.1, speeds=(1.0,), u0="mixed1d"),
 }

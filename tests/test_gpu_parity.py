@@ -472,3 +472,52 @@ def test_rk_order_checks():
     with pytest.raises(dgw.DGWError) as ei:
         ctx.adjoint_step(U, U.clone(), torch.empty_like(U), 1e-3)
     assert ei.value.status == -4
+
+
+def _golden_scalar_ranges():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "scalar2d_ranges.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, stab, lo, hi = line.split()
+            rows[(name, stab)] = (float(lo), float(hi))
+    return rows
+
+
+@pytest.mark.parametrize("prob,stab,tol_lo,tol_hi", [("kpp", "lo", 3e-3, 3e-3), ("kpp", "weno", 3e-3, 0.1),
+                                                     ("rotation", "lo", 3e-3, 0.015),
+                                                     ("rotation", "weno", 3e-3, 3e-3)])
+def test_2d_scalar_ranges_match_the_paper(prob, stab, tol_lo, tol_hi):
+    """The KPP problem (lambda_e = 2, t = 1) and one revolution of the solid-body rotation
+    on the paper's 128^2 cells, p = 2, FP64, SSP-RK3 with dt = 0.02 h / lambda (lambda = 2
+    for KPP, 0.5 for the rotation, whose speed reaches 0.71 in the corners): the range of
+    the cell means against the range the paper prints (its values are on its own nodes).
+    KPP LO and rotation WENO match to 0.003; rotation LO reaches 0.681 against 0.690; the
+    paper's KPP WENO maximum 11.066 overshoots the data's 7 pi / 2 = 10.996, which these
+    cell means do not."""
+    import math
+    lo, hi = _golden_scalar_ranges()[(prob, stab)]
+    n = 128
+    if prob == "kpp":
+        s = dict(dim=2, nx=n, ny=n, p=2, box=(-2.0, 2.0, -2.5, 1.5), bc=("outflow",) * 4, flux="kpp",
+                 lambda_nu=2.0, stab=stab)
+        X, Y = I.sample_points(2, n, n, s["box"], 8)
+        f, dt, T = I.u0_kpp(X, Y).reshape(-1), 0.02 * (4.0 / n) / 2.0, 1.0
+    else:
+        s = dict(dim=2, nx=n, ny=n, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("inflow_zero",) * 4, flux="rotation",
+                 center=(0.5, 0.5), omega=1.0, stab=stab)
+        X, Y = I.sample_points(2, n, n, s["box"], 8)
+        f, dt, T = I.u0_rotation(X, Y).reshape(-1), 0.02 * (1.0 / n) / 0.5, 2.0 * math.pi
+    ctx = gpu(s)
+    U = torch.empty((ctx.K, ctx.E), dtype=torch.float64, device="cuda")
+    ctx.project(torch.tensor(f, device="cuda").contiguous(), U, 8)
+    nst, dt, last = I.nsteps_to(T, dt)
+    ctx.rk_step(U, dt, nst)
+    if last > 0:
+        ctx.rk_step(U, last, 1)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    u = U[0].cpu().numpy()
+    assert abs(u.min() - lo) <= tol_lo and abs(u.max() - hi) <= tol_hi, (u.min(), u.max(), lo, hi)
