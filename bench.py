@@ -417,17 +417,18 @@ def run_small(name, prec, steps, warmup, local):
     return out
 
 
-def run_reference(w, steps, warmup, budget_s=12.0):
-    """The FP64 CPU oracle on this host's cores, each step a bounded sample: the
-    residual (per-stage work) of a contiguous block of elements."""
+def run_reference(w, steps, warmup, budget_s=12.0, threads=None):
+    """The FP64 CPU oracle on this host's cores (or `threads` of them), each step a
+    bounded sample: the residual (per-stage work) of a contiguous block of elements."""
     from oracle import oracle as O
     O.build()
-    cores = os.cpu_count() or 1
-    O.set_threads(cores)
+    cores = threads or os.cpu_count() or 1
+    O.set_threads(os.cpu_count() or 1)        # the projection is set-up, not the sample
     P = O.Problem(**spec_of(w))
     U = O.project(P, initial_samples(w))
+    O.set_threads(cores)
     E, K = P.E, P.K
-    block = 4096
+    block = 4096 if cores > 1 else 512
     # calibrate the sample so that all steps fit in the budget
     t0 = time.perf_counter()
     O.residual_at(P, U, np.arange(block))
@@ -556,8 +557,11 @@ def main():
     line.update(extras)
     if not args.no_cpu and world == 1:
         v, cores, n_el = run_reference(w, 3, 1, budget_s=12.0)
+        v1, _, n1 = run_reference(w, 2, 1, budget_s=4.0, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
-                                "sample": f"oracle residual (per-stage work) of {n_el} contiguous cells, 3 repeats"}
+                                "sample": f"oracle residual (per-stage work) of {n_el} contiguous cells, 3 repeats",
+                                "value_1_thread": v1,
+                                "sample_1_thread": f"{n1} contiguous cells, 2 repeats, one thread"}
     print(json.dumps(line))
 
 
