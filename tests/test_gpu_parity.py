@@ -555,3 +555,35 @@ def test_fp32_l1_error_within_one_percent_of_fp64_on_discontinuous_data(oracle_m
         ctx.sync_status()
         err[prec] = oracle_mod.l1_error(oracle_mod.Problem(**s), U.double().cpu().numpy(), f, 8)
     assert abs(err["fp32"] - err["fp64"]) <= 0.01 * err["fp64"], err
+
+
+@pytest.mark.parametrize("stab", ["lo", "weno"])
+def test_2d_burgers_stays_in_its_invariant_set_as_in_the_paper(stab):
+    """The 2D Burgers problem with four constant quadrants (the paper's Sec. 5.4), p = 2,
+    t = 0.5, FP64.  The paper takes inflow values from the exact solution in R^2; here the
+    mesh is widened to (-1, 2)^2 with h = 1/128, so that no boundary influence reaches the
+    unit square by t = 0.5 (speeds are at most |u| sqrt 2 <= 1.42) and the far sides see
+    constant states.  On the unit square the LO and WENO cell means span the paper's
+    [-1.000, 0.800] (the data's invariant set) to 0.003, while DG leaves it."""
+    lo, hi = _golden_scalar_ranges()[("burgers", stab)]
+    n, box = 384, (-1.0, 2.0, -1.0, 2.0)
+    X, Y = I.sample_points(2, n, n, box, 8)
+    f = np.where(X < 0.5, np.where(Y > 0.5, -0.2, 0.5), np.where(Y > 0.5, -1.0, 0.8)).reshape(-1)
+    xc = box[0] + (np.arange(n) + 0.5) * 3.0 / n
+    unit = (((xc > 0) & (xc < 1))[None, :] & ((xc > 0) & (xc < 1))[:, None]).reshape(-1)
+    out = {}
+    for st in (stab, "dg"):
+        s = dict(dim=2, nx=n, ny=n, p=2, box=box, bc=("outflow",) * 4, flux="burgers", a=(1.0, 1.0), stab=st)
+        ctx = gpu(s)
+        U = torch.empty((ctx.K, ctx.E), dtype=torch.float64, device="cuda")
+        ctx.project(torch.tensor(f, device="cuda").contiguous(), U, 8)
+        nst, dt, last = I.nsteps_to(0.5, 0.02 * (3.0 / n))
+        ctx.rk_step(U, dt, nst)
+        if last > 0:
+            ctx.rk_step(U, last, 1)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        out[st] = U[0].cpu().numpy()[unit]
+    u = out[stab]
+    assert abs(u.min() - lo) <= 3e-3 and abs(u.max() - hi) <= 3e-3, (u.min(), u.max())
+    assert out["dg"].min() < -1.0 - 1e-3 or out["dg"].max() > 0.8 + 1e-3
