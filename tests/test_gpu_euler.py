@@ -473,3 +473,19 @@ def test_2d_kelvin_helmholtz_lo_range_matches_the_paper():
     ctx.sync_status()
     rho = U[0].double().cpu().numpy()
     assert abs(rho.min() - lo) <= 3e-3 and abs(rho.max() - hi) <= 3e-3, (rho.min(), rho.max(), lo, hi)
+
+
+@pytest.mark.parametrize("rk", [2, 4])
+def test_2d_rk_orders_fp64(oracle_mod, rk):
+    """The SSP Runge-Kutta schemes of order 2 and 4 on the 2D Euler system against the
+    oracle's (six steps, walls, p = 2)."""
+    s = spec2(2, bc="walls")
+    U = state2(2, 37 * 11, seed=500 + rk)
+    dt = I.euler_cfl(2, 2) / 16.0 / 3.0
+    ref = oracle_mod.rk(oracle_mod.Problem(**s), U, dt, 6, rk)
+    ctx = dgw.Context(dgw.Problem(**s, prec="fp64", rk_order=rk))
+    Ud = dev(U, "fp64")
+    ctx.rk_step(Ud, dt, 6)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert per_comp_rel2(Ud.cpu().numpy(), ref, 2) <= 1e-12
