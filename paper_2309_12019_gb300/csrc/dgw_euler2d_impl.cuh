@@ -7,7 +7,8 @@
 // One CTA of EX x EY = 32 x 4 threads owns a tile of as many cells, one per thread:
 //   0. the tile's coefficients and a one-cell face halo (all four components) are
 //      staged in shared memory by coalesced row loads; halo cells beyond a periodic side
-//      are its images, beyond a wall or an outflow side they are absent
+//      are its images, beyond a wall or an outflow side they are absent; in float the
+//      Un coefficients of the tile start to arrive by cp.async
 //   1. per cell: the sensor of Sec. 4 on the density, the volume term at the (p+2)^2
 //      Gauss points by sum factorisation, lambda_e over those points
 //   2. every face of the tile once: both traces at the p+2 Gauss points, the ghost
