@@ -343,3 +343,34 @@ def test_2d_inputs_are_face_aligned_at_the_paper_sizes():
         rho = f[0]
         assert np.all(rho.max(axis=1) == rho.min(axis=1))
         assert set(np.unique(rho)) <= {1.0, 2.0, 0.125, 0.389, 0.927}
+
+
+def _density_wave_error(nx, p, stab, T=0.5, v=1.0, pr=1.0):
+    """L1 density error of a smooth density wave rho = 1 + 0.2 sin(2 pi (x - v t)) at
+    uniform velocity and pressure, an exact solution of the Euler equations (they reduce
+    to advection for it), after SSP-RK of order p + 1 to t = T on a periodic mesh."""
+    P = _problem(nx, p, stab)
+    X, _ = I.sample_points(1, nx, 1, P.box, 8)
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * X.reshape(-1))
+    U = O.project(P, np.stack([rho, rho * v, pr / (G - 1) + 0.5 * rho * v * v]), 8)
+    lam = v + np.sqrt(G * pr / 0.8)
+    n, dt, last = I.nsteps_to(T, I.euler_cfl(p) / nx / lam)
+    U = O.rk(P, U, dt, n, p + 1)
+    if last > 0:
+        U = O.rk(P, U, last, 1, p + 1)
+    exact = 1.0 + 0.2 * np.sin(2 * np.pi * (X.reshape(-1) - v * T))
+    Pd = dataclasses.replace(P, flux="advect", bc=("periodic",) * 4)
+    return O.l1_error(Pd, U[:p + 1], exact, 8)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_density_wave_converges_at_optimal_order(p):
+    """DG on the Euler system converges at the optimal order p + 1 on a smooth exact
+    solution (16 -> 32 -> 64 cells); with the WENO sensor p = 2 stays near it (the paper's
+    claim of optimal convergence for smooth data)."""
+    e = [_density_wave_error(n, p, "dg") for n in (16, 32, 64)]
+    assert abs(np.log2(e[1] / e[2]) - (p + 1)) < 0.15, e
+    assert abs(np.log2(e[0] / e[1]) - (p + 1)) < 0.2, e
+    if p == 2:
+        w = [_density_wave_error(n, p, "weno") for n in (32, 64)]
+        assert np.log2(w[0] / w[1]) > 2.7, w
