@@ -181,10 +181,11 @@ dgw_status dgw_rk_step(dgw_ctx* ctx, void* U, double dt, int nsteps, void* strea
 /* As dgw_rk_step for a state held in HOST memory: copies U_in (host, K*E elements,
  * pinned for asynchronous copies) to the device, runs nsteps steps and copies the
  * result to U_out (host; may equal U_in).  Returns after the stream has finished.
- * On 2D meshes not periodic in y (at least two tile rows high) the first and the last
- * step run as a pipeline over bands of rows, overlapping the input copy, the three
- * stages and the output copy; the context then uses streams of its own, ordered after
- * the work already on `stream` and joined back to it.  nsteps >= 1. */
+ * For the scalar laws on 2D meshes not periodic in y (at least two tile rows high), with
+ * rk_order 3, the first and the last step run as a pipeline over bands of rows,
+ * overlapping the input copy, the three stages and the output copy; the context then
+ * uses streams of its own, ordered after the work already on `stream` and joined back to
+ * it.  Otherwise the whole state is copied in, stepped and copied out.  nsteps >= 1. */
 dgw_status dgw_rk_step_host(dgw_ctx* ctx, const void* U_in, void* U_out, double dt,
                             int nsteps, void* stream);
 
