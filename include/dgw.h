@@ -112,7 +112,11 @@ typedef struct {
                                + m_e) over the same candidates and weights; 0 without
                                neighbours; q and b do not apply; needs w_nbr > 0) */
     double q;               /* sensor exponent, Eq. (sensor); the paper uses 1 */
-    double b;               /* threshold of Eq. (gensensor); 0 recovers Eq. (sensor) */
+    double b;               /* threshold of Eq. (gensensor): gamma = 0 where the ratio
+                               ||U - U*||_e / ||U||_e is below b; 0 recovers Eq. (sensor).
+                               dgw_defaults sets 0.1, the tolerance of the remark in Sec. 4
+                               with which the scalar problems' WENO errors equal DG's on
+                               smooth data (Tables 1-2); the Euler runs of Sec. 5.6 use 0 */
     double w_nbr;           /* linear weight of each neighbour candidate (paper: 1e-2);
                                the cell's own candidate gets 1 - m_e * w_nbr */
     double eps_w;           /* nonlinear weights w_l ~ lin_l / (eps_w + beta_l)^2 (1e-6) */
@@ -129,7 +133,7 @@ typedef struct {
 typedef struct dgw_ctx dgw_ctx;
 
 /* Fills *m, *f, *s with the defaults above (periodic unit interval, advection with
- * a = (1, 0), WENO with q = 1, b = 0, w_nbr = 1e-2, eps_w = 1e-6, eps_s = 1e-12, FP64).
+ * a = (1, 0), WENO with q = 1, b = 0.1, w_nbr = 1e-2, eps_w = 1e-6, eps_s = 1e-12, FP64).
  * Any argument may be NULL. */
 void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s);
 
@@ -194,9 +198,19 @@ dgw_status dgw_rk_step_host(dgw_ctx* ctx, const void* U_in, void* U_out, double 
  * the host. */
 dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream);
 
-/* Reads and clears the context's device-side error flag (non-finite stage output).
- * Synchronizes the stream.  DGW_OK or DGW_ENONFINITE. */
+/* Reads and clears the context's device-side error flags.  Synchronizes the stream.
+ * DGW_ETIMEOUT: a stage kernel's bounded wait for its TMA tile copy gave up, so that
+ * tile was skipped and the output is incomplete; DGW_ENONFINITE: a stage produced a
+ * NaN or Inf; else DGW_OK. */
 dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
+
+/* Diagnostic: poll limit of the stage kernels' bounded waits on their TMA copies (2D
+ * meshes whose rows are 16-byte multiples).  0 restores the default (2^22 polls); a
+ * negative value makes every such wait give up at once: the kernel then still waits
+ * (bounded) for its copy to land, sets the flag that dgw_sync_status reports as
+ * DGW_ETIMEOUT and skips the tile.  Exists so that tests can exercise that path without
+ * a hang.  Drops the context's cached graphs. */
+dgw_status dgw_debug(dgw_ctx* ctx, int wait_limit);
 
 /* ------------------------------------------------------------------------------------
  * Discrete adjoint (the paper has no counterpart: it differentiates the discrete scheme
@@ -286,9 +300,11 @@ dgw_status dgw_batch_debug(dgw_batch* b, long long wait_limit, int unreachable);
  * synchronously: make those calls before any stream capture.  Later calls only
  * enqueue kernels on the stream.  All calls share the array, so calls whose work
  * overlaps on the GPU (other streams, other threads) race and corrupt each other:
- * order them on one stream.  Non-finite results are not reported by this entry
- * point (there is no context to hold the flag).  Scalar laws only: the Euler system
- * returns DGW_EUNSUPPORTED. */
+ * order them on one stream.  Device-side conditions are not reported by this entry
+ * point (there is no context to hold the flag): neither non-finite results nor a
+ * bounded TMA wait that gave up, after which a tile is skipped and its output keeps
+ * whatever the array held before.  Scalar laws only: the Euler system returns
+ * DGW_EUNSUPPORTED. */
 dgw_status dgw_rk_step_noalloc(const dgw_mesh* mesh, int p, const dgw_flux* flux,
                                const dgw_params* params, void* U, double dt, int nsteps,
                                void* stream);

@@ -40,7 +40,14 @@
  *      beta_l = ||U_{h,l}^e||_e^2 (the same seminorm).
  *   R4 the seminorm sums over all multi-indices 1 <= |k| <= p, mixed ones included.
  *   R5 guard: numerator <= eps_s gives gamma = 0; otherwise a zero denominator gives
- *      gamma = 1; otherwise gamma = min(1, r)^q, and gamma = 0 if r < b.
+ *      gamma = 1; otherwise gamma = min(1, r)^q, and gamma = 0 if r < b.  The remark of
+ *      Sec. 4 switches the sensor off below a prescribed tolerance; its value is the b of
+ *      Eq. (gensensor).  The scalar problems use b = 0.1, one of the two values Sec. 5.6
+ *      names: it reproduces the WENO columns of Tables 1-2 (equal to DG at p = 2, 3, and
+ *      at p = 1 from 256 cells), which b = 0 does not (the sensor then falls only like
+ *      h^p on smooth data and the error stays several times DG's).  The Euler runs of
+ *      Sec. 5.6 use gamma_e itself (b = 0) and compare b = 0.1, 0.2 as a variant.  The
+ *      caller passes b; this file has no default.
  *   R6 gamma is recomputed from the state each residual evaluation (every RK stage).
  *   R7 lambda_e = max |F'(U_h)|_2 over the element's volume and face Gauss points
  *      (unless a fixed value is given, as the paper does for the KPP problem).

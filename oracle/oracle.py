@@ -30,6 +30,14 @@ _lock = threading.Lock()
 _lib = None
 
 BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3}
+
+# Threshold b of Eq. (gensensor) when none is given (reading R5): the remark of Sec. 4
+# switches the sensor off below a prescribed tolerance, and b = 0.1 (the smaller of the
+# two values Sec. 5.6 names) reproduces the WENO columns of Tables 1-2 (WENO = DG for
+# p = 2, 3; for p = 1 from 256 cells).  The Euler runs of Sec. 5.6 use the unmodified
+# sensor gamma_e (b = 0) and treat b > 0 as the variant to compare.
+B_SCALAR = 0.1
+B_EULER = 0.0
 FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3, "euler": 4}
 STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 
@@ -82,12 +90,16 @@ class Problem:
     lambda_nu: float = 0.0
     stab: str = "weno"
     q: float = 1.0
-    b: float = 0.0
+    b: float = None          # None: B_SCALAR for the scalar laws, B_EULER for the Euler system
     w_nbr: float = 1e-2
     eps_w: float = 1e-6
     eps_s: float = 1e-12
     theta: float = 1.0
     gas_gamma: float = 1.4
+
+    def __post_init__(self):
+        if self.b is None:
+            self.b = B_EULER if self.flux == "euler" else B_SCALAR
 
     @property
     def E(self) -> int:

@@ -67,6 +67,7 @@ struct dgw_ctx {
     double* partial = nullptr;   // mass partial sums
     double* mass_dev = nullptr;
     unsigned* flag = nullptr;
+    int wait_limit = 0;          // bounded TMA waits: 0 the kernels' default limit (dgw_debug)
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<std::pair<const void*, int>, CUtensorMap> tmaps;   // TMA descriptors (2D): (array, box kind)
     void* adj_ws = nullptr;      // adjoint: per-cell partials (own), K*E
@@ -104,7 +105,7 @@ extern "C" void dgw_defaults(dgw_mesh* m, dgw_flux* f, dgw_params* s)
     }
     if (s) {
         std::memset(s, 0, sizeof *s);
-        s->stab = DGW_STAB_WENO; s->q = 1.0; s->b = 0.0; s->w_nbr = 1e-2;
+        s->stab = DGW_STAB_WENO; s->q = 1.0; s->b = 0.1; s->w_nbr = 1e-2;
         s->eps_w = 1e-6; s->eps_s = 1e-12; s->prec = DGW_FP64; s->theta = 1.0; s->rk_order = 3;
     }
 }
@@ -328,6 +329,7 @@ static StageArgs base_args(const dgw_ctx* c)
     a.theta = c->params.theta;
     a.gas_gamma = c->flux.gas_gamma;
     a.flag = c->flag;
+    a.wait_limit = c->wait_limit;
     return a;
 }
 
@@ -1311,7 +1313,17 @@ extern "C" dgw_status dgw_sync_status(dgw_ctx* c, void* stream)
     DGW_CUDA(cudaMemcpyAsync(&v, c->flag, sizeof v, cudaMemcpyDeviceToHost, s));
     DGW_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(unsigned), s));
     DGW_CUDA(cudaStreamSynchronize(s));
+    if (v & 2u) return fail(DGW_ETIMEOUT, "a stage kernel's bounded wait for its TMA copy gave up (its tile was skipped)");
     if (v & 1u) return fail(DGW_ENONFINITE, "a stage produced a non-finite value");
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_debug(dgw_ctx* c, int wait_limit)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    c->wait_limit = wait_limit;
+    drop_graphs(c);          // the cached graphs hold the old launch parameters
     return DGW_OK;
 }
 

@@ -66,11 +66,13 @@ struct StageArgs {
     double q, b, w_nbr, eps_w, eps_s, theta;
     double gas_gamma;      // Euler system: ratio of heat capacities
     double* gamma_out;     // optional per-element gamma (double)
-    unsigned* flag;        // bit 0: non-finite output; bit 1: a bounded wait gave up
+    unsigned* flag;        // bit 0: non-finite output; bit 1 (value 2): a bounded wait gave up
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x (stage_rows + 2) x K), or null
     const CUtensorMap* tmap_un;  // 2D: TMA descriptor of Un (box kTileX2 x stage_rows x K), or null
     int tile_row0;         // 2D: first tile row of the launch
     int tile_rows;         // 2D: tile rows of the launch (0: through the last row of the mesh)
+    int wait_limit;        // polls of a bounded TMA wait: 0 the default limit, < 0 none (the
+                           // wait gives up at once; diagnostic)
 };
 
 // ------------------------------------------------------------------------------------

@@ -112,6 +112,7 @@ struct alignas(64) KParams {
     int use_tma;
     int use_tma_un;
     int cg_loads;        // load Uk / Un through L2 only (data written earlier in the same launch)
+    int wait_limit;      // polls of a TMA mbarrier wait before it gives up (kWaitLimit)
     int tile_row0;       // first tile row of a stage launch over a band of rows
     const Real* Uk;
     const Real* Un;
@@ -324,10 +325,11 @@ __device__ __forceinline__ int wrap_y(const KParams& A, int gy)
 }
 
 // Bounded wait for the completion of the given phase parity of an mbarrier; false if
-// it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// it gave up after `limit` polls.
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = kWaitLimit)
 {
-    for (int it = 0; it < (1 << 22); ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -415,7 +417,12 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                    "r"(0), "r"(bar)
                 : "memory");
         }
-        if (!mbar_wait(bar, 0)) fail_s = 1;
+        if (!mbar_wait(bar, 0, A.wait_limit)) {
+            // gave up: the tile is skipped and the flag reports it, but the copy still
+            // lands in this CTA's shared memory, so wait for it (bounded) before leaving
+            fail_s = 1;
+            mbar_wait(bar, 0);
+        }
         __syncthreads();
         if (fail_s) {
             if (tid == 0) atomicOr(A.flag, 2u);
@@ -904,8 +911,9 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     }
     V chk = vbc<V>(0);         // becomes NaN if any output is not finite
     const Real* sun = reinterpret_cast<const Real*>(&su[0][0][0]);   // Un tile [K][TYC][TX]
-    if (un_tma && !mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1)) {
+    if (un_tma && !mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1, A.wait_limit)) {
         atomicOr(A.flag, 2u);
+        mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1);   // let the copy land first
         return;
     }
     int64_t e[L];
@@ -976,6 +984,7 @@ static KParams make_params(const StageArgs& s)
     a.use_tma = 0;
     a.use_tma_un = 0;
     a.cg_loads = 0;
+    a.wait_limit = s.wait_limit > 0 ? s.wait_limit : (s.wait_limit == 0 ? kWaitLimit : 0);
     a.tile_row0 = DIM == 2 ? s.tile_row0 : 0;
     if (s.tmap) {
         a.tmap = *s.tmap;
@@ -1023,6 +1032,7 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     A.use_tma = 0;
     A.use_tma_un = 0;
     A.cg_loads = 1;
+    A.wait_limit = kWaitLimit;
     A.tile_row0 = 0;
     const Real* U = static_cast<const Real*>(B.U) + I.off;
     const Real* S1 = static_cast<const Real*>(B.S1) + I.off;

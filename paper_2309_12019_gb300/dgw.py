@@ -22,6 +22,12 @@ FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3, "euler": 4}
 STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 PREC = {"fp64": 0, "fp32": 1}
 
+# Threshold b of Eq. (gensensor) when a Problem gives none: 0.1 for the scalar laws (the
+# tolerance of the remark in Sec. 4, as dgw_defaults sets it), 0 for the Euler system
+# (Sec. 5.6 runs the unmodified sensor and compares b > 0 as a variant).
+B_SCALAR = 0.1
+B_EULER = 0.0
+
 STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ECUDA", -4: "DGW_EUNSUPPORTED",
           -5: "DGW_ETIMEOUT", -6: "DGW_ENONFINITE"}
 
@@ -53,7 +59,7 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
+           "dgw_sync_status", "dgw_debug", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
            "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
            "dgw_last_error", "dgw_version")
@@ -83,6 +89,7 @@ def load(build: bool = True):
         L.dgw_rk_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
+        L.dgw_debug.argtypes = [vp, ctypes.c_int]
         L.dgw_residual_vjp.argtypes = [vp, vp, vp, vp, vp]
         L.dgw_adjoint_step.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp]
         L.dgw_misfit.argtypes = [vp, vp, vp, dp, vp, vp]
@@ -142,7 +149,7 @@ class Problem:
     lambda_nu: float = 0.0
     stab: str = "weno"
     q: float = 1.0
-    b: float = 0.0
+    b: float = None          # None: B_SCALAR for the scalar laws, B_EULER for the Euler system
     w_nbr: float = 1e-2
     eps_w: float = 1e-6
     eps_s: float = 1e-12
@@ -150,6 +157,10 @@ class Problem:
     theta: float = 1.0
     rk_order: int = 3
     gas_gamma: float = 1.4
+
+    def __post_init__(self):
+        if self.b is None:
+            self.b = B_EULER if self.flux == "euler" else B_SCALAR
 
     @property
     def E(self) -> int:
@@ -258,6 +269,10 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+    def debug(self, wait_limit: int):
+        """Poll limit of the stage kernels' bounded TMA waits (dgw_debug)."""
+        _check(load().dgw_debug(self._h, int(wait_limit)))
 
     def residual_vjp(self, U, lam, out, stream=None):
         """out = J_L(U)^T lam (dgw_residual_vjp)."""

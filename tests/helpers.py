@@ -37,3 +37,29 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cell_err(got, ref):
+    """Largest per-cell error: max over cells e of ||got[:, e] - ref[:, e]||_2, over the
+    root-mean-square cell norm of ref.  A single wrong cell shows at its own size here,
+    where a global relative L2 would divide it by sqrt(E)."""
+    a = np.asarray(got, dtype=np.float64)
+    b = np.asarray(ref, dtype=np.float64)
+    scale = max(float(np.sqrt(np.mean(np.sum(b * b, axis=0)))), 1e-300)
+    return float(np.max(np.linalg.norm(a - b, axis=0)) / scale)
+
+
+# Float error bound of the sensor ratio r = ||U - U*||_e / ||U||_e in the float kernels:
+# the sensor tests hold |gamma_fp32 - gamma_oracle| <= 1e-4 wherever gamma = min(1, r).
+R_FLOAT_ERR = 1e-4
+
+
+def near_threshold(O, s, U, delta=R_FLOAT_ERR):
+    """Cells where the oracle's sensor ratio lies within delta of the threshold b of
+    Eq. (gensensor): there the float kernel may take the other side of r < b (gamma 0
+    against gamma ~ b).  All False unless the problem's sensor is WENO with b > 0."""
+    P = O.Problem(**s)
+    if P.stab != "weno" or not P.b > 0:
+        return np.zeros(P.E, dtype=bool)
+    _, r, _ = O.sensor(P, U)
+    return np.abs(r - P.b) < delta

@@ -69,5 +69,5 @@ def test_defaults():
     L = dgw.load()
     m, f, s = dgw.Mesh(), dgw.Flux(), dgw.Params()
     L.dgw_defaults(ctypes.byref(m), ctypes.byref(f), ctypes.byref(s))
-    assert (m.dim, s.stab, s.q, s.b, s.w_nbr, s.eps_w) == (1, 2, 1.0, 0.0, 1e-2, 1e-6)
+    assert (m.dim, s.stab, s.q, s.b, s.w_nbr, s.eps_w) == (1, 2, 1.0, 0.1, 1e-2, 1e-6)
     assert f.gas_gamma == 1.4

@@ -13,6 +13,7 @@ operand) breaks at least one of them:
 * an independent brute-force evaluation (tests/bruteforce.py) on 4-cell meshes;
 * the paper's printed L1 errors (Tables 1 and 2, DG and LO columns) and EOCs.
 """
+import functools
 import math
 import os
 
@@ -202,7 +203,7 @@ def test_sensor_worked_example_1d_p1(oracle_mod):
     (Sec. 5).  Slopes (0.9, 1, 1.1) give w = (0.977974, 0.015210, 0.006816) and
     gamma = 2|1 - b*| / 2 = 8.394052e-4; a step cell (0, 0.5, 0) gives gamma = 1 - 4.9e-11."""
     O = oracle_mod
-    P = O.Problem(dim=1, nx=3, p=1, stab="weno")
+    P = O.Problem(dim=1, nx=3, p=1, stab="weno", b=0.0)
     g, r, w = O.sensor(P, np.array([[0.0, 0.0, 0.0], [0.9, 1.0, 1.1]]))
     assert np.allclose(w[1, :3], [0.977974, 0.015210, 0.006816], atol=2e-6)
     assert abs(g[1] - 8.394052e-4) < 1e-9
@@ -280,7 +281,7 @@ def test_sensor_shift_invariance_and_range(oracle_mod, dim, p):
     and gamma in [0, 1] (Sec. 3)."""
     O = oracle_mod
     n = 6
-    P = O.Problem(dim=dim, nx=n, ny=n, p=p)
+    P = O.Problem(dim=dim, nx=n, ny=n, p=p, b=0.0)
     U = I.random_state(dim, p, P.E, seed=21, smooth=True)
     g, r, w = O.sensor(P, U)
     U2 = U.copy()
@@ -295,7 +296,7 @@ def test_sensor_shift_invariance_and_range(oracle_mod, dim, p):
 def test_threshold_b_zero_recovers_sensor(oracle_mod):
     """Eq. (gensensor): b = 0 gives Eq. (sensor); b > 0 zeroes exactly the ratios below b."""
     O = oracle_mod
-    P = O.Problem(dim=2, nx=6, ny=6, p=2)
+    P = O.Problem(dim=2, nx=6, ny=6, p=2, b=0.0)
     U = I.random_state(2, 2, P.E, seed=4, smooth=True)
     g0, r0, _ = O.sensor(P, U)
     Pb = O.Problem(**{**P.__dict__, "b": 0.3})
@@ -408,9 +409,12 @@ def exact_burgers(x, t):
     return u
 
 
-def run_1d(O, test, p, E, stab, lambda_nu=0.0, cfl=0.05):
+@functools.lru_cache(maxsize=None)
+def run_1d(O, test, p, E, stab, lambda_nu=0.0, cfl=0.05, b=None):
+    """L1 error at t_end of one run of Table 1 (advect) or Table 2 (burgers); b = None is
+    the Problem's default threshold.  Cached: several pins share runs."""
     flux, t_end, u0 = ("advect", 1.0, I.u0_cos) if test == "advect" else ("burgers", 0.1, I.u0_sin)
-    P = O.Problem(dim=1, nx=E, p=p, flux=flux, stab=stab, a=(1.0, 0.0), lambda_nu=lambda_nu)
+    P = O.Problem(dim=1, nx=E, p=p, flux=flux, stab=stab, a=(1.0, 0.0), lambda_nu=lambda_nu, b=b)
     X, _ = I.sample_points(1, E, 1, P.box, 8)
     U = O.project(P, u0(X))
     n, dt, last = I.nsteps_to(t_end, I.cfl_dt(cfl if p < 3 else 0.02, [1.0], [1.0 / E]))
@@ -441,15 +445,75 @@ def test_paper_tables_dg_lo(oracle_mod, test, p):
         assert abs(e_dg / dg - 1) < 0.25, (E, e_dg, dg)
 
 
+@pytest.mark.parametrize("test", ["advect", "burgers"])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_paper_tables_weno_column(oracle_mod, test, p):
+    """The WENO columns of Tables 1-2 with the threshold b = 0.1 of Eq. (gensensor)
+    (reading R5, the tolerance of the remark in Sec. 4).  The paper prints WENO = DG to
+    its three digits for p = 2, 3 on every mesh, and for p = 1 from 256 cells on, with
+    WENO above DG on the coarser p = 1 meshes (Table 1: 10x DG at 16 cells, 1.8x at 128;
+    Table 2: 1.8x at 16 cells).  The oracle: WENO within 2 % of DG at p = 2, 3 (16-64
+    cells; p = 3 Table 1 to 32), WENO over 1.2x DG at p = 1 on 16-64 cells and within 2 %
+    of DG at 256 cells; and the WENO values within the DG column's 25 % of the paper's
+    WENO column where the paper prints WENO = DG.  The unthresholded sensor (b = 0) fails
+    this: its WENO error is 1.7-50x DG at p = 2, 3 (checked at 16 cells)."""
+    O = oracle_mod
+    rows = {r[2]: r for r in _load_tables() if r[0] == test and r[1] == p}
+    Es = [16, 32] if (p == 3 and test == "advect") else [16, 32, 64]
+    for E in Es:
+        dg, weno = run_1d(O, test, p, E, "dg"), run_1d(O, test, p, E, "weno")
+        if p == 1:
+            assert weno > 1.2 * dg, (E, weno, dg)
+        else:
+            assert abs(weno / dg - 1) < 0.02, (E, weno, dg)
+            assert abs(weno / rows[E][5] - 1) < 0.25, (E, weno, rows[E][5])
+    if p == 1:
+        dg, weno = run_1d(O, test, 1, 256, "dg"), run_1d(O, test, 1, 256, "weno")
+        assert abs(weno / dg - 1) < 0.02, (weno, dg)
+        assert abs(weno / rows[256][5] - 1) < 0.25, (weno, rows[256][5])
+    else:
+        dg, w0 = run_1d(O, test, p, 16, "dg"), run_1d(O, test, p, 16, "weno", b=0.0)
+        assert w0 > 1.5 * dg, (w0, dg)
+
+
+@pytest.mark.parametrize("test", ["advect", "burgers"])
+def test_sensor_ratio_below_threshold_on_smooth_data(oracle_mod, test):
+    """Why the WENO column equals DG (Tables 1-2): on the L2 projection of the exact
+    solution at t_end (cos for Table 1, the Burgers solution at t = 0.1 for Table 2) the
+    sensor ratio ||U - U*||_e / ||U||_e stays below b = 0.1 in every cell for p = 2 on
+    16-2048 cells and p = 3 on 16-512 (the paper's meshes), and for p = 1 from 256 cells
+    on; on 16-64 cells at p = 1 it exceeds b somewhere (the p = 1 WENO errors there are
+    above DG's, as in the paper).  So gamma^b = 0 and the stabilized residual is the
+    plain DG residual on these states."""
+    O = oracle_mod
+    t_end, f = (1.0, lambda x: I.u0_cos(x - 1.0)) if test == "advect" else \
+        (0.1, lambda x: exact_burgers(x, 0.1))
+    flux = "advect" if test == "advect" else "burgers"
+    for p, Es in ((1, (16, 32, 64, 256, 512, 1024, 2048)), (2, (16, 32, 64, 128, 256, 512, 1024, 2048)),
+                  (3, (16, 32, 64, 128, 256, 512))):
+        for E in Es:
+            P = O.Problem(dim=1, nx=E, p=p, flux=flux, a=(1.0, 0.0))
+            assert P.b == 0.1
+            X, _ = I.sample_points(1, E, 1, P.box, 8)
+            g, r, _ = O.sensor(P, O.project(P, f(X)))
+            if p == 1 and E <= 64:
+                assert np.max(r) > P.b, (p, E)
+            else:
+                assert np.max(r) < P.b and np.all(g == 0.0), (p, E, np.max(r))
+
+
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_eoc_smooth_advection(oracle_mod, p):
-    """Optimal EOC ~ p + 1 for DG; WENO keeps the order (rate at least p + 1/2)."""
+    """Optimal EOC ~ p + 1 (Table 1) for DG and for WENO (rate at least p + 0.8) on the
+    finest meshes these pins run: 128 -> 256 cells at p = 1 (where the paper's WENO
+    column reaches DG), 32 -> 64 -> 128 at p = 2, 16 -> 32 at p = 3."""
     O = oracle_mod
-    Es = [32, 64] if p > 1 else [64, 128]
-    for stab, lo_bound in (("dg", p + 0.85), ("weno", p + 0.5)):
+    Es = {1: [128, 256], 2: [32, 64, 128], 3: [16, 32]}[p]
+    for stab in ("dg", "weno"):
         e = [run_1d(O, "advect", p, E, stab) for E in Es]
-        eoc = math.log(e[0] / e[1]) / math.log(2)
-        assert eoc > lo_bound, (stab, e, eoc)
+        for e1, e2 in zip(e, e[1:]):
+            eoc = math.log(e1 / e2) / math.log(2)
+            assert eoc > p + 0.8, (stab, e, eoc)
 
 
 # ---------------------------------------------------------------------------------------
