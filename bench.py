@@ -105,11 +105,12 @@ def dt_of(w):
     return I.cfl_dt(w["cfl"], w["speeds"], [h] * w["dim"])
 
 
-# DRAM bytes (read + write) per stage launch of the current stage kernel at the
-# 1024^2 Q3 KPP workload, averaged over the three stages of one step, from one ncu
-# capture (profiles/stage_kernel_kpp_1024x1024_q3.md).  Reset to None whenever the
-# stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = 138.5e6
+# DRAM bytes (read + write) per stage launch of the stage kernel at the 1024^2 Q3 KPP
+# workload, averaged over the three stages of one step, as one ncu capture of the
+# kernel in its current form measured them (dram__bytes_read.sum + dram__bytes_write.sum).
+# None until the current kernel has been captured: the figure of an earlier kernel is
+# not reported.
+STAGE_TRAFFIC_BYTES = None
 
 # FP32 peak of one GB300 from its unit counts and maximum clock: 152 SMs x 128 FP32
 # lanes x 2 flops per FMA x 2.07 GHz.
