@@ -359,8 +359,10 @@ def run_adjoint(local, n=512, steps=200, every=20):
 
     from paper_2309_12019_gb300 import adjoint, dgw
     dev = torch.device("cuda", local)
+    # the unthresholded sensor (b = 0): the threshold of Eq. (gensensor) makes the scheme
+    # jump where a ratio crosses b, and the gradient is that of one smooth piece
     s = dict(dim=2, nx=n, ny=n, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4, flux="burgers",
-             a=(1.0, 1.0), stab="weno")
+             a=(1.0, 1.0), stab="weno", b=0.0)
     pc, pt = I.adjoint_field(I.SEED + 5001), I.adjoint_field(I.SEED + 5002)
     dt = I.cfl_dt(0.1, [float(np.sum(pc["amp"])) + 1.0] * 2, [1.0 / n] * 2)
     c = dgw.Context(dgw.Problem(**s, prec="fp32"))

@@ -219,11 +219,102 @@ __device__ __forceinline__ float2 vmax(float2 a, float2 b) { return make_float2(
 template <class V> struct Lanes { static constexpr int n = 1; };
 template <> struct Lanes<float2> { static constexpr int n = 2; };
 
+// sin and cos of every lane: float pairs reduce their arguments on the packed pipe
+__device__ __forceinline__ void sincos_v(Real x, Real& s, Real& c) { sincos_r(x, &s, &c); }
+__device__ __forceinline__ void sincos_v(float2 x, float2& s, float2& c) { fast_sincos2(x, &s, &c); }
+
 template <int FLUX, class V>
 __device__ __forceinline__ void vol_flux_v(const KParams& A, V u, Real x, V y, V& fx, V& fy, V& spd)
 {
+    if constexpr (FLUX == FLUX_KPP) {
+        sincos_v(u, fx, fy);
 #pragma unroll
-    for (int l = 0; l < Lanes<V>::n; ++l) vol_flux<FLUX>(A, lane(u, l), x, lane(y, l), lane(fx, l), lane(fy, l), lane(spd, l));
+        for (int l = 0; l < Lanes<V>::n; ++l) lane(spd, l) = DIM == 1 ? fabs(lane(fy, l)) : Real(1);
+    } else {
+#pragma unroll
+        for (int l = 0; l < Lanes<V>::n; ++l) vol_flux<FLUX>(A, lane(u, l), x, lane(y, l), lane(fx, l), lane(fy, l), lane(spd, l));
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Quadrature on the symmetric Gauss nodes (g_{NQ-1-q} = -g_q, g = 0 at the centre of an
+// odd rule).  P_i has the parity of i and P_i' the opposite one, so only the table rows
+// of the positive nodes are used: u(+-g) = E(g) +- O(g) from the even and odd parts of
+// the expansion, and a weighted sum over the nodes takes f(+g) + f(-g) or f(+g) - f(-g)
+// per pair.  Terms that vanish by parity (P_odd(0), P_even'(0), P_0' = 0) and the
+// factor P_0 = 1 are left out.
+// ------------------------------------------------------------------------------------
+// u[q] = sum_i r[i] P_i(g_q), q = 0 .. NQ-1 (nodes ascending)
+template <int N1, int NQ, class V>
+__device__ __forceinline__ void interp_sym(const Real (&B)[NQ][N1], const V (&r)[N1], V (&u)[NQ])
+{
+#pragma unroll
+    for (int m = 0; m < NQ / 2; ++m) {
+        const int qp = NQ - 1 - m;
+        V e = r[0], o = vmul(B[qp][1], r[1]);
+#pragma unroll
+        for (int i = 2; i < N1; ++i) {
+            if (i & 1) o = vfma(B[qp][i], r[i], o);
+            else e = vfma(B[qp][i], r[i], e);
+        }
+        u[qp] = vadd(e, o);
+        u[m] = vsub(e, o);
+    }
+    if constexpr ((NQ & 1) != 0) {
+        constexpr int qc = NQ / 2;
+        V e = r[0];
+#pragma unroll
+        for (int i = 2; i < N1; i += 2) e = vfma(B[qc][i], r[i], e);
+        u[qc] = e;
+    }
+}
+
+// out[i] = sum_q W[q][i] f[q] for a table W[q][i] = w_q P_i(g_q) (DERIV false) or
+// w_q P_i'(g_q) (DERIV true; out[0] = 0 is then not written: callers skip it)
+template <bool DERIV, int N1, int NQ, class V>
+__device__ __forceinline__ void project_sym(const Real (&W)[NQ][N1], const V (&f)[NQ], V (&out)[N1])
+{
+    constexpr int NP = NQ / 2;
+    V S[NP > 0 ? NP : 1], D[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        S[m] = vadd(f[NQ - 1 - m], f[m]);
+        D[m] = vsub(f[NQ - 1 - m], f[m]);
+    }
+#pragma unroll
+    for (int i = DERIV ? 1 : 0; i < N1; ++i) {
+        const bool even_fn = DERIV ? (i & 1) != 0 : (i & 1) == 0;   // parity of the table row
+        V a;
+        if ((NQ & 1) != 0 && even_fn) a = vmul(W[NQ / 2][i], f[NQ / 2]);
+        else a = vmul(W[NQ - 1][i], even_fn ? S[0] : D[0]);
+#pragma unroll
+        for (int m = ((NQ & 1) != 0 && even_fn) ? 0 : 1; m < NP; ++m)
+            a = vfma(W[NQ - 1 - m][i], even_fn ? S[m] : D[m], a);
+        out[i] = a;
+    }
+}
+
+// Local Lax-Friedrichs flux of the KPP problem (Sec. 5, F = (sin u, cos u)) across a face
+// of normal +e_x, the states given as u' = u + sh: an x-face takes sh = 0
+// (n.F = sin u, |F'.n| = |cos u|), a y-face sh = pi/2 (n.F = cos u = sin(u + pi/2),
+// |F'.n| = |sin u| = |cos(u + pi/2)|), so that one body serves both orientations.  The
+// wave speed is exact: 1 if [min, max] of the two states holds a multiple of pi (a
+// maximiser of |cos|), else the larger end value.
+template <class V>
+__device__ __forceinline__ V llf_kpp(V uL, V uR)
+{
+    V sL, cL, sR, cR;
+    sincos_v(uL, sL, cL);
+    sincos_v(uR, sR, cR);
+    V spd;
+#pragma unroll
+    for (int l = 0; l < Lanes<V>::n; ++l) {
+        const Real a = lane(uL, l), b = lane(uR, l);
+        const Real k = ceil(fmin(a, b) * Real(1.0 / kPi));
+        lane(spd, l) = k * Real(kPi) <= fmax(a, b) ? Real(1) : fmax(fabs(lane(cL, l)), fabs(lane(cR, l)));
+    }
+    // H = (sin uL' + sin uR') / 2 - s+ (uR' - uL') / 2
+    return vfma(vmul(Real(-0.5), spd), vsub(uR, uL), vmul(Real(0.5), vadd(sL, sR)));
 }
 
 // F'(u) along the axis (inflow test of the ghost state).
@@ -590,10 +681,11 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
             for (int k = 1; k < K; ++k) {
                 const int i = k % N1, j = k / N1;
                 const int a = axis == 0 ? i : j;
-                V sacc = vbc<V>(0);
+                // P_m(xi +- 2) has degree m and leading coefficient 1: the m = a term
+                // is cn[k] itself, the others have m > a
+                V sacc = cn[k];
 #pragma unroll
-                for (int m = 0; m < N1; ++m) {
-                    if (m < a) continue;   // P_m(xi +- 2) has degree m
+                for (int m = a + 1; m < N1; ++m) {
                     const int km = axis == 0 ? m + N1 * j : i + N1 * m;
                     sacc = vfma(T.T[side][a][m], cn[km], sacc);
                 }
@@ -674,55 +766,68 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 #pragma unroll
     for (int l = 0; l < L; ++l) lane(yc, l) = DIM == 2 ? A.y0 + (Real(gy[l]) + Real(0.5)) * A.h : Real(0);
     if constexpr (DIM == 1) {
+        V u[NQ], fx[NQ];
+        interp_sym<N1, NQ>(T.B, c, u);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            V u = vbc<V>(0);
-#pragma unroll
-            for (int i = 0; i < N1; ++i) u = vfma(T.B[q][i], c[i], u);
-            V fx, fy, spd;
-            vol_flux_v<FLUX>(A, u, xc + A.hh * T.g[q], vbc<V>(0), fx, fy, spd);
+            V fy, spd;
+            vol_flux_v<FLUX>(A, u[q], xc + A.hh * T.g[q], vbc<V>(0), fx[q], fy, spd);
             lam = vmax(lam, spd);
-#pragma unroll
-            for (int i = 0; i < N1; ++i) acc[i] = vfma(T.WD[q][i], fx, acc[i]);
         }
+        project_sym<true, N1, NQ>(T.WD, fx, acc);
+        acc[0] = vbc<V>(0);
     } else {
-        V tmp[N1][NQ];
-#pragma unroll
-        for (int j = 0; j < N1; ++j)
-#pragma unroll
-            for (int qx = 0; qx < NQ; ++qx) {
-                V sacc = vbc<V>(0);
-#pragma unroll
-                for (int i = 0; i < N1; ++i) sacc = vfma(T.B[qx][i], c[i + N1 * j], sacc);
-                tmp[j][qx] = sacc;
-            }
-#pragma unroll
-        for (int qy = 0; qy < NQ; ++qy) {
+        // one Gauss row qy at a time: the polynomial reduced to the row (rr[i] =
+        // sum_j P_j(g_qy) c_ij), its values at the row's points, the fluxes there, and
+        // their projection acc_ij += W_qy [P_j(g_qy) sum_qx W_qx P_i'(g_qx) Fx
+        //                                 + P_j'(g_qy) sum_qx W_qx P_i(g_qx) Fy]
+        auto row = [&](const int qy, const V (&rr)[N1]) {
             V y;
 #pragma unroll
             for (int l = 0; l < L; ++l) lane(y, l) = lane(yc, l) + A.hh * T.g[qy];
-            V px[N1], py[N1];
-#pragma unroll
-            for (int i = 0; i < N1; ++i) { px[i] = vbc<V>(0); py[i] = vbc<V>(0); }
+            V u[NQ], fx[NQ], fy[NQ];
+            interp_sym<N1, NQ>(T.B, rr, u);
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
-                V u = vbc<V>(0);
-#pragma unroll
-                for (int j = 0; j < N1; ++j) u = vfma(T.B[qy][j], tmp[j][qx], u);
-                V fx, fy, spd;
-                vol_flux_v<FLUX>(A, u, xc + A.hh * T.g[qx], y, fx, fy, spd);
+                V spd;
+                vol_flux_v<FLUX>(A, u[qx], xc + A.hh * T.g[qx], y, fx[qx], fy[qx], spd);
                 lam = vmax(lam, spd);
-#pragma unroll
-                for (int i = 0; i < N1; ++i) {
-                    px[i] = vfma(T.WD[qx][i], fx, px[i]);
-                    py[i] = vfma(T.WB[qx][i], fy, py[i]);
-                }
             }
+            V px[N1], py[N1];
+            project_sym<true, N1, NQ>(T.WD, fx, px);      // px[0] = 0 (P_0' = 0)
+            project_sym<false, N1, NQ>(T.WB, fy, py);
 #pragma unroll
             for (int j = 0; j < N1; ++j)
 #pragma unroll
-                for (int i = 0; i < N1; ++i)
-                    acc[i + N1 * j] = vfma(T.WB[qy][j], px[i], vfma(T.WD[qy][j], py[i], acc[i + N1 * j]));
+                for (int i = 0; i < N1; ++i) {
+                    V t = acc[i + N1 * j];
+                    if (i > 0) t = vfma(T.WB[qy][j], px[i], t);
+                    if (j > 0) t = vfma(T.WD[qy][j], py[i], t);   // P_0' = 0
+                    acc[i + N1 * j] = t;
+                }
+        };
+        // the rows at +-g together: rr = E +- O over the even and odd degrees in y
+#pragma unroll
+        for (int m = 0; m < (NQ + 1) / 2; ++m) {
+            const int qp = NQ - 1 - m;
+            V rp[N1], rm[N1];
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                V e = c[i], o = vbc<V>(0);
+#pragma unroll
+                for (int j = 2; j < N1; j += 2) e = vfma(T.B[qp][j], c[i + N1 * j], e);
+                if (qp != m) {
+                    o = vmul(T.B[qp][1], c[i + N1]);
+#pragma unroll
+                    for (int j = 3; j < N1; j += 2) o = vfma(T.B[qp][j], c[i + N1 * j], o);
+                    rp[i] = vadd(e, o);
+                    rm[i] = vsub(e, o);
+                } else {
+                    rp[i] = e;
+                }
+            }
+            row(qp, rp);
+            if (qp != m) row(m, rm);
         }
     }
     __syncthreads();
@@ -786,50 +891,81 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                     lane(tp[t], l) = trys[DIM == 2 ? fly[l] + 1 : 0][0][t][flx[l]];
                 }
             }
-        V hq[TN];
-#pragma unroll
-        for (int t = 0; t < TN; ++t) hq[t] = vbc<V>(0);
-        V lm = vbc<V>(0), lp = vbc<V>(0);
         constexpr int NFQ = DIM == 1 ? 1 : NQ;
+        // KPP: a y-face is an x-face of the states shifted by pi/2 (llf_kpp).  P_0 = 1, so
+        // the shift added to the first trace coefficient shifts every face value.
+        const Real sh = (FLUX == FLUX_KPP && DIM == 2 && !xf) ? Real(0.5 * kPi) : Real(0);
+        if constexpr (FLUX == FLUX_KPP && DIM == 2) {
+            tm[0] = vadd(tm[0], vbc<V>(sh));
+            tp[0] = vadd(tp[0], vbc<V>(sh));
+        }
+        V uLq[NFQ], uRq[NFQ];
+        if constexpr (DIM == 1) {
+            uLq[0] = tm[0];
+            uRq[0] = tp[0];
+        } else {
+            interp_sym<N1, NQ>(T.B, tm, uLq);
+            interp_sym<N1, NQ>(T.B, tp, uRq);
+        }
+        V Hq[NFQ];
+        V lm = vbc<V>(0), lp = vbc<V>(0);
 #pragma unroll
         for (int q = 0; q < NFQ; ++q) {
-            V uL, uR;
-            if constexpr (DIM == 1) {
-                uL = tm[0];
-                uR = tp[0];
-            } else {
-                uL = vbc<V>(0);
-                uR = vbc<V>(0);
+            if constexpr (FLUX == FLUX_KPP) {
+                V uL = uLq[q], uR = uRq[q];
+                if (!minus_in || !plus_in) {
+                    // ghost state; in the shifted variable F'(u).e_axis = cos u' on both axes
 #pragma unroll
-                for (int t = 0; t < TN; ++t) { uL = vfma(T.B[q][t], tm[t], uL); uR = vfma(T.B[q][t], tp[t], uR); }
-            }
-            V H;
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                Real x = Real(0), y = Real(0);
-                if (FLUX == FLUX_ROTATION || need_lam || !minus_in || !plus_in) {
-                    const int fgx = tx0 + flx[l], fgy = ty0 + fly[l];
-                    if (xf) { x = A.x0 + Real(fgx) * A.h; y = DIM == 2 ? A.y0 + (Real(fgy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
-                    else { x = A.x0 + (Real(fgx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(fgy) * A.h; }
-                }
-                Real ul = lane(uL, l), ur = lane(uR, l);
-                if (!minus_in) {
-                    // ghost for the plus cell, whose outward normal is -e_axis
-                    const int bside = xf ? 0 : 2;
-                    ul = (A.bc[bside] == BC_INFLOW_ZERO && -dflux_axis<FLUX>(A, axis, ur, x, y) < Real(0)) ? Real(0) : ur;
-                } else if (!plus_in) {
-                    const int bside = xf ? 1 : 3;
-                    ur = (A.bc[bside] == BC_INFLOW_ZERO && dflux_axis<FLUX>(A, axis, ul, x, y) < Real(0)) ? Real(0) : ul;
+                    for (int l = 0; l < L; ++l) {
+                        Real ul = lane(uL, l), ur = lane(uR, l), sn, cs;
+                        if (!minus_in) {
+                            sincos_r(ur, &sn, &cs);
+                            ul = (A.bc[xf ? 0 : 2] == BC_INFLOW_ZERO && -cs < Real(0)) ? sh : ur;
+                        } else {
+                            sincos_r(ul, &sn, &cs);
+                            ur = (A.bc[xf ? 1 : 3] == BC_INFLOW_ZERO && cs < Real(0)) ? sh : ul;
+                        }
+                        lane(uL, l) = ul;
+                        lane(uR, l) = ur;
+                    }
                 }
                 if (need_lam) {
-                    lane(lm, l) = fmax(lane(lm, l), speed_norm<FLUX>(A, ul, x, y));
-                    lane(lp, l) = fmax(lane(lp, l), speed_norm<FLUX>(A, ur, x, y));
-                }
-                lane(H, l) = llf<FLUX>(A, axis, ul, ur, x, y);
-            }
 #pragma unroll
-            for (int t = 0; t < TN; ++t) hq[t] = DIM == 1 ? vadd(hq[t], H) : vfma(T.WB[q][t], H, hq[t]);
+                    for (int l = 0; l < L; ++l) {   // |F'| = 1 in 2D; 1D: |cos u| (no shift)
+                        lane(lm, l) = fmax(lane(lm, l), speed_norm<FLUX>(A, lane(uL, l), Real(0), Real(0)));
+                        lane(lp, l) = fmax(lane(lp, l), speed_norm<FLUX>(A, lane(uR, l), Real(0), Real(0)));
+                    }
+                }
+                Hq[q] = llf_kpp(uL, uR);
+            } else {
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    Real x = Real(0), y = Real(0);
+                    if (FLUX == FLUX_ROTATION || need_lam || !minus_in || !plus_in) {
+                        const int fgx = tx0 + flx[l], fgy = ty0 + fly[l];
+                        if (xf) { x = A.x0 + Real(fgx) * A.h; y = DIM == 2 ? A.y0 + (Real(fgy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
+                        else { x = A.x0 + (Real(fgx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(fgy) * A.h; }
+                    }
+                    Real ul = lane(uLq[q], l), ur = lane(uRq[q], l);
+                    if (!minus_in) {
+                        // ghost for the plus cell, whose outward normal is -e_axis
+                        const int bside = xf ? 0 : 2;
+                        ul = (A.bc[bside] == BC_INFLOW_ZERO && -dflux_axis<FLUX>(A, axis, ur, x, y) < Real(0)) ? Real(0) : ur;
+                    } else if (!plus_in) {
+                        const int bside = xf ? 1 : 3;
+                        ur = (A.bc[bside] == BC_INFLOW_ZERO && dflux_axis<FLUX>(A, axis, ul, x, y) < Real(0)) ? Real(0) : ul;
+                    }
+                    if (need_lam) {
+                        lane(lm, l) = fmax(lane(lm, l), speed_norm<FLUX>(A, ul, x, y));
+                        lane(lp, l) = fmax(lane(lp, l), speed_norm<FLUX>(A, ur, x, y));
+                    }
+                    lane(Hq[q], l) = llf<FLUX>(A, axis, ul, ur, x, y);
+                }
+            }
         }
+        V hq[TN];
+        if constexpr (DIM == 1) hq[0] = Hq[0];
+        else project_sym<false, N1, NQ>(T.WB, Hq, hq);
         // the flux replaces the minus-side trace, which only this face reads
 #pragma unroll
         for (int l = 0; l < L; ++l) {

@@ -52,6 +52,13 @@ void gauss_rule(int n, double* x, double* w)
         x[n - 1 - i] = z;
         w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dP[n] * dP[n]);
     }
+    // exactly symmetric nodes and weights (the kernels use the rows of the positive nodes
+    // for both of a pair): mirror the positive half, centre at 0 for odd n
+    for (int i = 0; i < n / 2; ++i) {
+        x[i] = -x[n - 1 - i];
+        w[i] = w[n - 1 - i];
+    }
+    if (n & 1) x[n / 2] = 0.0;
 }
 
 // Legendre differentiation matrix on coefficients: (D c)_r = sum_n D[r][n] c_n,

@@ -55,6 +55,18 @@ def per_comp_rel(got, ref, p):
     return max(H.rel_l2(got[c * n1:(c + 1) * n1], ref[c * n1:(c + 1) * n1]) for c in range(3))
 
 
+def per_comp_cell(got, ref, p, dim=1):
+    """Largest per-cell error of any component (helpers.cell_err)."""
+    K = (p + 1) ** dim
+    return max(H.cell_err(got[c * K:(c + 1) * K], ref[c * K:(c + 1) * K]) for c in range(dim + 2))
+
+
+# per-cell FP32 bars: one residual on a float-rounded state, and 20 steps of a shock tube
+# (where the float and double runs differ most next to the shocks)
+FP32_CELL_TOL = 1e-4
+FP32_CELL_TOL_STEPS = 1e-3
+
+
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("stab", ["dg", "lo", "weno", "zhao"])
 @pytest.mark.parametrize("bc", sorted(BCS))
@@ -147,7 +159,9 @@ def test_residual_fp32(oracle_mod, p, stab):
     s = spec(p, stab=stab, bc="wall_out")
     U = I.random_euler_state(p, s["nx"], seed=80 + p, amp=0.1).astype(np.float32).astype(np.float64)
     ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
-    assert per_comp_rel(residual(ctx_for(s, "fp32"), U), ref, p) <= 1e-5
+    got = residual(ctx_for(s, "fp32"), U)
+    assert per_comp_rel(got, ref, p) <= 1e-5
+    assert per_comp_cell(got, ref, p) <= FP32_CELL_TOL
 
 
 @pytest.mark.parametrize("name,p", [("sod", 1), ("sod", 3), ("lax", 2), ("sod_modified", 2), ("shu_osher", 3)])
@@ -165,7 +179,9 @@ def test_shock_tube_fp32_steps(oracle_mod, name, p):
     ctx.rk_step(Ud, dt, 20)
     torch.cuda.synchronize()
     ctx.sync_status()
-    assert per_comp_rel(Ud.double().cpu().numpy(), ref, p) <= 2e-5
+    got = Ud.double().cpu().numpy()
+    assert per_comp_rel(got, ref, p) <= 2e-5
+    assert per_comp_cell(got, ref, p) <= FP32_CELL_TOL_STEPS
     assert d["t_end"] > 20 * dt
 
 
@@ -340,7 +356,9 @@ def test_2d_residual_fp32(oracle_mod, p, stab):
     s = spec2(p, stab=stab, bc="mixed")
     U = state2(p, 37 * 11, seed=400 + p).astype(np.float32).astype(np.float64)
     ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
-    assert per_comp_rel2(residual(ctx_for(s, "fp32"), U), ref, p) <= 1e-5
+    got = residual(ctx_for(s, "fp32"), U)
+    assert per_comp_rel2(got, ref, p) <= 1e-5
+    assert per_comp_cell(got, ref, p, dim=2) <= FP32_CELL_TOL
 
 
 def _problem2d(name, nx, ny, p):
