@@ -449,6 +449,62 @@ def run_reference(w, steps, warmup, budget_s=12.0, threads=None):
     return value, cores, n_el
 
 
+def run_reference_configs(budget_s=4.0):
+    """The FP64 oracle's per-stage residual throughput on the other configurations, each a
+    bounded sample of about budget_s seconds on all host cores: the 1D advection profile
+    (128 cells, P2) and the solid-body rotation (256^2, Q2) on their whole meshes, the
+    ensemble on its smallest instances (8 of each dimension), and the 512^2 Q2 Burgers
+    adjoint workload's forward residual on a contiguous block of cells."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    out = {}
+
+    def timed(fn, dofs):
+        fn()                                     # warm-up
+        n, t0 = 0, time.perf_counter()
+        while True:
+            fn()
+            n += 1
+            t = time.perf_counter() - t0
+            if t >= budget_s:
+                return dofs * n / t, n
+
+    for key, name in (("advect1d_128_p2", "advect1d_128_p2"), ("rotation_256x256_q2", "rotation_256x256_q2")):
+        w = WORKLOADS[name]
+        P = O.Problem(**spec_of(w))
+        U = O.project(P, initial_samples(w))
+        v, n = timed(lambda: O.residual(P, U), P.K * P.E)
+        out[key] = {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                    "sample": f"oracle residual of the whole {w['nx']}x{w['ny']} mesh, {n} repeats"}
+    insts = I.ensemble_instances(512)
+    size = lambda i: insts[i]["nx"] * insts[i]["ny"]
+    pick = (sorted([i for i in range(512) if insts[i]["dim"] == 1], key=size)[:8] +
+            sorted([i for i in range(512) if insts[i]["dim"] == 2], key=size)[:8])
+    probs, states = [], []
+    for i in pick:
+        d = insts[i]
+        P = O.Problem(dim=d["dim"], nx=d["nx"], ny=d["ny"], p=d["p"], box=(0.0, 1.0, 0.0, 1.0),
+                      bc=("periodic",) * 4, flux=d["flux"], a=d["a"], stab="weno")
+        X, Y = I.sample_points(d["dim"], d["nx"], d["ny"], P.box, 8)
+        probs.append(P)
+        states.append(O.project(P, I.u0_fourier_steps(d["init"], X, Y)))
+    v, n = timed(lambda: [O.residual(P, U) for P, U in zip(probs, states)], sum(P.K * P.E for P in probs))
+    out["ensemble_512"] = {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                           "sample": f"oracle residuals of the 8 smallest 1D and 8 smallest 2D instances, {n} repeats"}
+    n_ = 512
+    P = O.Problem(dim=2, nx=n_, ny=n_, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4, flux="burgers",
+                  a=(1.0, 1.0), stab="weno", b=0.0)
+    X, Y = I.sample_points(2, n_, n_, P.box, 8)
+    U = O.project(P, I.u0_fourier_steps(I.adjoint_field(I.SEED + 5001), X, Y))
+    idx = np.arange(16384) + (P.E - 16384) // 2
+    v, n = timed(lambda: O.residual_at(P, U, idx), P.K * idx.size)
+    out["adjoint_burgers_512x512_q2"] = {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                                         "sample": f"oracle forward residual of 16384 contiguous cells, {n} repeats"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,6 +622,8 @@ def main():
                                 "sample": f"oracle residual (per-stage work) of {n_el} contiguous cells, 3 repeats",
                                 "value_1_thread": v1,
                                 "sample_1_thread": f"{n1} contiguous cells, 2 repeats, one thread"}
+        if not args.no_extras:
+            line["cpu_baseline"]["other_configs"] = run_reference_configs()
     print(json.dumps(line))
 
 

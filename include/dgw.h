@@ -242,9 +242,11 @@ dgw_status dgw_misfit(dgw_ctx* ctx, const void* U, const void* U_target, double*
 /* ------------------------------------------------------------------------------------
  * Batched ensemble: many independent meshes (their own size, degree, flux, time step)
  * advanced together.  The paper has no counterpart; each instance is the scalar problem
- * above.  One persistent kernel per dimension (cooperative launch) takes work items
- * (stage, instance, chunk of tiles) in order; an item waits, with a bounded spin, only
- * for its own instance's previous stage, so instances of different sizes overlap.
+ * above.  The instances form groups by (dimension, degree); each group's persistent
+ * kernel takes work items (stage, instance, chunk of tiles) in order, and an item waits,
+ * with a bounded spin, only for its own instance's previous stage, so instances of
+ * different sizes overlap.  The groups' kernels run side by side on streams the batch
+ * owns, forked from and joined back into the caller's stream.
  * Fluxes: advection and Burgers (others return DGW_EUNSUPPORTED; reflecting walls
  * DGW_EINVAL).  Stabilization parameters and precision are common.
  * ---------------------------------------------------------------------------------- */
@@ -273,9 +275,20 @@ dgw_status dgw_batch_project(dgw_batch* b, int nq, int first, int count, const d
 /* nsteps SSP-RK3 steps (Eq. ssp) of every instance, in place on the packed state U. */
 dgw_status dgw_batch_rk_step(dgw_batch* b, void* U, int nsteps, void* stream);
 
-/* Times `steps` steps for each work-item size (1, 2, 4, 8, 16 tiles) on a copy of U and
- * keeps the fastest; *chosen_chunk receives it.  Allocates a temporary copy of U. */
+/* For each group alone, times `steps` steps for every tile height built (2D float: tiles
+ * 32 cells wide and 2, 4 or 8 rows high; 2D double: 4 rows; 1D: 128 x 1) and every
+ * work-item size (1, 2, 4, 8, 16 tiles) on a copy of U, and keeps the fastest pair for
+ * that group.  *chosen_chunk (may be NULL) receives the work-item size of the group with
+ * the most cells.  Allocates a temporary copy of U.  The schedule changes no result. */
 dgw_status dgw_batch_autotune(dgw_batch* b, void* U, int steps, int* chosen_chunk, void* stream);
+
+/* Schedule of the group of instances of dimension dim and degree p: the tile height of its
+ * kernel (*rows) and the tiles per work item (*chunk).  Either pointer may be NULL. */
+dgw_status dgw_batch_schedule(const dgw_batch* b, int dim, int p, int* rows, int* chunk);
+
+/* Sets that schedule (a tile height that is built, chunk >= 1; DGW_EINVAL otherwise), e.g.
+ * one an earlier autotune found.  Synchronous.  The schedule changes no result. */
+dgw_status dgw_batch_set_schedule(dgw_batch* b, int dim, int p, int rows, int chunk);
 
 /* Reads and clears the batch's error flag: DGW_ETIMEOUT if a wait gave up,
  * DGW_ENONFINITE for a non-finite result.  Synchronizes the stream. */

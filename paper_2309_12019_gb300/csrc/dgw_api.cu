@@ -774,46 +774,84 @@ struct dgw_batch {
     std::vector<int> dims;
     int64_t total = 0;
     BatchInst* d_inst = nullptr;
-    BatchItem* d_items[2][kMaxP + 1] = {};     // per (dimension, degree)
+    // per group (dimension, degree): its work items, kernel tile height, items' chunk of
+    // tiles, grid, and the stream its persistent kernel runs on
+    BatchItem* d_items[2][kMaxP + 1] = {};
     int nitems[2][kMaxP + 1] = {};
+    int rows[2][kMaxP + 1] = {};
+    int chunk[2][kMaxP + 1] = {};
+    int grid[2][kMaxP + 1] = {};
     void* S1 = nullptr;
     void* S2 = nullptr;
-    unsigned long long* counters = nullptr;   // queue[kQueues], one per (dimension, degree), then done[n]
+    unsigned long long* counters = nullptr;   // queue[kQueues], one per group, then done[n]
     unsigned* flag = nullptr;
     int* abort = nullptr;
-    int grid[2][kMaxP + 1] = {};
-    int chunk = 4;
-    int blocks_per_sm[2][kMaxP + 1] = {};
     int sms = 0;
     long long wait_limit = 1ll << 24;
     int unreachable = 0;
+    cudaStream_t st[2 * (kMaxP + 1)] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[2 * (kMaxP + 1)] = {};
 };
 
 static const int kQueues = 2 * (kMaxP + 1);
 
-static dgw_status batch_build_items(dgw_batch* b)
+static bool batch_group_used(const dgw_batch* b, int d, int p)
 {
-    for (int d = 0; d < 2; ++d)
-        for (int p = 1; p <= kMaxP; ++p) {
-            std::vector<int> order;
-            for (int i = 0; i < b->n; ++i)
-                if (b->dims[i] == d + 1 && b->inst[i].p == p) order.push_back(i);
-            // longest instances first, so the tail of each stage is made of small items
-            std::stable_sort(order.begin(), order.end(),
-                             [&](int x, int y) { return b->inst[x].ntiles > b->inst[y].ntiles; });
-            std::vector<BatchItem> items;
-            for (int i : order)
-                for (int t = 0; t < b->inst[i].ntiles; t += b->chunk)
-                    items.push_back(BatchItem{i, t, std::min(b->chunk, b->inst[i].ntiles - t), 0});
-            cudaFree(b->d_items[d][p]);
-            b->d_items[d][p] = nullptr;
-            b->nitems[d][p] = (int)items.size();
-            if (!items.empty()) {
-                DGW_CUDA(cudaMalloc(&b->d_items[d][p], sizeof(BatchItem) * items.size()));
-                DGW_CUDA(cudaMemcpy(b->d_items[d][p], items.data(), sizeof(BatchItem) * items.size(),
-                                    cudaMemcpyHostToDevice));
-            }
-        }
+    for (int i = 0; i < b->n; ++i)
+        if (b->dims[i] == d + 1 && b->inst[i].p == p) return true;
+    return false;
+}
+
+static bool batch_rows_ok(const dgw_batch* b, int d, int rows)
+{
+    const bool f64 = b->eb == 8;
+    return d == 0 ? (f64 ? batch_rows_built_f64_d1(rows) : batch_rows_built_f32_d1(rows))
+                  : (f64 ? batch_rows_built_f64_d2(rows) : batch_rows_built_f32_d2(rows));
+}
+
+// Tiles of every instance of group (d, p) for the group's tile height, and the group's
+// grid (resident CTAs per SM x SMs).  Uploads the instance table.
+static dgw_status batch_layout(dgw_batch* b, int d, int p)
+{
+    const int rows = b->rows[d][p];
+    for (int i = 0; i < b->n; ++i) {
+        BatchInst& I = b->inst[i];
+        if (b->dims[i] != d + 1 || I.p != p) continue;
+        I.ntx = d == 0 ? (I.nx + 127) / 128 : (I.nx + kTileX2 - 1) / kTileX2;
+        I.ntiles = d == 0 ? I.ntx : I.ntx * ((I.ny + rows - 1) / rows);
+    }
+    const bool f64 = b->eb == 8;
+    const int bps = d == 0 ? (f64 ? batch_blocks_per_sm_f64_d1(p, rows) : batch_blocks_per_sm_f32_d1(p, rows))
+                           : (f64 ? batch_blocks_per_sm_f64_d2(p, rows) : batch_blocks_per_sm_f32_d2(p, rows));
+    if (bps <= 0) return fail(DGW_ECUDA, "batch kernel (dim %d, p %d, %d rows): occupancy query failed", d + 1, p, rows);
+    b->grid[d][p] = bps * b->sms;
+    DGW_CUDA(cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->n, cudaMemcpyHostToDevice));
+    return DGW_OK;
+}
+
+// Work items of group (d, p): chunks of the group's chunk size over each instance's
+// tiles, longest instances first, so that the tail of each stage is made of small items.
+static dgw_status batch_build_items(dgw_batch* b, int d, int p)
+{
+    std::vector<int> order;
+    for (int i = 0; i < b->n; ++i)
+        if (b->dims[i] == d + 1 && b->inst[i].p == p) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->inst[x].ntiles > b->inst[y].ntiles; });
+    const int c = b->chunk[d][p];
+    std::vector<BatchItem> items;
+    for (int i : order)
+        for (int t = 0; t < b->inst[i].ntiles; t += c)
+            items.push_back(BatchItem{i, t, std::min(c, b->inst[i].ntiles - t), 0});
+    cudaFree(b->d_items[d][p]);
+    b->d_items[d][p] = nullptr;
+    b->nitems[d][p] = (int)items.size();
+    if (!items.empty()) {
+        DGW_CUDA(cudaMalloc(&b->d_items[d][p], sizeof(BatchItem) * items.size()));
+        DGW_CUDA(cudaMemcpy(b->d_items[d][p], items.data(), sizeof(BatchItem) * items.size(),
+                            cudaMemcpyHostToDevice));
+    }
     return DGW_OK;
 }
 
@@ -829,6 +867,11 @@ extern "C" dgw_status dgw_batch_destroy(dgw_batch* b)
     cudaFree(b->counters);
     cudaFree(b->flag);
     cudaFree(b->abort);
+    for (int g = 0; g < 2 * (kMaxP + 1); ++g) {
+        if (b->st[g]) cudaStreamDestroy(b->st[g]);
+        if (b->join[g]) cudaEventDestroy(b->join[g]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return DGW_OK;
 }
@@ -873,8 +916,6 @@ extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int*
         I.p = p;
         I.flux = f.kind;
         const int K = m.dim == 1 ? p + 1 : (p + 1) * (p + 1);
-        I.ntx = m.dim == 1 ? (m.nx + 127) / 128 : (m.nx + kTileX2 - 1) / kTileX2;
-        I.ntiles = m.dim == 1 ? I.ntx : I.ntx * ((m.ny + kTileY2 - 1) / kTileY2);
         for (int s = 0; s < 4; ++s) I.bc[s] = s < 2 * m.dim ? m.bc[s] : DGW_BC_PERIODIC;
         I.x0 = m.x0; I.y0 = m.y0; I.h = hx;
         I.a0 = f.a[0]; I.a1 = f.a[1]; I.cx = f.center[0]; I.cy = f.center[1];
@@ -917,25 +958,23 @@ extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int*
         dgw_batch_destroy(b);
         return s2;
     }
-    const bool f64 = b->eb == 8;
-    bool bad = false;
-    for (int d = 0; d < 2; ++d)
-        for (int p = 1; p <= kMaxP; ++p) {
-            bool used = false;
-            for (int i = 0; i < n; ++i) used = used || (b->dims[i] == d + 1 && b->inst[i].p == p);
-            if (!used) continue;
-            b->blocks_per_sm[d][p] = d == 0 ? (f64 ? batch_blocks_per_sm_f64_d1(p) : batch_blocks_per_sm_f32_d1(p))
-                                            : (f64 ? batch_blocks_per_sm_f64_d2(p) : batch_blocks_per_sm_f32_d2(p));
-            b->grid[d][p] = b->blocks_per_sm[d][p] * b->sms;
-            bad = bad || b->grid[d][p] <= 0;
-        }
-    if (bad) {
-        dgw_batch_destroy(b);
-        return fail(DGW_ECUDA, "dgw_batch_create: occupancy query failed");
+    for (int g = 0; g < 2 * (kMaxP + 1) && ce == cudaSuccess; ++g) {
+        ce = cudaStreamCreateWithFlags(&b->st[g], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->join[g], cudaEventDisableTiming);
     }
-    st = batch_build_items(b);
-    if (st == DGW_OK && cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice) != cudaSuccess)
-        st = fail(DGW_ECUDA, "dgw_batch_create: upload failed");
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+        dgw_batch_destroy(b);
+        return fail(DGW_ECUDA, "dgw_batch_create: %s", cudaGetErrorString(ce));
+    }
+    for (int d = 0; d < 2 && st == DGW_OK; ++d)
+        for (int p = 1; p <= kMaxP && st == DGW_OK; ++p) {
+            b->rows[d][p] = d == 0 ? 1 : kTileY2;
+            b->chunk[d][p] = 4;
+            if (!batch_group_used(b, d, p)) continue;
+            st = batch_layout(b, d, p);
+            if (st == DGW_OK) st = batch_build_items(b, d, p);
+        }
     if (st != DGW_OK) {
         dgw_batch_destroy(b);
         return st;
@@ -998,39 +1037,65 @@ extern "C" dgw_status dgw_batch_project(dgw_batch* b, int nq, int first, int cou
     return DGW_OK;
 }
 
-// One persistent launch per (dimension, degree) present, in turn on the stream; each
-// advances its instances through all 3 * nsteps stages.
-static dgw_status batch_enqueue(dgw_batch* b, void* U, int nsteps, cudaStream_t s)
+// Launch of group (d, p)'s persistent kernel on stream s: it advances the group's
+// instances through all 3 * nsteps stages.
+static dgw_status batch_launch_group(dgw_batch* b, int d, int p, void* U, int nsteps, cudaStream_t s)
+{
+    BatchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = b->d_inst;
+    a.items = b->d_items[d][p];
+    a.nitems = b->nitems[d][p];
+    a.nstages = 3 * nsteps;
+    a.U = U;
+    a.S1 = b->S1;
+    a.S2 = b->S2;
+    a.queue = b->counters + d * (kMaxP + 1) + p;
+    a.done = b->counters + kQueues;
+    a.flag = b->flag;
+    a.abort = b->abort;
+    a.stab = b->params.stab;
+    a.q = b->params.q; a.b = b->params.b; a.w_nbr = b->params.w_nbr;
+    a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s; a.theta = b->params.theta;
+    a.wait_limit = b->wait_limit;
+    a.unreachable = b->unreachable;
+    const bool f64 = b->eb == 8;
+    const int rows = b->rows[d][p], g = b->grid[d][p];
+    cudaError_t e = d == 0 ? (f64 ? launch_batch_f64_d1(a, p, rows, g, s) : launch_batch_f32_d1(a, p, rows, g, s))
+                           : (f64 ? launch_batch_f64_d2(a, p, rows, g, s) : launch_batch_f32_d2(a, p, rows, g, s));
+    if (e != cudaSuccess) return fail(DGW_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    return DGW_OK;
+}
+
+// The persistent kernels of all groups (or of group `only` = d * (kMaxP + 1) + p) side by
+// side: each on the batch's stream of its group, forked from s after the counters are
+// cleared and joined back into s.  Groups with more DOFs start first; the others fill the
+// SMs as its CTAs drain.
+static dgw_status batch_enqueue(dgw_batch* b, void* U, int nsteps, cudaStream_t s, int only = -1)
 {
     DGW_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (kQueues + b->n), s));
     DGW_CUDA(cudaMemsetAsync(b->abort, 0, sizeof(int), s));
+    std::vector<std::pair<double, int>> groups;
     for (int d = 0; d < 2; ++d)
         for (int p = 1; p <= kMaxP; ++p) {
-            if (b->nitems[d][p] == 0) continue;
-            BatchArgs a;
-            std::memset(&a, 0, sizeof a);
-            a.inst = b->d_inst;
-            a.items = b->d_items[d][p];
-            a.nitems = b->nitems[d][p];
-            a.nstages = 3 * nsteps;
-            a.U = U;
-            a.S1 = b->S1;
-            a.S2 = b->S2;
-            a.queue = b->counters + d * (kMaxP + 1) + p;
-            a.done = b->counters + kQueues;
-            a.flag = b->flag;
-            a.abort = b->abort;
-            a.stab = b->params.stab;
-            a.q = b->params.q; a.b = b->params.b; a.w_nbr = b->params.w_nbr;
-            a.eps_w = b->params.eps_w; a.eps_s = b->params.eps_s; a.theta = b->params.theta;
-            a.wait_limit = b->wait_limit;
-            a.unreachable = b->unreachable;
-            const bool f64 = b->eb == 8;
-            const int g = b->grid[d][p];
-            cudaError_t e = d == 0 ? (f64 ? launch_batch_f64_d1(a, p, g, s) : launch_batch_f32_d1(a, p, g, s))
-                                   : (f64 ? launch_batch_f64_d2(a, p, g, s) : launch_batch_f32_d2(a, p, g, s));
-            if (e != cudaSuccess) return fail(DGW_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+            const int gi = d * (kMaxP + 1) + p;
+            if (b->nitems[d][p] == 0 || (only >= 0 && gi != only)) continue;
+            double dofs = 0.0;
+            for (int i = 0; i < b->n; ++i)
+                if (b->dims[i] == d + 1 && b->inst[i].p == p)
+                    dofs += (double)b->inst[i].E * (d == 0 ? p + 1 : (p + 1) * (p + 1));
+            groups.push_back({-dofs, gi});
         }
+    std::sort(groups.begin(), groups.end());
+    DGW_CUDA(cudaEventRecord(b->fork, s));
+    for (const auto& gr : groups) {
+        const int gi = gr.second, d = gi / (kMaxP + 1), p = gi % (kMaxP + 1);
+        DGW_CUDA(cudaStreamWaitEvent(b->st[gi], b->fork, 0));
+        dgw_status st = batch_launch_group(b, d, p, U, nsteps, b->st[gi]);
+        if (st != DGW_OK) return st;
+        DGW_CUDA(cudaEventRecord(b->join[gi], b->st[gi]));
+        DGW_CUDA(cudaStreamWaitEvent(s, b->join[gi], 0));
+    }
     return DGW_OK;
 }
 
@@ -1047,6 +1112,8 @@ extern "C" dgw_status dgw_batch_rk_step(dgw_batch* b, void* U, int nsteps, void*
     return batch_enqueue(b, U, nsteps, (cudaStream_t)stream);
 }
 
+// For each group alone: time `steps` steps for every built tile height and every chunk of
+// 1, 2, 4, 8, 16 tiles on a copy of U, and keep the fastest pair.
 extern "C" dgw_status dgw_batch_autotune(dgw_batch* b, void* U, int steps, int* chosen_chunk, void* stream)
 {
     if (!b || !U || steps < 1) return fail(DGW_EINVAL, "bad arguments");
@@ -1060,34 +1127,75 @@ extern "C" dgw_status dgw_batch_autotune(dgw_batch* b, void* U, int steps, int* 
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int chunks[] = {1, 2, 4, 8, 16};
-    int best = b->chunk;
-    float best_ms = 1e30f;
+    const int heights[] = {1, 2, 4, 8};
     dgw_status st = DGW_OK;
-    for (int c : chunks) {
-        b->chunk = c;
-        st = batch_build_items(b);
-        if (st != DGW_OK) break;
-        if (cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { st = fail(DGW_ECUDA, "copy"); break; }
-        st = batch_enqueue(b, tmp, 1, s);    // warm-up
-        if (st != DGW_OK) break;
-        cudaEventRecord(e0, s);
-        st = batch_enqueue(b, tmp, steps, s);
-        if (st != DGW_OK) break;
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = c; }
-    }
+    double best_dofs = -1.0;
+    for (int d = 0; d < 2 && st == DGW_OK; ++d)
+        for (int p = 1; p <= kMaxP && st == DGW_OK; ++p) {
+            if (!batch_group_used(b, d, p)) continue;
+            int best_rows = b->rows[d][p], best_chunk = b->chunk[d][p];
+            float best_ms = 1e30f;
+            for (int rows : heights) {
+                if (!batch_rows_ok(b, d, rows)) continue;
+                b->rows[d][p] = rows;
+                st = batch_layout(b, d, p);
+                for (int c : chunks) {
+                    if (st != DGW_OK) break;
+                    b->chunk[d][p] = c;
+                    st = batch_build_items(b, d, p);
+                    if (st != DGW_OK) break;
+                    if (cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                        st = fail(DGW_ECUDA, "copy");
+                        break;
+                    }
+                    const int gi = d * (kMaxP + 1) + p;
+                    st = batch_enqueue(b, tmp, 1, s, gi);    // warm-up
+                    if (st != DGW_OK) break;
+                    cudaEventRecord(e0, s);
+                    st = batch_enqueue(b, tmp, steps, s, gi);
+                    if (st != DGW_OK) break;
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) { best_ms = ms; best_rows = rows; best_chunk = c; }
+                }
+            }
+            if (st != DGW_OK) break;
+            b->rows[d][p] = best_rows;
+            b->chunk[d][p] = best_chunk;
+            st = batch_layout(b, d, p);
+            if (st == DGW_OK) st = batch_build_items(b, d, p);
+            double dofs = 0.0;
+            for (int i = 0; i < b->n; ++i)
+                if (b->dims[i] == d + 1 && b->inst[i].p == p) dofs += (double)b->inst[i].E;
+            if (dofs > best_dofs && chosen_chunk) { best_dofs = dofs; *chosen_chunk = best_chunk; }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
     cudaFree(tmp);
-    if (st != DGW_OK) return st;
-    b->chunk = best;
-    st = batch_build_items(b);
-    if (chosen_chunk) *chosen_chunk = best;
     return st;
+}
+
+extern "C" dgw_status dgw_batch_schedule(const dgw_batch* b, int dim, int p, int* rows, int* chunk)
+{
+    if (!b || (dim != 1 && dim != 2) || p < 1 || p > kMaxP) return fail(DGW_EINVAL, "bad arguments");
+    if (rows) *rows = b->rows[dim - 1][p];
+    if (chunk) *chunk = b->chunk[dim - 1][p];
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_batch_set_schedule(dgw_batch* b, int dim, int p, int rows, int chunk)
+{
+    if (!b || (dim != 1 && dim != 2) || p < 1 || p > kMaxP) return fail(DGW_EINVAL, "bad arguments");
+    if (!batch_rows_ok(b, dim - 1, rows)) return fail(DGW_EINVAL, "tile height %d not built for dim %d", rows, dim);
+    if (chunk < 1) return fail(DGW_EINVAL, "chunk must be >= 1");
+    b->rows[dim - 1][p] = rows;
+    b->chunk[dim - 1][p] = chunk;
+    if (!batch_group_used(b, dim - 1, p)) return DGW_OK;
+    dgw_status st = batch_layout(b, dim - 1, p);
+    return st == DGW_OK ? batch_build_items(b, dim - 1, p) : st;
 }
 
 extern "C" dgw_status dgw_batch_sync_status(dgw_batch* b, void* stream)

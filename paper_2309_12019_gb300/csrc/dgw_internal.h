@@ -13,8 +13,9 @@ constexpr int kMaxN1 = kMaxP + 1;          // modes per direction
 constexpr int kMaxNQ = kMaxP + 2;          // Gauss points per direction (p + 2)
 constexpr int kMaxK = kMaxN1 * kMaxN1;     // modes per element (2D)
 
-// 2D tiles are kTileX2 threads wide.  The batch kernel runs kTileY2 thread rows of one
-// cell each.  The stage kernel runs stage_thread_rows() rows, and in float a thread
+// 2D tiles are kTileX2 threads wide.  The batch kernel runs 2, 4 or 8 (float; double:
+// kTileY2) thread rows of one cell each, the height picked per degree by its autotuner.
+// The stage kernel runs stage_thread_rows() rows, and in float a thread
 // advances two cells stacked in y (their arithmetic paired on the packed FP32 pipe), so a
 // stage tile spans kTileX2 x stage_rows() cells.  Its TMA box spans kTileX2 + 8 columns
 // (the halo column on each side, widened so the box starts on a 16-byte boundary) and
@@ -131,14 +132,20 @@ cudaError_t launch_stage_f32_d2(const StageArgs& a, int p, int flux, int mode, c
 cudaError_t launch_stage_f64_d1(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 cudaError_t launch_stage_f64_d2(const StageArgs& a, int p, int flux, int mode, cudaStream_t s);
 
-cudaError_t launch_batch_f32_d1(const BatchArgs& a, int p, int grid, cudaStream_t s);
-cudaError_t launch_batch_f32_d2(const BatchArgs& a, int p, int grid, cudaStream_t s);
-cudaError_t launch_batch_f64_d1(const BatchArgs& a, int p, int grid, cudaStream_t s);
-cudaError_t launch_batch_f64_d2(const BatchArgs& a, int p, int grid, cudaStream_t s);
-int batch_blocks_per_sm_f32_d1(int p);
-int batch_blocks_per_sm_f32_d2(int p);
-int batch_blocks_per_sm_f64_d1(int p);
-int batch_blocks_per_sm_f64_d2(int p);
+// Batch kernels per (degree p, tile height `rows`): 2D float tiles of 2, 4 or 8 cell rows,
+// 2D double tiles of kTileY2, 1D tiles of one row (batch_rows_built_*).
+cudaError_t launch_batch_f32_d1(const BatchArgs& a, int p, int rows, int grid, cudaStream_t s);
+cudaError_t launch_batch_f32_d2(const BatchArgs& a, int p, int rows, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64_d1(const BatchArgs& a, int p, int rows, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64_d2(const BatchArgs& a, int p, int rows, int grid, cudaStream_t s);
+int batch_blocks_per_sm_f32_d1(int p, int rows);
+int batch_blocks_per_sm_f32_d2(int p, int rows);
+int batch_blocks_per_sm_f64_d1(int p, int rows);
+int batch_blocks_per_sm_f64_d2(int p, int rows);
+bool batch_rows_built_f32_d1(int rows);
+bool batch_rows_built_f32_d2(int rows);
+bool batch_rows_built_f64_d1(int rows);
+bool batch_rows_built_f64_d2(int rows);
 
 cudaError_t launch_vjp_f32_d1(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);
 cudaError_t launch_vjp_f32_d2(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s);

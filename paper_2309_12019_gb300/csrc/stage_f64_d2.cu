@@ -9,11 +9,12 @@ cudaError_t launch_stage_f64_d2(const StageArgs& a, int p, int flux, int mode, c
 {
     return f64_d2::launch(a, p, flux, mode, s);
 }
-cudaError_t launch_batch_f64_d2(const BatchArgs& a, int p, int grid, cudaStream_t s)
+cudaError_t launch_batch_f64_d2(const BatchArgs& a, int p, int rows, int grid, cudaStream_t s)
 {
-    return f64_d2::launch_batch(a, p, grid, s);
+    return f64_d2::launch_batch(a, p, rows, grid, s);
 }
-int batch_blocks_per_sm_f64_d2(int p) { return f64_d2::batch_blocks_per_sm(p); }
+int batch_blocks_per_sm_f64_d2(int p, int rows) { return f64_d2::batch_blocks_per_sm(p, rows); }
+bool batch_rows_built_f64_d2(int rows) { return f64_d2::batch_rows_built(rows); }
 cudaError_t launch_vjp_f64_d2(const StageArgs& a, int p, int flux, const void* lam, void* ws, void* wn, cudaStream_t s)
 {
     return f64_d2::launch_vjp(a, p, flux, lam, ws, wn, s);

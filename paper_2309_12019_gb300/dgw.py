@@ -61,7 +61,7 @@ EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_pa
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
            "dgw_sync_status", "dgw_debug", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
-           "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
+           "dgw_batch_schedule", "dgw_batch_set_schedule", "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
            "dgw_last_error", "dgw_version")
 
 
@@ -101,6 +101,8 @@ def load(build: bool = True):
         L.dgw_batch_project.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         L.dgw_batch_rk_step.argtypes = [vp, vp, ctypes.c_int, vp]
         L.dgw_batch_autotune.argtypes = [vp, vp, ctypes.c_int, ip, vp]
+        L.dgw_batch_schedule.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip, ip]
+        L.dgw_batch_set_schedule.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.dgw_batch_sync_status.argtypes = [vp, vp]
         L.dgw_batch_debug.argtypes = [vp, ctypes.c_longlong, ctypes.c_int]
         L.dgw_rk_step_noalloc.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.POINTER(Flux),
@@ -366,6 +368,15 @@ class Batch:
 
     def sync_status(self, stream=None):
         _check(load().dgw_batch_sync_status(self._h, _stream(stream)))
+
+    def schedule(self, dim: int, p: int):
+        """(tile rows, tiles per work item) of the group (dim, p) (dgw_batch_schedule)."""
+        rows, chunk = ctypes.c_int(), ctypes.c_int()
+        _check(load().dgw_batch_schedule(self._h, int(dim), int(p), ctypes.byref(rows), ctypes.byref(chunk)))
+        return rows.value, chunk.value
+
+    def set_schedule(self, dim: int, p: int, rows: int, chunk: int):
+        _check(load().dgw_batch_set_schedule(self._h, int(dim), int(p), int(rows), int(chunk)))
 
     def debug(self, wait_limit: int, unreachable: bool):
         _check(load().dgw_batch_debug(self._h, int(wait_limit), 1 if unreachable else 0))

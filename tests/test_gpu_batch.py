@@ -97,11 +97,73 @@ def test_batch_autotune_and_repeatability():
     b.rk_step(U1, 5)
     chunk = b.autotune(U0, steps=2)
     assert chunk in (1, 2, 4, 8, 16)
+    for dim, p in ((1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3)):
+        rows, c = b.schedule(dim, p)
+        assert rows in ((1,) if dim == 1 else (2, 4, 8)) and c in (1, 2, 4, 8, 16)
     U2 = U0.clone()        # autotuning worked on a copy: U0 is untouched
     b.rk_step(U2, 5)
     torch.cuda.synchronize()
     b.sync_status()
-    assert torch.equal(U1, U2)     # work-item size changes the schedule, not the arithmetic
+    assert torch.equal(U1, U2)     # the schedule changes, not the arithmetic
+
+
+@pytest.mark.parametrize("rows,chunk", [(2, 1), (8, 16), (4, 3)])
+def test_batch_tile_heights_bitwise(rows, chunk):
+    """Every tile height of the 2D float batch kernels (and odd work-item sizes) gives the
+    same bits as the default schedule; heights that are not built are refused."""
+    specs = _specs(5)
+    b = _batch(specs, "fp32")
+    states = [H.state_for(s, seed=970 + i) for i, s in enumerate(specs)]
+    b.set_dt([0.005 / s["nx"] for s in specs])
+    U0 = _pack(b, states, torch.float32)
+    U1 = U0.clone()
+    b.rk_step(U1, 4)
+    for p in (1, 2, 3):
+        b.set_schedule(2, p, rows, chunk)
+        b.set_schedule(1, p, 1, chunk)
+    U2 = U0.clone()
+    b.rk_step(U2, 4)
+    torch.cuda.synchronize()
+    b.sync_status()
+    assert torch.equal(U1, U2)
+    with pytest.raises(dgw.DGWError):
+        b.set_schedule(2, 2, 3, 4)
+    with pytest.raises(dgw.DGWError):
+        b.set_schedule(1, 2, 4, 4)
+
+
+def test_ensemble_fp32_members_match_oracle(oracle_mod):
+    """FP32 members of the 512-instance ensemble workload (the smooth ones, without unit
+    steps: the 6 smallest 1D and 3 smallest 2D) against the FP64 oracle after 10 steps:
+    relative L2 <= 2e-5 and every cell within 4e-4 of the RMS cell norm."""
+    from paper_2309_12019_gb300 import inputs as I
+    insts = I.ensemble_instances(512)
+    size = lambda i: insts[i]["nx"] * insts[i]["ny"]
+    smooth = [i for i in range(512) if len(insts[i]["init"]["lo"]) == 0]
+    pick = (sorted([i for i in smooth if insts[i]["dim"] == 1], key=size)[:6] +
+            sorted([i for i in smooth if insts[i]["dim"] == 2], key=size)[:3])
+    specs, refs, samples = [], [], []
+    for i in pick:
+        d = insts[i]
+        s = dict(dim=d["dim"], nx=d["nx"], ny=d["ny"], p=d["p"], box=(0.0, 1.0, 0.0, 1.0),
+                 bc=("periodic",) * 4, flux=d["flux"], a=d["a"], stab="weno")
+        X, Y = I.sample_points(d["dim"], d["nx"], d["ny"], s["box"], 8)
+        f = I.u0_fourier_steps(d["init"], X, Y)
+        samples.append(f.reshape(-1))
+        refs.append(oracle_mod.project(oracle_mod.Problem(**s), f))
+        specs.append(s)
+    b = _batch(specs, "fp32")
+    dts = [insts[i]["dt"] for i in pick]
+    b.set_dt(dts)
+    U = torch.zeros(b.total, dtype=torch.float32, device="cuda")
+    b.project(torch.tensor(np.concatenate(samples), device="cuda"), U, nq=8)
+    b.rk_step(U, 10)
+    b.sync_status()
+    for j, s in enumerate(specs):
+        ref = oracle_mod.rk3(oracle_mod.Problem(**s), refs[j], dts[j], 10)
+        got = b.view(U, j).double().cpu().numpy()
+        assert H.rel_l2(got, ref) <= 2e-5, (j, s["dim"], s["p"], s["nx"])
+        assert H.cell_err(got, ref) <= 4e-4, (j, s["dim"], s["p"], s["nx"])
 
 
 def test_batch_bounded_wait_gives_up():

@@ -732,3 +732,38 @@ def test_paper_tables_weno_column_fine_meshes(test):
             assert abs(weno / rows[(test, p, E)] - 1) < 0.25, (p, E, weno, rows[(test, p, E)])
     if test == "advect":
         assert _table_run(test, 3, 256, "weno", 0.0) > 100 * _table_run(test, 3, 256, "dg", 0.0)
+
+
+def test_fp32_sensor_decisions_on_kpp_1024():
+    """The float kernel keeps the sensor ratio and weights in float.  On the 1024^2 Q3 KPP
+    workload after 200 FP32 steps (a state with shocks, smooth regions and the constant far
+    field), the FP32 sensor and the FP64 sensor of the same float state take the same
+    decision (gamma = 0 by the eps_s guard or by r < b, or gamma > 0) in every cell whose
+    FP64 ratio lies outside the float error of b, and agree to 1e-4 where both are
+    positive.  The counts are printed for the record."""
+    import bench
+    w = bench.WORKLOADS["kpp_1024x1024_q3"]
+    spec = bench.spec_of(w)
+    c32 = dgw.Context(dgw.Problem(**spec, prec="fp32"))
+    U = torch.empty((c32.K, c32.E), dtype=torch.float32, device="cuda")
+    c32.project(torch.tensor(bench.initial_samples(w), device="cuda"), U)
+    c32.rk_step(U, bench.dt_of(w), 200)
+    g32 = torch.empty(c32.E, dtype=torch.float64, device="cuda")
+    c32.sensor(U, g32)
+    c64 = dgw.Context(dgw.Problem(**spec, prec="fp64"))
+    g64 = torch.empty_like(g32)
+    c64.sensor(U.double(), g64)
+    c0 = dgw.Context(dgw.Problem(**dict(spec, b=0.0), prec="fp64"))
+    r64 = torch.empty_like(g32)                 # min(1, r) in double: the ratio below 1
+    c0.sensor(U.double(), r64)
+    torch.cuda.synchronize()
+    g32, g64, r64 = g32.cpu().numpy(), g64.cpu().numpy(), r64.cpu().numpy()
+    b = c32.problem.b
+    near = np.abs(r64 - b) < H.R_FLOAT_ERR
+    differ = (g32 > 0) != (g64 > 0)
+    both = (g32 > 0) & (g64 > 0)
+    print(f"cells {g32.size}: active FP64 {int((g64 > 0).sum())}, FP32 {int((g32 > 0).sum())}; "
+          f"decisions differ {int(differ.sum())}, of which near b {int((differ & near).sum())}; "
+          f"max |dgamma| where both active {float(np.max(np.abs(g32 - g64)[both], initial=0.0)):.2e}")
+    assert not np.any(differ & ~near)
+    assert np.max(np.abs(g32 - g64)[both], initial=0.0) <= H.R_FLOAT_ERR
