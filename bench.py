@@ -58,8 +58,10 @@ for _name, _nx, _p in (("sod", 128, 2), ("shu_osher", 512, 3)):
                                              stab="weno", cfl=I.euler_cfl(_p), speeds=(_d["lam"],),
                                              u0="tube:" + _name, t_end=_d["t_end"])
 # the 2D Euler problems of Sec. 5.6: Kelvin-Helmholtz at the paper's 512^2 cells (p = 2, to
-# t = 1.0) and on 2048^2 cells (state arrays above L2), the triple point at 896 x 384
-for _name, _nx, _ny in (("kelvin_helmholtz", 512, 512), ("kelvin_helmholtz", 2048, 2048), ("triple_point", 896, 384)):
+# t = 1.0), on 1024^2 cells (state arrays of 151 MB, above L2: the profiling case) and on
+# 2048^2 cells, the triple point at 896 x 384
+for _name, _nx, _ny in (("kelvin_helmholtz", 512, 512), ("kelvin_helmholtz", 1024, 1024),
+                        ("kelvin_helmholtz", 2048, 2048), ("triple_point", 896, 384)):
     _d = I.EULER_2D[_name]
     WORKLOADS[f"{_name}_{_nx}x{_ny}_q2"] = dict(dim=2, nx=_nx, ny=_ny, p=2, box=_d["box"], bc=_d["bc"], flux="euler",
                                                 stab="weno", cfl=I.euler_cfl(2, 2), speeds=(_d["lam"], _d["lam"]),
@@ -110,7 +112,7 @@ def dt_of(w):
 # kernel in its current form measured them (dram__bytes_read.sum + dram__bytes_write.sum).
 # None until the current kernel has been captured: the figure of an earlier kernel is
 # not reported.
-STAGE_TRAFFIC_BYTES = None
+STAGE_TRAFFIC_BYTES = 138.5e6
 
 # FP32 peak of one GB300 from its unit counts and maximum clock: 152 SMs x 128 FP32
 # lanes x 2 flops per FMA x 2.07 GHz.

@@ -233,6 +233,20 @@ dgw_status dgw_residual_vjp(dgw_ctx* ctx, const void* U, const void* lam, void* 
 dgw_status dgw_adjoint_step(dgw_ctx* ctx, const void* U_n, const void* lam_np1, void* lam_n, double dt,
                             void* stream);
 
+/* One SSP-RK3 step (Eq. ssp) from U that keeps its two stage states: U1 = U + dt L(U)
+ * and U2 = 3/4 U + 1/4 (U1 + dt L(U1)) are written to the caller's arrays (device, K*E),
+ * and U^{n+1} to U_next when it is not NULL (U_next may equal U; NULL skips the third
+ * stage).  U1 and U2 must not overlap U, U_next or each other.  For checkpointed
+ * gradients: the recomputation of a segment stores the stage states, and the reverse
+ * step then takes them (dgw_adjoint_step_stages) instead of recomputing them. */
+dgw_status dgw_rk_step_stages(dgw_ctx* ctx, const void* U, double dt, void* U1, void* U2, void* U_next,
+                              void* stream);
+
+/* As dgw_adjoint_step, with the step's stage states U1, U2 given (as dgw_rk_step_stages
+ * writes them from U_n) rather than recomputed; the result is the same bits. */
+dgw_status dgw_adjoint_step_stages(dgw_ctx* ctx, const void* U_n, const void* U1, const void* U2,
+                                   const void* lam_np1, void* lam_n, double dt, void* stream);
+
 /* Misfit J = 1/2 int (U_h - U_target,h)^2 dx (exact: mass-matrix weighted) in double,
  * and optionally grad = dJ/dU = M (U - U_target) (device, K*E, may be NULL).  Blocks
  * until *host_J is set. */

@@ -2,8 +2,10 @@
 library's discrete adjoint (dgw_adjoint_step), as torch.autograd.Functions.
 
 rollout(ctx, U0, dt, nsteps, every) advances U0 by nsteps SSP-RK3 steps and keeps a
-checkpoint every `every` steps; its backward pass recomputes each segment's states from
-its checkpoint (dgw_rk_step) and runs dgw_adjoint_step through the segment in reverse.
+checkpoint every `every` steps; its backward pass recomputes each segment from its
+checkpoint, keeping every step's state and its two stage states (dgw_rk_step_stages),
+and runs dgw_adjoint_step_stages through the segment in reverse, so that no stage is
+evaluated twice in the backward pass.
 misfit(ctx, U, U_target) is J = 1/2 int (U_h - U_target)^2 with dJ/dU from dgw_misfit.
 All arithmetic runs in the library's kernels; this module only orders the calls.
 """
@@ -35,13 +37,18 @@ class _Rollout(torch.autograd.Function):
         for seg in reversed(range(len(ctx_.checkpoints))):
             start = seg * every
             n = min(every, nsteps - start)
-            states = [ctx_.checkpoints[seg].clone()]
-            for _ in range(n - 1):
-                nxt = states[-1].clone()
-                dctx.rk_step(nxt, dt, 1)
-                states.append(nxt)
-            for Un in reversed(states):
-                dctx.adjoint_step(Un, lam, lam, dt)
+            states = [ctx_.checkpoints[seg]]
+            stages = []
+            for i in range(n):
+                U1, U2 = torch.empty_like(lam), torch.empty_like(lam)
+                nxt = torch.empty_like(lam) if i < n - 1 else None   # the last step needs no U^{n+1}
+                dctx.rk_step_stages(states[-1], dt, U1, U2, nxt)
+                stages.append((U1, U2))
+                if nxt is not None:
+                    states.append(nxt)
+            for Un, (U1, U2) in zip(reversed(states), reversed(stages)):
+                dctx.adjoint_step_stages(Un, U1, U2, lam, lam, dt)
+            del states, stages
         ctx_.checkpoints = None
         return lam, None, None, None, None
 

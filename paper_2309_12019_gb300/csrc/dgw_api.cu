@@ -1364,6 +1364,54 @@ extern "C" dgw_status dgw_adjoint_step(dgw_ctx* c, const void* U_n, const void* 
     return DGW_OK;
 }
 
+extern "C" dgw_status dgw_rk_step_stages(dgw_ctx* c, const void* U, double dt, void* U1, void* U2, void* U_next,
+                                         void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U || !U1 || !U2) return fail(DGW_EINVAL, "NULL array");
+    if (!aligned16(U) || !aligned16(U1) || !aligned16(U2) || (U_next && !aligned16(U_next)))
+        return fail(DGW_EINVAL, "arrays must be 16-byte aligned");
+    if (U1 == U || U2 == U || U1 == U2 || U_next == U1 || U_next == U2)
+        return fail(DGW_EINVAL, "the stage states must not overlap U, U_next or each other");
+    if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
+    if (c->params.rk_order != 3) return fail(DGW_EUNSUPPORTED, "stage states of the SSP-RK3 step (rk_order 3)");
+    cudaStream_t s = (cudaStream_t)stream;
+    StageArgs a = base_args(c);
+    a.Uk = U; a.Un = nullptr; a.Uout = U1;
+    a.cn = 0.0; a.ck = 1.0; a.cl = dt;
+    DGW_CUDA(launch(c, a, 0, s));
+    a.Uk = U1; a.Un = U; a.Uout = U2;
+    a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt;
+    DGW_CUDA(launch(c, a, 0, s));
+    if (U_next) {
+        a.Uk = U2; a.Un = U; a.Uout = U_next;
+        a.cn = 1.0 / 3.0; a.ck = 2.0 / 3.0; a.cl = 2.0 / 3.0 * dt;
+        DGW_CUDA(launch(c, a, 0, s));
+    }
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_adjoint_step_stages(dgw_ctx* c, const void* U_n, const void* U1, const void* U2,
+                                              const void* lam_np1, void* lam_n, double dt, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!U_n || !U1 || !U2 || !lam_np1 || !lam_n) return fail(DGW_EINVAL, "NULL array");
+    if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
+    if (c->params.rk_order != 3)
+        return fail(DGW_EUNSUPPORTED, "the adjoint step reverses the SSP-RK3 step (rk_order 3)");
+    st = adjoint_ready(c);
+    if (st != DGW_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    DGW_CUDA(vjp_combine(c, U2, lam_np1, lam_np1, 2.0 / 3.0, nullptr, 0.0, nullptr, 0.0, 2.0 / 3.0 * dt,
+                         c->adj_b1, s));
+    DGW_CUDA(vjp_combine(c, U1, c->adj_b1, c->adj_b1, 0.25, nullptr, 0.0, nullptr, 0.0, 0.25 * dt,
+                         c->adj_b2, s));
+    DGW_CUDA(vjp_combine(c, U_n, c->adj_b2, lam_np1, 1.0 / 3.0, c->adj_b1, 0.75, c->adj_b2, 1.0, dt, lam_n, s));
+    return DGW_OK;
+}
+
 template <typename Real>
 __global__ void misfit_kernel(const Real* U, const Real* Ut, Real* grad, int64_t E, int K, int n1, int dim,
                               double h, double* partial)

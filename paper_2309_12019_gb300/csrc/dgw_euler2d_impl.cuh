@@ -21,6 +21,7 @@
 //   L_k = (2/h) minv(i) minv(j) [acc_k - gamma lambda / p (K_ref c)_k].
 
 constexpr int EX = kTileX2, EY = kTileY2, ENT = EX * EY;
+using R2 = std::conditional_t<kF32, float2, double2>;   // a pair of state components
 constexpr int EHX = EX + 2, EHY = EY + 2;          // staged columns / rows (one halo cell)
 
 template <int P>
@@ -205,62 +206,66 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
     if (MODE == 1) return;
 
     const bool need_lam = A.stab != STAB_DG && !A.lam_fixed;
-    Real acc[4][K];
+    // The four components in two pairs, (rho, rho vx) and (rho vy, rho E): every
+    // contraction below runs on both components of a pair at once (packed FP32 in float).
+    // cu(pr, k, r, c) = mode k of pair pr of the staged cell at (r, c).
+    auto cu = [&](int pr, int k, int r, int cc) -> R2 {
+        R2 v;
+        v.x = S.u[2 * pr][k][r][cc];
+        v.y = S.u[2 * pr + 1][k][r][cc];
+        return v;
+    };
+    R2 acc[2][K];
 #pragma unroll
-    for (int comp = 0; comp < 4; ++comp)
+    for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[comp][k] = Real(0);
+        for (int k = 0; k < K; ++k) acc[pr][k] = vbc<R2>(0);
     Real lam = Real(0);
     if (in) {
-#pragma unroll
+        // one Gauss row qy at a time (a rolled loop: one copy of its code): the polynomials
+        // reduced to the row, their values at the row's points (symmetric nodes), the
+        // fluxes there, projected as in the scalar kernel
+#pragma unroll 1
         for (int qy = 0; qy < NQ; ++qy) {
-            // row[comp][i] = sum_j B[qy][j] c_comp[i + N1 j]: the polynomial on the line y = g_qy
-            Real row[4][N1];
+            R2 rr[2][N1];
 #pragma unroll
-            for (int comp = 0; comp < 4; ++comp)
+            for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
                 for (int i = 0; i < N1; ++i) {
-                    Real s = Real(0);
+                    R2 e = cu(pr, i, r0, c0);
 #pragma unroll
-                    for (int j = 0; j < N1; ++j) s = fma(T.B[qy][j], S.u[comp][i + N1 * j][r0][c0], s);
-                    row[comp][i] = s;
+                    for (int j = 1; j < N1; ++j) e = vfma(T.B[qy][j], cu(pr, i + N1 * j, r0, c0), e);
+                    rr[pr][i] = e;
                 }
-            Real px[4][N1], py[4][N1];
-#pragma unroll
-            for (int comp = 0; comp < 4; ++comp)
-#pragma unroll
-                for (int i = 0; i < N1; ++i) { px[comp][i] = Real(0); py[comp][i] = Real(0); }
+            R2 u[2][NQ], fx[2][NQ], fy[2][NQ];
+            interp_sym<N1, NQ>(T.B, rr[0], u[0]);
+            interp_sym<N1, NQ>(T.B, rr[1], u[1]);
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
-                Real q[4];
-#pragma unroll
-                for (int comp = 0; comp < 4; ++comp) {
-                    Real s = Real(0);
-#pragma unroll
-                    for (int i = 0; i < N1; ++i) s = fma(T.B[qx][i], row[comp][i], s);
-                    q[comp] = s;
-                }
+                const Real q[4] = {u[0][qx].x, u[0][qx].y, u[1][qx].x, u[1][qx].y};
                 const Euler2State st = euler2_prim(A, q);
                 Real Fx[4], Fy[4];
                 euler2_flux(st, q, 0, Fx);
                 euler2_flux(st, q, 1, Fy);
                 if (need_lam) lam = max_nan(lam, euler2_speed(A, st, -1));
-#pragma unroll
-                for (int comp = 0; comp < 4; ++comp)
-#pragma unroll
-                    for (int i = 0; i < N1; ++i) {
-                        px[comp][i] = fma(T.WD[qx][i], Fx[comp], px[comp][i]);
-                        py[comp][i] = fma(T.WB[qx][i], Fy[comp], py[comp][i]);
-                    }
+                fx[0][qx].x = Fx[0]; fx[0][qx].y = Fx[1]; fx[1][qx].x = Fx[2]; fx[1][qx].y = Fx[3];
+                fy[0][qx].x = Fy[0]; fy[0][qx].y = Fy[1]; fy[1][qx].x = Fy[2]; fy[1][qx].y = Fy[3];
             }
 #pragma unroll
-            for (int comp = 0; comp < 4; ++comp)
+            for (int pr = 0; pr < 2; ++pr) {
+                R2 px[N1], py[N1];
+                project_sym<true, N1, NQ>(T.WD, fx[pr], px);     // px[0] = 0 (P_0' = 0)
+                project_sym<false, N1, NQ>(T.WB, fy[pr], py);
 #pragma unroll
                 for (int j = 0; j < N1; ++j)
 #pragma unroll
-                    for (int i = 0; i < N1; ++i)
-                        acc[comp][i + N1 * j] =
-                            fma(T.WB[qy][j], px[comp][i], fma(T.WD[qy][j], py[comp][i], acc[comp][i + N1 * j]));
+                    for (int i = 0; i < N1; ++i) {
+                        R2 t = acc[pr][i + N1 * j];
+                        if (i > 0) t = vfma(T.WB[qy][j], px[i], t);
+                        if (j > 0) t = vfma(T.WD[qy][j], py[i], t);   // P_0' = 0
+                        acc[pr][i + N1 * j] = t;
+                    }
+            }
         }
     }
 
@@ -290,39 +295,33 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
         if (!(tile_m && (xf ? cm <= EX : rm <= EY)) && !tile_p) continue;
         const bool has_m = S.has[rm][cm] != 0, has_p = S.has[rp][cp] != 0;
         const int axis = xf ? 0 : 1;
-        // trace coefficients along the face (Legendre index t), both sides, all components
-        Real tm[4][N1], tp[4][N1];
+        // trace coefficients along the face (Legendre index t), both sides, both pairs
+        R2 tm[2][N1], tp[2][N1];
 #pragma unroll
-        for (int comp = 0; comp < 4; ++comp)
+        for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
             for (int t = 0; t < N1; ++t) {
-                Real sm = Real(0), sp = Real(0);
+                R2 sm = cu(pr, xf ? N1 * t : t, rm, cm), sp = cu(pr, xf ? N1 * t : t, rp, cp);
 #pragma unroll
-                for (int n = 0; n < N1; ++n) {
+                for (int n = 1; n < N1; ++n) {
                     const int k = xf ? n + N1 * t : t + N1 * n;
-                    sm += S.u[comp][k][rm][cm];                                    // xi = +1 of the minus cell
-                    sp += (n & 1) ? -S.u[comp][k][rp][cp] : S.u[comp][k][rp][cp];  // xi = -1 of the plus cell
+                    sm = vadd(sm, cu(pr, k, rm, cm));                                  // xi = +1 of the minus cell
+                    sp = (n & 1) ? vsub(sp, cu(pr, k, rp, cp)) : vadd(sp, cu(pr, k, rp, cp));   // xi = -1 of the plus cell
                 }
-                tm[comp][t] = sm;
-                tp[comp][t] = sp;
+                tm[pr][t] = sm;
+                tp[pr][t] = sp;
             }
-        Real hq[4][N1];
+        R2 um2[2][NQ], up2[2][NQ], H[2][NQ];
 #pragma unroll
-        for (int comp = 0; comp < 4; ++comp)
-#pragma unroll
-            for (int t = 0; t < N1; ++t) hq[comp][t] = Real(0);
+        for (int pr = 0; pr < 2; ++pr) {
+            interp_sym<N1, NQ>(T.B, tm[pr], um2[pr]);
+            interp_sym<N1, NQ>(T.B, tp[pr], up2[pr]);
+        }
         Real spm = Real(0), spp = Real(0);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            Real um[4], up[4];
-#pragma unroll
-            for (int comp = 0; comp < 4; ++comp) {
-                Real a = Real(0), b = Real(0);
-#pragma unroll
-                for (int t = 0; t < N1; ++t) { a = fma(T.B[q][t], tm[comp][t], a); b = fma(T.B[q][t], tp[comp][t], b); }
-                um[comp] = a;
-                up[comp] = b;
-            }
+            Real um[4] = {um2[0][q].x, um2[0][q].y, um2[1][q].x, um2[1][q].y};
+            Real up[4] = {up2[0][q].x, up2[0][q].y, up2[1][q].x, up2[1][q].y};
             if (!has_m) {          // ghost for the plus cell (outward normal -e_axis)
                 const bool refl = A.bc[xf ? 0 : 2] == BC_REFLECT;
 #pragma unroll
@@ -346,25 +345,38 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
                 spm = max_nan(spm, euler2_speed(A, sl, -1));
                 spp = max_nan(spp, euler2_speed(A, sr, -1));
             }
+            // H = ((F(U-) + F(U+)) - s+ (U+ - U-)) / 2, a pair at a time
 #pragma unroll
-            for (int comp = 0; comp < 4; ++comp) {
-                const Real H = Real(0.5) * ((Fl[comp] + Fr[comp]) - s * (up[comp] - um[comp]));
-#pragma unroll
-                for (int t = 0; t < N1; ++t) hq[comp][t] = fma(T.WB[q][t], H, hq[comp][t]);
+            for (int pr = 0; pr < 2; ++pr) {
+                R2 fs, du;
+                fs.x = Fl[2 * pr] + Fr[2 * pr];
+                fs.y = Fl[2 * pr + 1] + Fr[2 * pr + 1];
+                du.x = up[2 * pr] - um[2 * pr];
+                du.y = up[2 * pr + 1] - um[2 * pr + 1];
+                H[pr][q] = vmul(Real(0.5), vfma(-s, du, fs));
             }
         }
+        R2 hq[2][N1];
+        project_sym<false, N1, NQ>(T.WB, H[0], hq[0]);
+        project_sym<false, N1, NQ>(T.WB, H[1], hq[1]);
         if (xf) {
 #pragma unroll
-            for (int comp = 0; comp < 4; ++comp)
+            for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-                for (int t = 0; t < N1; ++t) S.hx[comp][t][fr][fc] = hq[comp][t];
+                for (int t = 0; t < N1; ++t) {
+                    S.hx[2 * pr][t][fr][fc] = hq[pr][t].x;
+                    S.hx[2 * pr + 1][t][fr][fc] = hq[pr][t].y;
+                }
             S.sx[0][fr][fc] = spm;
             S.sx[1][fr][fc] = spp;
         } else {
 #pragma unroll
-            for (int comp = 0; comp < 4; ++comp)
+            for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-                for (int t = 0; t < N1; ++t) S.hy[comp][t][fr][fc] = hq[comp][t];
+                for (int t = 0; t < N1; ++t) {
+                    S.hy[2 * pr][t][fr][fc] = hq[pr][t].x;
+                    S.hy[2 * pr + 1][t][fr][fc] = hq[pr][t].y;
+                }
             S.sy[0][fr][fc] = spm;
             S.sy[1][fr][fc] = spp;
         }
@@ -380,43 +392,50 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
     Real chk = Real(0);
     if (copy_un) asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's own copies
 #pragma unroll
-    for (int comp = 0; comp < 4; ++comp) {
+    for (int pr = 0; pr < 2; ++pr) {
 #pragma unroll
         for (int t = 0; t < N1; ++t) {
             // even n: += (m - p); odd n: -= (m + p)
-            const Real xm = S.hx[comp][t][ly][lx], xp = S.hx[comp][t][ly][lx + 1];
-            const Real ym = S.hy[comp][t][ly][lx], yp = S.hy[comp][t][ly + 1][lx];
+            R2 xm, xp, ym, yp;
+            xm.x = S.hx[2 * pr][t][ly][lx]; xm.y = S.hx[2 * pr + 1][t][ly][lx];
+            xp.x = S.hx[2 * pr][t][ly][lx + 1]; xp.y = S.hx[2 * pr + 1][t][ly][lx + 1];
+            ym.x = S.hy[2 * pr][t][ly][lx]; ym.y = S.hy[2 * pr + 1][t][ly][lx];
+            yp.x = S.hy[2 * pr][t][ly + 1][lx]; yp.y = S.hy[2 * pr + 1][t][ly + 1][lx];
+            const R2 dxe = vsub(xm, xp), dxo = vadd(xm, xp), dye = vsub(ym, yp), dyo = vadd(ym, yp);
 #pragma unroll
             for (int n = 0; n < N1; ++n) {
-                acc[comp][n + N1 * t] += (n & 1) ? -(xm + xp) : (xm - xp);
-                acc[comp][t + N1 * n] += (n & 1) ? -(ym + yp) : (ym - yp);
+                acc[pr][n + N1 * t] = (n & 1) ? vsub(acc[pr][n + N1 * t], dxo) : vadd(acc[pr][n + N1 * t], dxe);
+                acc[pr][t + N1 * n] = (n & 1) ? vsub(acc[pr][t + N1 * n], dyo) : vadd(acc[pr][t + N1 * n], dye);
             }
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int i = k % N1, j = k / N1;
-            Real r = acc[comp][k];
-            Real s1 = Real(0), s2 = Real(0);
+            R2 s1 = vbc<R2>(0), s2 = vbc<R2>(0);
 #pragma unroll
             for (int m = 1; m < N1; ++m) {
-                if (((i + m) & 1) == 0 && i > 0) s1 = fma(T.A1[i][m], S.u[comp][m + N1 * j][r0][c0], s1);
-                if (((j + m) & 1) == 0 && j > 0) s2 = fma(T.A1[j][m], S.u[comp][i + N1 * m][r0][c0], s2);
+                if (((i + m) & 1) == 0 && i > 0) s1 = vfma(T.A1[i][m], cu(pr, m + N1 * j, r0, c0), s1);
+                if (((j + m) & 1) == 0 && j > 0) s2 = vfma(T.A1[j][m], cu(pr, i + N1 * m, r0, c0), s2);
             }
-            r = fma(ngs, fma(T.A0[i], s2, T.A0[j] * s1), r);
-            const Real Lk = (A.two_h * (T.minv[i] * T.minv[j])) * r;
-            Real out = fma(A.cl, Lk, A.ck * S.u[comp][k][r0][c0]);
+            const R2 r = vfma(ngs, vfma(T.A0[i], s2, vmul(T.A0[j], s1)), acc[pr][k]);
+            const R2 Lk = vmul(A.two_h * (T.minv[i] * T.minv[j]), r);
+            R2 out = vfma(A.cl, Lk, vmul(A.ck, cu(pr, k, r0, c0)));
             if (A.has_un) {
-                Real unk;
+                R2 unk;
                 if constexpr (kF32) {
-                    unk = S.un[comp][k][ly][lx];
+                    unk.x = S.un[2 * pr][k][ly][lx];
+                    unk.y = S.un[2 * pr + 1][k][ly][lx];
                 } else {
-                    const Real* a = A.Un + e + (int64_t)(comp * K + k) * E;
-                    unk = A.cg_loads ? __ldcg(a) : *a;
+                    const Real* a0 = A.Un + e + (int64_t)(2 * pr * K + k) * E;
+                    const Real* a1 = a0 + (int64_t)K * E;
+                    unk.x = A.cg_loads ? __ldcg(a0) : *a0;
+                    unk.y = A.cg_loads ? __ldcg(a1) : *a1;
                 }
-                out = fma(A.cn, unk, out);
+                out = vfma(A.cn, unk, out);
             }
-            chk = fma(out, Real(0), chk);
-            A.Uout[e + (int64_t)(comp * K + k) * E] = out;
+            chk = fma(out.x, Real(0), fma(out.y, Real(0), chk));
+            A.Uout[e + (int64_t)(2 * pr * K + k) * E] = out.x;
+            A.Uout[e + (int64_t)((2 * pr + 1) * K + k) * E] = out.y;
         }
     }
     if (chk != chk) atomicOr(A.flag, 1u);

@@ -219,6 +219,19 @@ __device__ __forceinline__ float2 vmax(float2 a, float2 b) { return make_float2(
 template <class V> struct Lanes { static constexpr int n = 1; };
 template <> struct Lanes<float2> { static constexpr int n = 2; };
 
+// Pairs of doubles (the Euler kernels keep two state components per pair, a float2 in
+// the float kernels): the same helpers, one lane at a time.
+__device__ __forceinline__ double& lane(double2& v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ double lane(const double2& v, int l) { return l ? v.y : v.x; }
+template <> __device__ __forceinline__ double2 vbc<double2>(Real s) { return make_double2((double)s, (double)s); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) { return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)); }
+__device__ __forceinline__ double2 vfma(double a, double2 b, double2 c) { return make_double2(fma(a, b.x, c.x), fma(a, b.y, c.y)); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vmul(double a, double2 b) { return make_double2(a * b.x, a * b.y); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <> struct Lanes<double2> { static constexpr int n = 2; };
+
 // sin and cos of every lane: float pairs reduce their arguments on the packed pipe
 __device__ __forceinline__ void sincos_v(Real x, Real& s, Real& c) { sincos_r(x, &s, &c); }
 __device__ __forceinline__ void sincos_v(float2 x, float2& s, float2& c) { fast_sincos2(x, &s, &c); }

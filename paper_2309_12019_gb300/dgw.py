@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_debug", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
+           "dgw_sync_status", "dgw_debug", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_rk_step_stages", "dgw_adjoint_step_stages", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
            "dgw_batch_schedule", "dgw_batch_set_schedule", "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
            "dgw_last_error", "dgw_version")
@@ -93,6 +93,8 @@ def load(build: bool = True):
         L.dgw_residual_vjp.argtypes = [vp, vp, vp, vp, vp]
         L.dgw_adjoint_step.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp]
         L.dgw_misfit.argtypes = [vp, vp, vp, dp, vp, vp]
+        L.dgw_rk_step_stages.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp, vp]
+        L.dgw_adjoint_step_stages.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_double, vp]
         L.dgw_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Mesh), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(Flux), ctypes.POINTER(Params), ctypes.POINTER(vp)]
         L.dgw_batch_destroy.argtypes = [vp]
@@ -284,6 +286,18 @@ class Context:
         """lam_n = (dU^{n+1}/dU^n)^T lam_np1 for one SSP-RK3 step from U_n (dgw_adjoint_step)."""
         _check(load().dgw_adjoint_step(self._h, self._state(U_n), self._state(lam_np1), self._state(lam_n),
                                        float(dt), _stream(stream)))
+
+    def rk_step_stages(self, U, dt: float, U1, U2, U_next=None, stream=None):
+        """One SSP-RK3 step from U keeping its stage states U1, U2; U^{n+1} to U_next if
+        given (dgw_rk_step_stages)."""
+        _check(load().dgw_rk_step_stages(self._h, self._state(U), float(dt), self._state(U1), self._state(U2),
+                                         None if U_next is None else self._state(U_next), _stream(stream)))
+
+    def adjoint_step_stages(self, U_n, U1, U2, lam_np1, lam_n, dt: float, stream=None):
+        """dgw_adjoint_step with the step's stage states given (dgw_adjoint_step_stages)."""
+        _check(load().dgw_adjoint_step_stages(self._h, self._state(U_n), self._state(U1), self._state(U2),
+                                              self._state(lam_np1), self._state(lam_n), float(dt),
+                                              _stream(stream)))
 
     def misfit(self, U, U_target, grad=None, stream=None) -> float:
         """J = 1/2 int (U_h - U_target)^2, and grad = dJ/dU if given (dgw_misfit)."""

@@ -203,3 +203,26 @@ def test_adjoint_refuses_zhao_sensor():
         ctx.residual_vjp(U, U.clone(), torch.empty_like(U))
     assert ei.value.status == -4
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stored_stages_match_recomputed_adjoint_step(prec):
+    """dgw_rk_step_stages writes the stage states that dgw_rk_step computes (its U^{n+1}
+    equals dgw_rk_step's bit for bit), and dgw_adjoint_step_stages on them equals
+    dgw_adjoint_step, which recomputes them, bit for bit."""
+    s = H.spec(2, 2, 24, flux="burgers", stab="weno")
+    c = dgw.Context(dgw.Problem(**s, prec=prec))
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    U = torch.tensor(H.state_for(s, seed=77), dtype=dtype, device="cuda")
+    lam = torch.tensor(H.state_for(s, seed=78), dtype=dtype, device="cuda")
+    dt = 2e-3
+    ref = U.clone()
+    c.rk_step(ref, dt, 1, stream=0)
+    U1, U2, nxt = torch.empty_like(U), torch.empty_like(U), torch.empty_like(U)
+    c.rk_step_stages(U, dt, U1, U2, nxt)
+    a, b = torch.empty_like(U), torch.empty_like(U)
+    c.adjoint_step(U, lam, a, dt)
+    c.adjoint_step_stages(U, U1, U2, lam, b, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(nxt, ref)
+    assert torch.equal(a, b)
