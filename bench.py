@@ -302,7 +302,7 @@ def run_gpu(w, prec, steps, warmup, world, local, measure_e2e):
     return res
 
 
-def run_ensemble(steps, warmup, local, n=512):
+def run_ensemble(steps, warmup, local, n=512, autotune=True):
     """The batched ensemble: n independent 1D Burgers / 2D advection instances of uneven
     size and degree (inputs.ensemble_instances), one persistent kernel per dimension."""
     import torch
@@ -333,7 +333,7 @@ def run_ensemble(steps, warmup, local, n=512):
     b.set_dt([d["dt"] for d in insts])
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        chunk = b.autotune(U, steps=2)
+        chunk = b.autotune(U, steps=2) if autotune else None
         b.rk_step(U, warmup)
     stream.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -348,6 +348,7 @@ def run_ensemble(steps, warmup, local, n=512):
     out = {"workload": f"ensemble_{n}", "value": 3 * N * steps / t, "unit": "DOF-updates/s", "dofs": N,
            "instances": n, "instances_1d": sum(d["dim"] == 1 for d in insts), "steps": steps,
            "ms_per_step": 1e3 * t / steps, "work_item_tiles": chunk, "dtype": "f32",
+           "schedule": {f"{d}d_p{p}": b.schedule(d, p) for d in (1, 2) for p in (1, 2, 3)},
            "finite": bool(torch.isfinite(U).all().item())}
     b.close()
     return out
@@ -521,6 +522,8 @@ def main():
                     help="skip the ensemble and the smaller configurations")
     ap.add_argument("--only", choices=["ensemble", "adjoint"],
                     help="run one secondary leg alone (--steps steps) and print its line")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="ensemble: keep the default schedule (for profiling a fixed launch sequence)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world, rank, local = dist_setup(args)
@@ -549,7 +552,7 @@ def main():
     if args.only:
         if rank == 0:
             if args.only == "ensemble":
-                leg = run_ensemble(args.steps, args.warmup, local)
+                leg = run_ensemble(args.steps, args.warmup, local, autotune=not args.no_autotune)
             else:
                 leg = run_adjoint(local, steps=args.steps, every=min(20, args.steps))
             print(json.dumps(dict(leg, leg=args.only)))

@@ -269,20 +269,29 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 // box kind 0: tile plus halo (kBoxX2 x (rows + 2) x K); 1: tile (kTileX2 x rows x K),
-// rows = stage_rows() of the context's precision
-static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U, int kind = 0)
+// rows = stage_rows() of the context's precision.  True and the descriptor in *out if TMA
+// applies.  The descriptor is copied out: the cache evicts all its entries when it grows
+// past 64 arrays, so a pointer into it would not outlive the next lookup.
+static bool tensor_map(const dgw_ctx* cc, const void* U, int kind, CUtensorMap* out)
 {
     dgw_ctx* c = const_cast<dgw_ctx*>(cc);
-    if (c->mesh.dim != 2 || !U || c->flux.kind == DGW_FLUX_EULER) return nullptr;   // the Euler kernel stages by plain loads
+    if (c->mesh.dim != 2 || !U || c->flux.kind == DGW_FLUX_EULER) return false;   // the Euler kernel stages by plain loads
     const auto key = std::make_pair(U, kind);
     auto it = c->tmaps.find(key);
-    if (it != c->tmaps.end()) return &it->second;
-    if (c->no_tmap.count(key)) return nullptr;
+    if (it != c->tmaps.end()) {
+        *out = it->second;
+        return true;
+    }
+    if (c->no_tmap.count(key)) return false;
+    if (c->tmaps.size() + c->no_tmap.size() > 64) {
+        c->tmaps.clear();
+        c->no_tmap.clear();
+    }
     const uint64_t eb = (uint64_t)c->eb, nx = (uint64_t)c->mesh.nx, ny = (uint64_t)c->mesh.ny;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || (nx * eb) % 16 || (nx * ny * eb) % 16 || ((uintptr_t)U & 15u)) {
         c->no_tmap[key] = true;
-        return nullptr;
+        return false;
     }
     cuuint64_t dims[3] = {nx, ny, (cuuint64_t)c->K};
     cuuint64_t strides[2] = {nx * eb, nx * ny * eb};
@@ -297,10 +306,11 @@ static const CUtensorMap* tensor_map(const dgw_ctx* cc, const void* U, int kind 
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         c->no_tmap[key] = true;
-        return nullptr;
+        return false;
     }
-    if (c->tmaps.size() > 64) c->tmaps.clear();
-    return &(c->tmaps[key] = m);
+    c->tmaps[key] = m;
+    *out = m;
+    return true;
 }
 
 static StageArgs base_args(const dgw_ctx* c)
@@ -336,8 +346,9 @@ static StageArgs base_args(const dgw_ctx* c)
 static cudaError_t launch(const dgw_ctx* c, const StageArgs& a0, int mode, cudaStream_t s)
 {
     StageArgs a = a0;
-    a.tmap = tensor_map(c, a.Uk, 0);
-    a.tmap_un = (a.cn != 0.0 && a.Un) ? tensor_map(c, a.Un, 1) : nullptr;
+    CUtensorMap m_k, m_n;      // copies: the launch parameters take them by value
+    a.tmap = tensor_map(c, a.Uk, 0, &m_k) ? &m_k : nullptr;
+    a.tmap_un = (a.cn != 0.0 && a.Un && tensor_map(c, a.Un, 1, &m_n)) ? &m_n : nullptr;
     const bool f64 = c->params.prec == DGW_FP64;
     if (c->mesh.dim == 1)
         return f64 ? launch_stage_f64_d1(a, c->p, c->flux.kind, mode, s)

@@ -27,15 +27,17 @@ constexpr int EHX = EX + 2, EHY = EY + 2;          // staged columns / rows (one
 template <int P>
 struct Euler2Smem {
     static constexpr int N1 = P + 1, K = N1 * N1;
-    Real u[4][K][EHY][EHX];         // coefficients; tile cell (lx, ly) at [ly + 1][lx + 1]
-    Real hx[4][N1][EY][EX + 1];     // lifted LLF flux of x-face f of row r (cells f - 1, f)
-    Real hy[4][N1][EY + 1][EX];     // lifted LLF flux of y-face r of column c (cells r - 1, r)
+    // the four components as two pairs (rho, rho vx), (rho vy, rho E), each pair one
+    // 8-byte (float) or 16-byte (double) word, so that a pair is one shared load or store
+    R2 u[2][K][EHY][EHX];           // coefficients; tile cell (lx, ly) at [ly + 1][lx + 1]
+    R2 hx[2][N1][EY][EX + 1];       // lifted LLF flux of x-face f of row r (cells f - 1, f)
+    R2 hy[2][N1][EY + 1][EX];       // lifted LLF flux of y-face r of column c (cells r - 1, r)
     Real sx[2][EY][EX + 1];         // max |v| + c of the minus (0) / plus (1) cell's own values on x-face f
     Real sy[2][EY + 1][EX];         // the same on y-face r
     int has[EHY][EHX];              // the staged cell exists
     // float: Un of the tile's cells, brought in by cp.async (in double this would halve
     // the CTAs per SM; double reads Un at the end)
-    Real un[kF32 ? 4 : 1][kF32 ? K : 1][EY][EX];
+    R2 un[kF32 ? 2 : 1][kF32 ? K : 1][EY][EX];
 };
 
 struct Euler2State {
@@ -112,7 +114,7 @@ __device__ __forceinline__ Real sensor_2d(const KParams& A, const Tab<P>& T, con
             for (int m = 0; m < N1; ++m) {
                 if (m < a) continue;
                 const int km = axis == 0 ? m + N1 * j : i + N1 * m;
-                s = fma(T.T[side][a][m], S.u[0][km][rr][cc], s);
+                s = fma(T.T[side][a][m], S.u[0][km][rr][cc].x, s);
             }
             cl[k] = s;
         }
@@ -149,7 +151,7 @@ __device__ __forceinline__ Real sensor_2d(const KParams& A, const Tab<P>& T, con
 
 // MODE 0: stage / residual; MODE 1: sensor only (writes gamma_out).
 template <int P, int MODE>
-__global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __grid_constant__ KParams A)
+__global__ void __launch_bounds__(ENT, (P == 3 || !kF32) ? 2 : 3) euler2d_kernel(const __grid_constant__ KParams A)
 {
     constexpr int N1 = P + 1, NQ = P + 2, K = N1 * N1;
     extern __shared__ __align__(16) unsigned char smem_e2[];
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
 #pragma unroll
         for (int comp = 0; comp < 4; ++comp)
 #pragma unroll
-            for (int k = 0; k < K; ++k) S.u[comp][k][r][cc] = ok ? src[(int64_t)(comp * K + k) * E] : Real(0);
+            for (int k = 0; k < K; ++k) lane(S.u[comp >> 1][k][r][cc], comp & 1) = ok ? src[(int64_t)(comp * K + k) * E] : Real(0);
     }
     const int lx = tid % EX, ly = tid / EX;
     const int gx = tx0 + lx, gy = ty0 + ly;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
         for (int comp = 0; comp < 4; ++comp)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.un[kF32 ? comp : 0][kF32 ? k : 0][ly][lx]);
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&lane(S.un[kF32 ? comp >> 1 : 0][kF32 ? k : 0][ly][lx], comp & 1));
                 const Real* src = A.Un + e + (int64_t)(comp * K + k) * E;
                 asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" :: "r"(dst), "l"(src), "n"((int)sizeof(Real))
                              : "memory");
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
     if (in && (MODE == 1 || A.stab >= STAB_WENO)) {
         Real c[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) c[k] = S.u[0][k][r0][c0];
+        for (int k = 0; k < K; ++k) c[k] = S.u[0][k][r0][c0].x;
         gamma = sensor_2d<P>(A, T, c, S, r0, c0);
         if (MODE == 1) A.gamma_out[e] = (double)gamma;
     }
@@ -209,12 +211,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
     // The four components in two pairs, (rho, rho vx) and (rho vy, rho E): every
     // contraction below runs on both components of a pair at once (packed FP32 in float).
     // cu(pr, k, r, c) = mode k of pair pr of the staged cell at (r, c).
-    auto cu = [&](int pr, int k, int r, int cc) -> R2 {
-        R2 v;
-        v.x = S.u[2 * pr][k][r][cc];
-        v.y = S.u[2 * pr + 1][k][r][cc];
-        return v;
-    };
+    auto cu = [&](int pr, int k, int r, int cc) -> R2 { return S.u[pr][k][r][cc]; };
     R2 acc[2][K];
 #pragma unroll
     for (int pr = 0; pr < 2; ++pr)
@@ -364,8 +361,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
             for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
                 for (int t = 0; t < N1; ++t) {
-                    S.hx[2 * pr][t][fr][fc] = hq[pr][t].x;
-                    S.hx[2 * pr + 1][t][fr][fc] = hq[pr][t].y;
+                    S.hx[pr][t][fr][fc] = hq[pr][t];
                 }
             S.sx[0][fr][fc] = spm;
             S.sx[1][fr][fc] = spp;
@@ -374,8 +370,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
             for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
                 for (int t = 0; t < N1; ++t) {
-                    S.hy[2 * pr][t][fr][fc] = hq[pr][t].x;
-                    S.hy[2 * pr + 1][t][fr][fc] = hq[pr][t].y;
+                    S.hy[pr][t][fr][fc] = hq[pr][t];
                 }
             S.sy[0][fr][fc] = spm;
             S.sy[1][fr][fc] = spp;
@@ -396,11 +391,8 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
 #pragma unroll
         for (int t = 0; t < N1; ++t) {
             // even n: += (m - p); odd n: -= (m + p)
-            R2 xm, xp, ym, yp;
-            xm.x = S.hx[2 * pr][t][ly][lx]; xm.y = S.hx[2 * pr + 1][t][ly][lx];
-            xp.x = S.hx[2 * pr][t][ly][lx + 1]; xp.y = S.hx[2 * pr + 1][t][ly][lx + 1];
-            ym.x = S.hy[2 * pr][t][ly][lx]; ym.y = S.hy[2 * pr + 1][t][ly][lx];
-            yp.x = S.hy[2 * pr][t][ly + 1][lx]; yp.y = S.hy[2 * pr + 1][t][ly + 1][lx];
+            const R2 xm = S.hx[pr][t][ly][lx], xp = S.hx[pr][t][ly][lx + 1];
+            const R2 ym = S.hy[pr][t][ly][lx], yp = S.hy[pr][t][ly + 1][lx];
             const R2 dxe = vsub(xm, xp), dxo = vadd(xm, xp), dye = vsub(ym, yp), dyo = vadd(ym, yp);
 #pragma unroll
             for (int n = 0; n < N1; ++n) {
@@ -423,8 +415,7 @@ __global__ void __launch_bounds__(ENT, P == 3 ? 2 : 3) euler2d_kernel(const __gr
             if (A.has_un) {
                 R2 unk;
                 if constexpr (kF32) {
-                    unk.x = S.un[2 * pr][k][ly][lx];
-                    unk.y = S.un[2 * pr + 1][k][ly][lx];
+                    unk = S.un[pr][k][ly][lx];
                 } else {
                     const Real* a0 = A.Un + e + (int64_t)(2 * pr * K + k) * E;
                     const Real* a1 = a0 + (int64_t)K * E;

@@ -1165,6 +1165,10 @@ static KParams make_params(const StageArgs& s)
 // ------------------------------------------------------------------------------------
 // batched ensemble: persistent kernel
 // ------------------------------------------------------------------------------------
+// cells per thread of the batch kernels: two stacked in y on the packed FP32 pipe (2D
+// float), else one
+constexpr int kBatchLanes = (kF32 && DIM == 2) ? 2 : 1;
+
 template <int P, int FLUX, int TYB>
 __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst& I, const int r,
                                             const int tile0, const int ntile, unsigned char* smem)
@@ -1204,11 +1208,11 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     A.cn = (Real)(r == 0 ? 0.0 : (r == 1 ? 0.75 : 1.0 / 3.0));
     A.ck = (Real)(r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0));
     A.cl = (Real)(r == 0 ? dt : (r == 1 ? 0.25 * dt : 2.0 / 3.0 * dt));
-    TileSmem<P, 1, TYB>& S = *reinterpret_cast<TileSmem<P, 1, TYB>*>(smem);
+    TileSmem<P, kBatchLanes, TYB>& S = *reinterpret_cast<TileSmem<P, kBatchLanes, TYB>*>(smem);
     for (int t = tile0; t < tile0 + ntile; ++t) {
         const int tx0 = (t % I.ntx) * TX;
-        const int ty0 = DIM == 2 ? (t / I.ntx) * TYB : 0;
-        process_tile<P, FLUX, 0, 1, TYB, false>(A, tx0, ty0, S);
+        const int ty0 = DIM == 2 ? (t / I.ntx) * (TYB * kBatchLanes) : 0;
+        process_tile<P, FLUX, 0, kBatchLanes, TYB, false>(A, tx0, ty0, S);
         __syncthreads();
     }
 }
@@ -1221,7 +1225,7 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 }
 
 // Persistent kernel over all work items of all stages of the instances of degree P, in
-// tiles of TX x TYB cells (TYB thread rows of one cell each): items are dequeued in
+// tiles of TX x (TYB kBatchLanes) cells (TYB thread rows): items are dequeued in
 // order, and an item waits only for its own instance's previous stage, whose items were
 // all dequeued earlier by CTAs that are running, so no wait can deadlock (whether or not
 // the whole grid is resident: the kernels of the batch run side by side on streams of
@@ -1231,15 +1235,18 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 template <int P, int TYB>
 constexpr size_t batch_smem_bytes()
 {
-    return (sizeof(TileSmem<P, 1, TYB>) + 127) / 128 * 128 + 128;   // tile + scheduler words
+    return (sizeof(TileSmem<P, kBatchLanes, TYB>) + 127) / 128 * 128 + 128;   // tile + scheduler words
 }
 
-// resident CTAs per SM the register budget is sized for: float 64 / 80 / 128 registers a
-// thread for P = 1 / 2 / 3 (the degree-3 tile spills at fewer), double 168
+// resident CTAs per SM the register budget is sized for: two cells per thread (2D float)
+// 80 / 104 / 168 registers a thread for P = 1 / 2 / 3, one cell (1D float) 64 / 80 / 128
+// (the degree-3 tile spills at fewer), double 168
 template <int P, int TYB>
 constexpr int batch_min_blocks()
 {
-    return kF32 ? 65536 / (TX * TYB * (P == 1 ? 64 : (P == 2 ? 80 : 128))) : 65536 / (TX * TYB * 168);
+    constexpr int regs = !kF32 ? 168 : (kBatchLanes == 2 ? (P == 1 ? 80 : (P == 2 ? 104 : 168))
+                                                         : (P == 1 ? 64 : (P == 2 ? 80 : 128)));
+    return 65536 / (TX * TYB * regs) > 0 ? 65536 / (TX * TYB * regs) : 1;
 }
 
 template <int P, int TYB>
@@ -1293,7 +1300,8 @@ __global__ void __launch_bounds__(TX * TYB, batch_min_blocks<P, TYB>()) batch_ke
     }
 }
 
-// Tile heights built for the batch kernel: 2, 4 and 8 cell rows (float, 2D), else one.
+// Tile heights (cell rows) built for the batch kernel: 2, 4 and 8 (float, 2D: one, two or
+// four thread rows of two cells), kTileY2 (double, 2D), one (1D).
 constexpr bool batch_rows_built(int rows)
 {
     return DIM == 1 ? rows == 1 : (kF32 ? (rows == 2 || rows == 4 || rows == 8) : rows == kTileY2);
@@ -1324,10 +1332,10 @@ static int batch_blocks_per_sm_p(int rows)
 {
     if constexpr (DIM == 1) return rows == 1 ? batch_blocks_per_sm_pt<P, 1>() : 0;
     else if constexpr (kF32) {
-        switch (rows) {
-        case 2: return batch_blocks_per_sm_pt<P, 2>();
-        case 4: return batch_blocks_per_sm_pt<P, 4>();
-        case 8: return batch_blocks_per_sm_pt<P, 8>();
+        switch (rows) {       // cell rows = thread rows x 2
+        case 2: return batch_blocks_per_sm_pt<P, 1>();
+        case 4: return batch_blocks_per_sm_pt<P, 2>();
+        case 8: return batch_blocks_per_sm_pt<P, 4>();
         default: return 0;
         }
     } else return rows == kTileY2 ? batch_blocks_per_sm_pt<P, kTileY2>() : 0;
@@ -1338,10 +1346,10 @@ static cudaError_t launch_batch_p(const BatchArgs& a, int rows, int grid, cudaSt
 {
     if constexpr (DIM == 1) return rows == 1 ? launch_batch_pt<P, 1>(a, grid, st) : cudaErrorInvalidValue;
     else if constexpr (kF32) {
-        switch (rows) {
-        case 2: return launch_batch_pt<P, 2>(a, grid, st);
-        case 4: return launch_batch_pt<P, 4>(a, grid, st);
-        case 8: return launch_batch_pt<P, 8>(a, grid, st);
+        switch (rows) {       // cell rows = thread rows x 2
+        case 2: return launch_batch_pt<P, 1>(a, grid, st);
+        case 4: return launch_batch_pt<P, 2>(a, grid, st);
+        case 8: return launch_batch_pt<P, 4>(a, grid, st);
         default: return cudaErrorInvalidValue;
         }
     } else return rows == kTileY2 ? launch_batch_pt<P, kTileY2>(a, grid, st) : cudaErrorInvalidValue;

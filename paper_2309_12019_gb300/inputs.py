@@ -245,6 +245,11 @@ SHOCK_TUBES = {
                 bc=("outflow", "outflow"), t_end=0.14, nx=512, p=2, lam=5.0),
     "shu_osher": dict(box=(-5.0, 5.0), jumps=(-4.0,), states=((3.857143, 2.629369, 10.3333), "sine"),
                       bc=("outflow", "reflect"), t_end=1.8, nx=512, p=2, lam=5.0),
+    # Woodward-Colella blast wave: the paper's three states (its middle pressure is 0.1)
+    # between reflecting walls, the jumps read as the cited problem's x = 0.1 and 0.9 (the
+    # paper gives none); |v| + c stays below 60 (c = 37.4 in the left state)
+    "blast": dict(box=(0.0, 1.0), jumps=(0.1, 0.9), states=((1.0, 0.0, 1000.0), (1.0, 0.0, 0.1), (1.0, 0.0, 100.0)),
+                  bc=("reflect", "reflect"), t_end=0.038, nx=512, p=2, lam=60.0),
 }
 
 GAS_GAMMA = 1.4

@@ -767,3 +767,21 @@ def test_fp32_sensor_decisions_on_kpp_1024():
           f"max |dgamma| where both active {float(np.max(np.abs(g32 - g64)[both], initial=0.0)):.2e}")
     assert not np.any(differ & ~near)
     assert np.max(np.abs(g32 - g64)[both], initial=0.0) <= H.R_FLOAT_ERR
+
+
+def test_tma_descriptor_cache_eviction():
+    """The context caches one TMA descriptor per array and evicts them all past 64 arrays.
+    Steps on 80 fresh arrays (each stage launch looks up the descriptors of two arrays, so
+    an eviction falls between the two lookups) still get valid descriptors: every step
+    equals dgw_rk_step's bit for bit and no bounded wait gives up."""
+    s = H.spec(2, 2, 64, ny=40, flux="burgers")
+    ctx = gpu(s, "fp32")
+    U = to_dev(H.state_for(s, seed=21), "fp32")
+    ref = U.clone()
+    ctx.rk_step(ref, 1e-3, 1, stream=0)
+    for _ in range(80):
+        U1, U2, nxt = torch.empty_like(U), torch.empty_like(U), torch.empty_like(U)
+        ctx.rk_step_stages(U.clone(), 1e-3, U1, U2, nxt)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        assert torch.equal(nxt, ref)
