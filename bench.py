@@ -128,31 +128,61 @@ def qform_flops(p, dim):
     return 2 * pairs + 2 * (k - 1) + 3
 
 
+def _interp_sym_flops(n1, nq):
+    """Flops of the values of sum_i r_i P_i at nq symmetric Gauss nodes from the even and
+    odd parts (P_0 = 1 and the vanishing odd terms at the centre left out)."""
+    f = (nq // 2) * (2 * (n1 - 1) + 2 - 1 + 2)     # per pair: e, o chains (first o a product), +-
+    if nq % 2:
+        f += 2 * len(range(2, n1, 2))
+    return f
+
+
+def _project_sym_flops(n1, nq, deriv):
+    """Flops of sum_q W_q P_i(g_q) f_q (or P_i') for all i on symmetric nodes: sums and
+    differences of the pairs, then one product per pair (and the centre where its row
+    does not vanish by parity); P_0' = 0 skipped."""
+    npair = nq // 2
+    f = 2 * npair
+    for i in range(1 if deriv else 0, n1):
+        even_fn = (i % 2 == 1) if deriv else (i % 2 == 0)
+        terms = npair + (1 if (nq % 2 and even_fn) else 0)
+        f += 2 * terms - 1
+    return f
+
+
 def stage_flops_per_cell(dim, p, flux, stab):
-    """Algorithmic FP32 flops of one stage per cell, following the stage kernel's
-    sum-factorised operators (an FMA counts 2, any other arithmetic operation 1), and the
-    number of sin/cos pairs (KPP flux).  Faces: dim owned faces per cell."""
+    """FP32 flops of one stage per cell as the stage kernel evaluates it (an FMA counts 2,
+    any other arithmetic operation 1): symmetric-node interpolations and projections,
+    structural zeros and unit factors left out, the parity-sparse quadratic forms of the
+    sensor; and the number of sin/cos pairs (KPP flux).  Faces: dim owned faces per cell."""
     n1, nq = p + 1, p + 2
     k = n1 ** dim
     kpp = flux == "kpp"
-    red = 6                                        # 2 pi reduction of one sin/cos argument
+    red = 5                                        # packed 2 pi reduction of one sin/cos argument
     f = 0
     if stab in ("weno", "zhao"):                   # Hermite candidates, indicators, blend
         qf = qform_flops(p, dim)
         for axis in range(dim):
-            shift = sum(2 * (n1 - ((c % n1) if axis == 0 else (c // n1))) for c in range(1, k))
+            shift = sum(2 * (n1 - 1 - ((c % n1) if axis == 0 else (c // n1))) for c in range(1, k))
             f += 2 * (shift + qf + 4 + 3 * (k - 1))
         f += 2 * qf + 2 + 3 + 1 + (k - 1) + 3
-    if dim == 2:                                   # volume: interpolation, flux, projection
-        f += 2 * n1 * nq * n1 + 2 * nq * nq * n1 + nq * nq * 4 * n1 + 4 * k * nq
+    if dim == 2:                                   # volume, one Gauss row at a time
+        per_row = (2 * n1 * (n1 - 1)               # the polynomial reduced to the row
+                   + _interp_sym_flops(n1, nq)     # values at the row's points
+                   + _project_sym_flops(n1, nq, True) + _project_sym_flops(n1, nq, False)
+                   + 2 * sum((i > 0) + (j > 0) for i in range(n1) for j in range(n1)))
+        f += nq * per_row
         npts = nq * nq
     else:
         npts = nq
-        f += nq * 4 * n1
+        f += _interp_sym_flops(n1, nq) + _project_sym_flops(n1, nq, True)
     f += npts * (red if kpp else 2)
     nfq = nq if dim == 2 else 1                    # faces: traces at the points, LLF, lift
-    llf = 2 * red + 14 if kpp else 6
-    f += dim * nfq * ((4 * n1 if dim == 2 else 0) + llf + (2 * n1 if dim == 2 else n1))
+    llf = 2 * red + 12 if kpp else 6
+    if dim == 2:
+        f += dim * (2 * _interp_sym_flops(n1, nq) + nfq * llf + _project_sym_flops(n1, nq, False))
+    else:
+        f += dim * (nfq * llf + 1)
     f += 2 * dim * k                               # face traces
     f += 4 * n1 + 2 * k if dim == 2 else 2 + 2 * n1   # face contributions
     if stab != "dg":                               # gamma nu K c

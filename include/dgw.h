@@ -314,9 +314,10 @@ dgw_status dgw_batch_sync_status(dgw_batch* b, void* stream);
 dgw_status dgw_batch_debug(dgw_batch* b, long long wait_limit, int unreachable);
 
 /* SSP-RK3 steps for callers that cannot allocate device memory (the paper has no
- * counterpart; this is a deployment convenience).  Such callers include work recorded
- * into a CUDA graph by stream capture, applications whose device memory belongs to
- * another allocator, and real-time code that allows no allocation after start-up.
+ * counterpart; this is a deployment convenience).  Such callers include applications
+ * whose device memory all belongs to another allocator (a framework's pool that leaves
+ * nothing to cudaMalloc), and real-time or safety-critical code that may not allocate
+ * after start-up, where an allocation can block or fail at an arbitrary point.
  * The arguments combine those of dgw_create and dgw_rk_step, and the result equals
  * theirs, but nothing is allocated: the two stage states live in one file-scope
  * device array of 2 x 8 MiB (+256 bytes) that every GPU loading the library keeps

@@ -69,7 +69,7 @@ __device__ __forceinline__ Real dspeed(const KParams& A, Real u)
 }
 
 template <int P, int FLUX>
-__global__ void __launch_bounds__(128) vjp_kernel(const KParams A, const Real* __restrict__ lam,
+__global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams A, const Real* __restrict__ lam,
                                                   Real* __restrict__ wself, Real* __restrict__ wnb)
 {
     constexpr int N1 = P + 1, NQ = P + 2, K = Tab<P>::K, NF = 2 * DIM;

@@ -1516,10 +1516,10 @@ extern "C" dgw_status dgw_selftest_sincos(const float* x, float* s, float* c, in
 // ------------------------------------------------------------------------------------
 // SSP-RK3 steps without any device allocation
 // ------------------------------------------------------------------------------------
-// Some callers cannot call cudaMalloc: work being recorded into a CUDA graph by stream
-// capture (allocating there breaks or invalidates the capture), applications whose
-// device memory is owned by another allocator, and real-time code that allows no
-// allocation after start-up.  dgw_rk_step_noalloc serves them: instead of a context's
+// Some callers cannot call cudaMalloc: applications whose device memory is all owned by
+// another allocator, and real-time code that allows no allocation after start-up (an
+// allocation can block or fail at an arbitrary point).  dgw_rk_step_noalloc serves them:
+// instead of a context's
 // stage buffers it keeps the two SSP-RK3 stage states in this fixed array, which every
 // GPU that loads the library holds until the process exits.  Layout: stage 1, stage 2
 // (kNoAllocStageBytes each), then the kernels' error flag.  Nothing in it has to start
