@@ -384,6 +384,24 @@ def run_ensemble(steps, warmup, local, n=512, autotune=True):
     return out
 
 
+def run_tc_volume(local, ntiles=8192):
+    """The Q3 KPP volume term of 1,048,576 cells (the headline workload's count) on the
+    CUDA cores as the stage kernel computes it, and on the tensor cores (tcgen05, three
+    TF32 passes): the kernels' times from CUDA events, best of 5 after a warm-up."""
+    import torch
+
+    from paper_2309_12019_gb300 import dgw
+    dev = torch.device("cuda", local)
+    U = torch.rand((16, ntiles * 128), dtype=torch.float32, device=dev) * 3.0 + 5.0
+    out = torch.empty_like(U)
+    t = {}
+    for variant in (0, 1):
+        dgw.selftest_tc_volume(U, out, variant)
+        t[variant] = min(dgw.selftest_tc_volume(U, out, variant) for _ in range(5))
+    return {"cells": ntiles * 128, "cuda_cores_us": 1e3 * t[0], "tensor_cores_us": 1e3 * t[1],
+            "what": "volume term of the Q3 KPP stage: [cells x 16] x [16 x 25], sin/cos, [cells x 50] x [50 x 16]"}
+
+
 def run_adjoint(local, n=512, steps=200, every=20):
     """The adjoint workload: 2D Burgers (u^2/2, u^2/2), periodic unit square, n^2 Q2,
     FP32, misfit after `steps` SSP-RK3 steps against a target grown from another seeded
@@ -602,6 +620,7 @@ def main():
         r64["steps"] = st64
     extras = {}
     if not args.no_extras:
+        extras["volume_term_tensor_cores"] = run_tc_volume(local)
         extras["ensemble"] = run_ensemble(100, 3, local)
         extras["adjoint"] = run_adjoint(local)
         extras["others"] = [run_small("kpp_1024x1024_q3_zhao", "fp32", 100, 5, local),

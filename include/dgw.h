@@ -342,6 +342,18 @@ dgw_status dgw_rk_step_noalloc(const dgw_mesh* mesh, int p, const dgw_flux* flux
  * (device).  Exists so that tests can bound its error against double precision. */
 dgw_status dgw_selftest_sincos(const float* x, float* s, float* c, int64_t n, void* stream);
 
+/* Diagnostic: the volume term of the KPP problem at Q3 (Eq. weak2, F = (sin u, cos u) at
+ * the 5 x 5 Gauss points) for ntiles tiles of 128 cells, by the packed-FP32 CUDA-core code
+ * of the stage kernel (variant 0) or on the tensor cores (variant 1: tcgen05.mma
+ * kind::tf32 in three passes, hi.hi + hi.lo + lo.hi of a TF32 split, accumulators in
+ * tensor memory).  U: device float[16][ntiles * 128] (mode-major, k = i + 4 j); out: the
+ * same shape, acc_k = sum over the Gauss points of W grad(phi_k).F in reference units.
+ * Synchronous; *ms (host, may be NULL) receives the kernel's duration from CUDA events
+ * on the stream.  Exists so that tests and the benchmark can compare the two on the same
+ * work; DGW_ETIMEOUT if a bounded wait of variant 1 gave up. */
+dgw_status dgw_selftest_tc_volume(const float* U, float* out, int64_t ntiles, int variant, float* ms,
+                                  void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* dgw_last_error(void);
 

@@ -1513,6 +1513,37 @@ extern "C" dgw_status dgw_selftest_sincos(const float* x, float* s, float* c, in
     return DGW_OK;
 }
 
+extern "C" dgw_status dgw_selftest_tc_volume(const float* U, float* out, int64_t ntiles, int variant, float* ms,
+                                             void* stream)
+{
+    if (!U || !out || ntiles < 0 || (variant != 0 && variant != 1)) return fail(DGW_EINVAL, "bad arguments");
+    if (((uintptr_t)U & 15u) || ((uintptr_t)out & 15u)) return fail(DGW_EINVAL, "arrays must be 16-byte aligned");
+    if (ntiles == 0) return DGW_OK;
+    static std::mutex mu;
+    static std::set<int> ready;                 // devices with the degree-3 float 2D tables
+    int dev = -1;
+    DGW_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready.count(dev)) {
+            HostTables t;
+            build_tables(3, &t);
+            DGW_CUDA(upload_tables_f32_d2(t));
+            ready.insert(dev);
+        }
+    }
+    unsigned* flag = nullptr;
+    DGW_CUDA(cudaMalloc(&flag, sizeof(unsigned)));
+    cudaError_t e = cudaMemset(flag, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = launch_tc_volume_f32_d2(U, out, ntiles, variant, flag, ms, (cudaStream_t)stream);
+    unsigned v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, flag, sizeof v, cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e != cudaSuccess) return fail(DGW_ECUDA, "tensor-core volume probe: %s", cudaGetErrorString(e));
+    if (v & 2u) return fail(DGW_ETIMEOUT, "tensor-core volume probe: a bounded wait for the MMAs gave up");
+    return DGW_OK;
+}
+
 // ------------------------------------------------------------------------------------
 // SSP-RK3 steps without any device allocation
 // ------------------------------------------------------------------------------------

@@ -156,6 +156,12 @@ cudaError_t launch_gather_f32_d2(const GatherArgs& g, int p, cudaStream_t s);
 cudaError_t launch_gather_f64_d1(const GatherArgs& g, int p, cudaStream_t s);
 cudaError_t launch_gather_f64_d2(const GatherArgs& g, int p, cudaStream_t s);
 
+// The Q3 KPP volume term on 128-cell tiles: variant 0 on the CUDA cores (packed FP32),
+// 1 on the tensor cores (tcgen05, three TF32 passes).  Synchronous; *ms (may be NULL)
+// receives the kernel's duration from CUDA events on the stream.  Diagnostic.
+cudaError_t launch_tc_volume_f32_d2(const float* U, float* out, int64_t ntiles, int variant, unsigned* flag,
+                                    float* ms, cudaStream_t s);
+
 cudaError_t upload_tables_f32_d1(const HostTables& t);
 cudaError_t upload_tables_f32_d2(const HostTables& t);
 cudaError_t upload_tables_f64_d1(const HostTables& t);

@@ -20,10 +20,14 @@
 //      and the SSP-RK3 combination Uout = cn Un + ck Uk + cl L(Uk) (Eq. ssp).
 // Constant factors are folded so that, in the reference element,
 //   L_k = (2/h) minv(k) [acc_k - gamma lambda / p (K_ref c)_k].
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "dgw_internal.h"
 #include "dgw_math.cuh"
@@ -899,7 +903,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         constexpr int NFQ = DIM == 1 ? 1 : NQ;
         // KPP: a y-face is an x-face of the states shifted by pi/2 (llf_kpp).  P_0 = 1, so
         // the shift added to the first trace coefficient shifts every face value.
-        const Real sh = (FLUX == FLUX_KPP && DIM == 2 && !xf) ? Real(0.5 * kPi) : Real(0);
+        [[maybe_unused]] const Real sh = (FLUX == FLUX_KPP && DIM == 2 && !xf) ? Real(0.5 * kPi) : Real(0);
         if constexpr (FLUX == FLUX_KPP && DIM == 2) {
             tm[0] = vadd(tm[0], vbc<V>(sh));
             tp[0] = vadd(tp[0], vbc<V>(sh));
@@ -1453,6 +1457,9 @@ __device__ __forceinline__ Real max_nan(Real a, Real b)
 #include "dgw_euler_impl.cuh"
 #else
 #include "dgw_euler2d_impl.cuh"
+#endif
+#if DGW_DIM == 2 && defined(DGW_TC_VOLUME)
+#include "dgw_tc_volume.cuh"
 #endif
 
 template <int P, int FLUX>

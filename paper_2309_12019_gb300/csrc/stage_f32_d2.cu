@@ -2,6 +2,7 @@
 #define DGW_REAL float
 #define DGW_DIM 2
 #define DGW_NS f32_d2
+#define DGW_TC_VOLUME 1
 #include "dgw_stage_impl.cuh"
 
 namespace dgw {
@@ -21,4 +22,9 @@ cudaError_t launch_vjp_f32_d2(const StageArgs& a, int p, int flux, const void* l
 }
 cudaError_t launch_gather_f32_d2(const GatherArgs& g, int p, cudaStream_t s) { return f32_d2::launch_gather(g, p, s); }
 cudaError_t upload_tables_f32_d2(const HostTables& t) { return f32_d2::upload_tables(t); }
+cudaError_t launch_tc_volume_f32_d2(const float* U, float* out, int64_t ntiles, int variant, unsigned* flag,
+                                    float* ms, cudaStream_t s)
+{
+    return f32_d2::launch_tc_volume(U, out, ntiles, variant, flag, ms, s);
+}
 }  // namespace dgw

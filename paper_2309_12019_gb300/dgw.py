@@ -61,7 +61,7 @@ EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_pa
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
            "dgw_sync_status", "dgw_debug", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_rk_step_stages", "dgw_adjoint_step_stages", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
-           "dgw_batch_schedule", "dgw_batch_set_schedule", "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos",
+           "dgw_batch_schedule", "dgw_batch_set_schedule", "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos", "dgw_selftest_tc_volume",
            "dgw_last_error", "dgw_version")
 
 
@@ -110,6 +110,7 @@ def load(build: bool = True):
         L.dgw_rk_step_noalloc.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.POINTER(Flux),
                                           ctypes.POINTER(Params), vp, ctypes.c_double, ctypes.c_int, vp]
         L.dgw_selftest_sincos.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
+        L.dgw_selftest_tc_volume.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]
         L.dgw_last_error.restype = ctypes.c_char_p
         L.dgw_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -420,3 +421,15 @@ def selftest_sincos(x, stream=None):
 
 def version() -> str:
     return load().dgw_version().decode()
+
+
+def selftest_tc_volume(U, out, variant: int, stream=None) -> float:
+    """The Q3 KPP volume term of U (float [16][ntiles * 128]) into out, on the CUDA cores
+    (variant 0) or the tensor cores (variant 1); returns the kernel's time in ms
+    (dgw_selftest_tc_volume)."""
+    if U.numel() % (16 * 128) or out.numel() != U.numel():
+        raise ValueError("U and out: float [16][ntiles * 128]")
+    ms = ctypes.c_float()
+    _check(load().dgw_selftest_tc_volume(_ptr(U), _ptr(out), U.numel() // (16 * 128), int(variant),
+                                          ctypes.byref(ms), _stream(stream)))
+    return ms.value
