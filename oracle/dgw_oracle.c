@@ -70,6 +70,12 @@
  *      |v.n| + c of the two states; lambda_e = max (|v| + c) over the volume Gauss points
  *      and the element's own values at the face Gauss points.  A reflecting wall mirrors
  *      the normal momentum: m+ = m- - 2 (m-.n) n.  Stabilization and sensor as in R15.
+ *   R19 prescribed boundary states (Euler system, the double Mach reflection of Sec. 5.6):
+ *      a side of kind ORC_BC_STATE takes, at each face point, the ghost bstate[0] or
+ *      bstate[1] or a reflecting wall, by whether the point's coordinate along the side
+ *      lies below bsplit + bspeed t or not (t the time of the evaluation).  The SSP-RK
+ *      steps evaluate stage residuals at their stage times: t, t + dt, t + dt / 2 (order 3),
+ *      t, t + dt (order 2); order 4 holds every stage at the step's start time.
  *   R13 the comparison sensor of Zhao et al. (restated in Sec. 5.6), stab = ZHAO:
  *      gamma^Z = sum_l |w_l / lin_l - 1|^theta / (|1 / min_l lin_l - 1|^theta + m_e) with
  *      the weights of R3; with no neighbour candidate (m_e = 0) the weights are the linear
@@ -91,7 +97,7 @@
 #define ORC_MAXK ((ORC_MAXP + 1) * (ORC_MAXP + 1))
 #define ORC_MAXNQ 32
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW_ZERO = 1, ORC_BC_OUTFLOW = 2, ORC_BC_REFLECT = 3 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW_ZERO = 1, ORC_BC_OUTFLOW = 2, ORC_BC_REFLECT = 3, ORC_BC_STATE = 4 };
 enum { ORC_FLUX_ADVECT = 0, ORC_FLUX_ROTATION = 1, ORC_FLUX_BURGERS = 2, ORC_FLUX_KPP = 3, ORC_FLUX_EULER = 4 };
 enum { ORC_STAB_DG = 0, ORC_STAB_LO = 1, ORC_STAB_WENO = 2, ORC_STAB_ZHAO = 3 };
 
@@ -108,6 +114,11 @@ typedef struct {
     double q, b, w_nbr, eps_w, eps_s;
     double theta;            /* exponent of the Zhao et al. sensor (stab = ZHAO) */
     double gas_gamma;        /* ratio of heat capacities (Euler) */
+    double t;                /* time of the evaluation (prescribed boundary states, R19) */
+    double bstate[2][4];     /* the two prescribed conservative states of ORC_BC_STATE sides */
+    double bsplit[4];        /* per side: position along the side where its ghost changes, t = 0 */
+    double bspeed[4];        /* per side: speed of that position */
+    int bbelow[4], babove[4];/* per side, below / from the split: 0, 1 = bstate[0], [1]; 2 = wall */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -776,7 +787,15 @@ static void euler_residual_elem(const orc_problem* P, const double* U, long e, d
                 euler_state(P, cn, fr[t] + sx, fs[t] + sy, up);
             } else {
                 for (int c = 0; c < m; ++c) up[c] = um[c];
-                if (P->bc[f] == ORC_BC_REFLECT) {
+                int wall = P->bc[f] == ORC_BC_REFLECT;
+                if (P->bc[f] == ORC_BC_STATE) {
+                    /* R19: the coordinate along the side against the moving split */
+                    double s = f < 2 ? fy[t] : fx[t];
+                    int ch = s < P->bsplit[f] + P->bspeed[f] * P->t ? P->bbelow[f] : P->babove[f];
+                    if (ch == 2) wall = 1;
+                    else for (int c = 0; c < m; ++c) up[c] = P->bstate[ch][c];
+                }
+                if (wall) {
                     /* mirror the normal momentum: m+ = m- - 2 (m-.n) n */
                     double mn = um[1] * n[0] + (P->dim == 2 ? um[2] * n[1] : 0.0);
                     up[1] = um[1] - 2.0 * mn * n[0];
@@ -839,8 +858,11 @@ int orc_check(const orc_problem* P)
         if (fabs(hx - hy) > 1e-12 * hx) return -1;
     }
     if (P->stab == ORC_STAB_ZHAO && !(P->w_nbr > 0.0 && P->theta > 0.0)) return -1;   /* lin_l > 0 */
-    for (int f = 0; f < 2 * P->dim; ++f)           /* walls are for the Euler system */
-        if (P->bc[f] == ORC_BC_REFLECT && P->flux != ORC_FLUX_EULER) return -1;
+    for (int f = 0; f < 2 * P->dim; ++f) {         /* walls and prescribed states: Euler system */
+        if ((P->bc[f] == ORC_BC_REFLECT || P->bc[f] == ORC_BC_STATE) && P->flux != ORC_FLUX_EULER) return -1;
+        if (P->bc[f] == ORC_BC_STATE && (P->bbelow[f] < 0 || P->bbelow[f] > 2 || P->babove[f] < 0 || P->babove[f] > 2))
+            return -1;
+    }
     if (P->flux == ORC_FLUX_EULER && !(P->gas_gamma > 1.0)) return -1;
     return 0;
 }
@@ -905,12 +927,17 @@ void orc_rk3(const orc_problem* P, double* U, double dt, int nsteps)
     double* L = malloc(sizeof(double) * N);
     double* U1 = malloc(sizeof(double) * N);
     double* U2 = malloc(sizeof(double) * N);
+    orc_problem Q = *P;                 /* the stage times (R19): t, t + dt, t + dt / 2 */
     for (int s = 0; s < nsteps; ++s) {
-        orc_residual(P, U, L);
+        const double t0 = P->t + s * dt;
+        Q.t = t0;
+        orc_residual(&Q, U, L);
         for (long i = 0; i < N; ++i) U1[i] = U[i] + dt * L[i];
-        orc_residual(P, U1, L);
+        Q.t = t0 + dt;
+        orc_residual(&Q, U1, L);
         for (long i = 0; i < N; ++i) U2[i] = 0.75 * U[i] + 0.25 * U1[i] + 0.25 * dt * L[i];
-        orc_residual(P, U2, L);
+        Q.t = t0 + 0.5 * dt;
+        orc_residual(&Q, U2, L);
         for (long i = 0; i < N; ++i) U[i] = U[i] / 3.0 + 2.0 / 3.0 * U2[i] + 2.0 / 3.0 * dt * L[i];
     }
     free(L); free(U1); free(U2);
@@ -924,10 +951,13 @@ void orc_rk2(const orc_problem* P, double* U, double dt, int nsteps)
     long N = nstate(P);
     double* L = malloc(sizeof(double) * N);
     double* U1 = malloc(sizeof(double) * N);
+    orc_problem Q = *P;                 /* the stage times (R19): t, t + dt */
     for (int s = 0; s < nsteps; ++s) {
-        orc_residual(P, U, L);
+        Q.t = P->t + s * dt;
+        orc_residual(&Q, U, L);
         for (long i = 0; i < N; ++i) U1[i] = U[i] + dt * L[i];
-        orc_residual(P, U1, L);
+        Q.t = P->t + s * dt + dt;
+        orc_residual(&Q, U1, L);
         for (long i = 0; i < N; ++i) U[i] = 0.5 * U[i] + 0.5 * U1[i] + 0.5 * dt * L[i];
     }
     free(L); free(U1);

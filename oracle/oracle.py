@@ -29,7 +29,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3}
+BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3, "state": 4}
 
 # Threshold b of Eq. (gensensor) when none is given (reading R5): the remark of Sec. 4
 # switches the sensor off below a prescribed tolerance, and b = 0.1 (the smaller of the
@@ -71,6 +71,9 @@ class _Problem(ctypes.Structure):
         ("q", ctypes.c_double), ("b", ctypes.c_double), ("w_nbr", ctypes.c_double),
         ("eps_w", ctypes.c_double), ("eps_s", ctypes.c_double),
         ("theta", ctypes.c_double), ("gas_gamma", ctypes.c_double),
+        ("t", ctypes.c_double), ("bstate", (ctypes.c_double * 4) * 2),
+        ("bsplit", ctypes.c_double * 4), ("bspeed", ctypes.c_double * 4),
+        ("bbelow", ctypes.c_int * 4), ("babove", ctypes.c_int * 4),
     ]
 
 
@@ -96,6 +99,15 @@ class Problem:
     eps_s: float = 1e-12
     theta: float = 1.0
     gas_gamma: float = 1.4
+    # prescribed boundary states (Euler, bc "state", reading R19): the time of the
+    # evaluation, two conservative states, and per side the split position along the side
+    # at t = 0, its speed, and the ghost below / from it (0, 1: bstate[0], [1]; 2: wall)
+    t: float = 0.0
+    bstate: tuple = ((0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0))
+    bsplit: tuple = (0.0, 0.0, 0.0, 0.0)
+    bspeed: tuple = (0.0, 0.0, 0.0, 0.0)
+    bbelow: tuple = (0, 0, 0, 0)
+    babove: tuple = (0, 0, 0, 0)
 
     def __post_init__(self):
         if self.b is None:
@@ -132,6 +144,13 @@ class Problem:
         s.q, s.b, s.w_nbr, s.eps_w, s.eps_s = self.q, self.b, self.w_nbr, self.eps_w, self.eps_s
         s.theta = self.theta
         s.gas_gamma = self.gas_gamma
+        s.t = self.t
+        for i in range(2):
+            for c in range(4):
+                s.bstate[i][c] = self.bstate[i][c]
+        for f in range(4):
+            s.bsplit[f], s.bspeed[f] = self.bsplit[f], self.bspeed[f]
+            s.bbelow[f], s.babove[f] = self.bbelow[f], self.babove[f]
         return s
 
 
@@ -276,7 +295,7 @@ def project(P: Problem, samples, nq: int = 8) -> np.ndarray:
     one component after the other)."""
     if P.flux == "euler":
         f = np.asarray(samples, dtype=np.float64).reshape(P.ncomp, -1)
-        Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b == "reflect" else b for b in P.bc))
+        Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b in ("reflect", "state") else b for b in P.bc))
         return np.concatenate([project(Ps, f[c], nq) for c in range(P.ncomp)], axis=0)
     c = _checked(P)
     f = np.ascontiguousarray(np.asarray(samples, dtype=np.float64)).reshape(-1)

@@ -282,7 +282,7 @@ def euler_residual(P, U):
     m = Mesh(dataclasses.replace(P, flux="advect"))
     E, g, K = P.E, P.gas_gamma, (P.p + 1) ** d
     nc = d + 2
-    Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b == "reflect" else b for b in P.bc))
+    Ps = dataclasses.replace(P, flux="advect", bc=tuple("outflow" if b in ("reflect", "state") else b for b in P.bc))
     if P.stab in ("weno", "zhao"):
         gam = sensor(Ps, U[:K])
     else:
@@ -323,11 +323,21 @@ def euler_residual(P, U):
             nb, cn = m.nbr(e, f)
             if nb is not None:
                 up = np.array([m.poly(U[comp * K:(comp + 1) * K, nb], 0, 0, cn, fx, fy) for comp in range(nc)])
-            elif P.bc[f] == "reflect":
+            elif P.bc[f] in ("reflect", "state"):
                 up = um.copy()
                 mn = sum(um[1 + a] * n[a] for a in range(d))
+                wall = np.ones(um.shape[1], dtype=bool)
+                if P.bc[f] == "state":
+                    # per face point: a prescribed state or a wall, by the point's position
+                    # along the side against the moving split
+                    along = fy if f < 2 else fx
+                    ch = np.where(along < P.bsplit[f] + P.bspeed[f] * P.t, P.bbelow[f], P.babove[f])
+                    wall = ch == 2
+                    for i in (0, 1):
+                        sel = ch == i
+                        up[:, sel] = np.asarray(P.bstate[i][:nc], dtype=np.float64)[:, None]
                 for a in range(d):
-                    up[1 + a] = um[1 + a] - 2.0 * mn * n[a]
+                    up[1 + a] = np.where(wall, um[1 + a] - 2.0 * mn * n[a], up[1 + a])
             else:
                 up = um.copy()
             s = np.maximum(_euler_speed(g, um, n), _euler_speed(g, up, n))

@@ -374,3 +374,59 @@ def test_density_wave_converges_at_optimal_order(p):
     if p == 2:
         w = [_density_wave_error(n, p, "weno") for n in (32, 64)]
         assert np.log2(w[0] / w[1]) > 2.7, w
+
+
+# ---------------------------------------------------------------------------------
+# prescribed boundary states (reading R19: the double Mach reflection of Sec. 5.6)
+# ---------------------------------------------------------------------------------
+def _cons(rho, vx, vy, pr):
+    return (rho, rho * vx, rho * vy, pr / (G - 1) + 0.5 * rho * (vx * vx + vy * vy))
+
+
+_ST = (_cons(1.1, 0.3, -0.2, 0.9), _cons(1.3, -0.1, 0.25, 1.1))
+
+
+def _state_sides(nx, ny, p, stab, t, speeds=(0.0, 0.7, -0.4, 1.3)):
+    """Every side prescribed, splits inside the sides, a wall on two of them, moving."""
+    box = (0.0, nx / 8.0, 0.0, ny / 8.0)
+    return _problem2(nx, ny, p, stab, ("state",) * 4, box=box, t=t, bstate=_ST,
+                     bsplit=(0.17, 0.23, 0.31, 0.05), bspeed=speeds, bbelow=(0, 2, 1, 0), babove=(1, 0, 2, 1))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "lo", "weno"])
+def test_2d_prescribed_states_match_brute_force(p, stab):
+    """Sides of kind "state" (R19): at each face point the ghost is one of two prescribed
+    states or a wall, chosen by the point's coordinate along the side against
+    split + speed t; the oracle against the NumPy brute force, at a time where the splits
+    have moved across face points."""
+    P = _state_sides(5, 4, p, stab, t=0.05)
+    U = _state2(P, 11 + p)
+    a, b = O.residual(P, U), B.euler_residual(P, U)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_2d_prescribed_states_free_stream_and_time(p):
+    """A constant state equal to the prescribed one on every side is steady; a residual at
+    time t equals the one at t = 0 with the splits moved by speed x t; one SSP-RK3 step
+    evaluates its stages at t, t + dt and t + dt / 2."""
+    K = (p + 1) ** 2
+    P = _problem2(5, 4, p, "weno", ("state",) * 4, box=(0.0, 5 / 8.0, 0.0, 0.5), bstate=(_ST[0], _ST[0]),
+                  bsplit=(0.1, 0.2, 0.3, 0.4), bspeed=(1.0, -1.0, 2.0, 0.5), bbelow=(0, 1, 0, 1), babove=(1, 0, 1, 0), t=0.3)
+    U = np.zeros((P.K, P.E))
+    for c in range(4):
+        U[c * K] = _ST[0][c]
+    assert np.abs(O.residual(P, U)).max() < 1e-12
+    P = _state_sides(5, 4, p, "weno", t=0.07)
+    U = _state2(P, 21 + p)
+    moved = dataclasses.replace(P, t=0.0, bspeed=(0.0,) * 4,
+                                bsplit=tuple(s + v * 0.07 for s, v in zip(P.bsplit, P.bspeed)))
+    assert np.array_equal(O.residual(P, U), O.residual(moved, U))
+    dt = 1e-3
+    at = lambda t: dataclasses.replace(P, t=t)
+    U1 = U + dt * O.residual(at(0.07), U)
+    U2 = 0.75 * U + 0.25 * U1 + 0.25 * dt * O.residual(at(0.07 + dt), U1)
+    U3 = U / 3.0 + 2.0 / 3.0 * U2 + 2.0 / 3.0 * dt * O.residual(at(0.07 + 0.5 * dt), U2)
+    assert np.abs(O.rk3(P, U, dt, 1) - U3).max() < 1e-14 * np.abs(U3).max()
+    assert not np.array_equal(O.rk3(P, U, dt, 1), O.rk3(dataclasses.replace(P, bspeed=(0.0,) * 4), U, dt, 1))
