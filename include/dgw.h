@@ -56,8 +56,13 @@ typedef enum {
     DGW_BC_INFLOW_ZERO = 1, /* ghost U+ = 0 where F'(U-).n < 0, U+ = U- elsewhere
                                (scalar laws only) */
     DGW_BC_OUTFLOW = 2,     /* ghost U+ = U- */
-    DGW_BC_REFLECT = 3      /* Euler system only: reflecting wall, ghost state with the
+    DGW_BC_REFLECT = 3,     /* Euler system only: reflecting wall, ghost state with the
                                normal momentum mirrored, (rho, m - 2 (m.n) n, rho E) */
+    DGW_BC_STATE = 4        /* 2D Euler system only: prescribed ghost states (the double Mach
+                               reflection of Sec. 5.6): at each face point the ghost is
+                               dgw_flux.bstate[0] or [1] or a reflecting wall, by whether the
+                               point's coordinate along the side (y on the x-sides, x on the
+                               y-sides) lies below bsplit + bspeed t (see dgw_flux) */
 } dgw_bc;
 
 /* Cartesian mesh of [x0,x1] (1D) or [x0,x1]x[y0,y1] (2D) with nx (x ny) equal cells.
@@ -96,6 +101,16 @@ typedef struct {
                                same points, the element's own values on its faces) */
     double gas_gamma;       /* Euler system: ratio of heat capacities (> 1; the paper and
                                dgw_defaults use 1.4); ignored by the scalar fluxes */
+    /* DGW_BC_STATE sides: two prescribed conservative states (rho, rho vx, rho vy, rho E);
+     * per side (-x, +x, -y, +y) the position along the side where the ghost changes at
+     * t = 0, its speed, and the ghost below / from it: 0 or 1 for bstate[0] or bstate[1],
+     * 2 for a reflecting wall.  t is the context's time (dgw_set_time); each stage of a
+     * step sees its stage time (SSP-RK3: t, t + dt, t + dt / 2). */
+    double bstate[2][4];
+    double bsplit[4];
+    double bspeed[4];
+    int bbelow[4];
+    int babove[4];
 } dgw_flux;
 
 typedef enum { DGW_STAB_DG = 0, DGW_STAB_LO = 1, DGW_STAB_WENO = 2, DGW_STAB_ZHAO = 3 } dgw_stab;
@@ -197,6 +212,14 @@ dgw_status dgw_rk_step_host(dgw_ctx* ctx, const void* U_in, void* U_out, double 
  * double, by a fixed-order tree (bitwise reproducible).  Blocks until the result is on
  * the host. */
 dgw_status dgw_mass(dgw_ctx* ctx, const void* U, double* host_mass, void* stream);
+
+/* The context's time t, which DGW_BC_STATE sides read (the paper's double Mach
+ * reflection moves its top boundary's switch with time): dgw_set_time sets it (ordered on
+ * the stream), each step of dgw_rk_step / dgw_rk_step_host advances it by dt on the
+ * device, and dgw_residual / dgw_sensor evaluate at it.  dgw_get_time synchronizes the
+ * stream and returns it.  A new context starts at t = 0. */
+dgw_status dgw_set_time(dgw_ctx* ctx, double t, void* stream);
+dgw_status dgw_get_time(dgw_ctx* ctx, double* t, void* stream);
 
 /* Reads and clears the context's device-side error flags.  Synchronizes the stream.
  * DGW_ETIMEOUT: a stage kernel's bounded wait for its TMA tile copy gave up, so that

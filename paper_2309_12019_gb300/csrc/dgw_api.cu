@@ -67,6 +67,8 @@ struct dgw_ctx {
     double* partial = nullptr;   // mass partial sums
     double* mass_dev = nullptr;
     unsigned* flag = nullptr;
+    double* t_dev = nullptr;     // the context's time (DGW_BC_STATE sides), advanced per step
+    bool state_sides = false;
     int wait_limit = 0;          // bounded TMA waits: 0 the kernels' default limit (dgw_debug)
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<std::pair<const void*, int>, CUtensorMap> tmaps;   // TMA descriptors (2D): (array, box kind)
@@ -136,7 +138,7 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
     if (m.nx < 1 || (m.dim == 2 && m.ny < 1)) return fail(DGW_EINVAL, "nx, ny must be >= 1");
     if (!(m.x1 > m.x0) || (m.dim == 2 && !(m.y1 > m.y0))) return fail(DGW_EINVAL, "empty box");
     for (int f = 0; f < 2 * m.dim; ++f)
-        if (m.bc[f] < DGW_BC_PERIODIC || m.bc[f] > DGW_BC_REFLECT) return fail(DGW_EINVAL, "bad bc[%d]", f);
+        if (m.bc[f] < DGW_BC_PERIODIC || m.bc[f] > DGW_BC_STATE) return fail(DGW_EINVAL, "bad bc[%d]", f);
     for (int a = 0; a < m.dim; ++a)
         if ((m.bc[2 * a] == DGW_BC_PERIODIC) != (m.bc[2 * a + 1] == DGW_BC_PERIODIC))
             return fail(DGW_EINVAL, "periodic sides must come in pairs");
@@ -149,10 +151,21 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
     if (flux->kind < DGW_FLUX_ADVECT || flux->kind > DGW_FLUX_EULER) return fail(DGW_EINVAL, "bad flux kind");
     if (!(flux->lambda_nu >= 0.0)) return fail(DGW_EINVAL, "lambda_nu must be >= 0");
     const bool euler = flux->kind == DGW_FLUX_EULER;
+    bool state_sides = false;
     for (int f = 0; f < 2 * m.dim; ++f) {
         if (m.bc[f] == DGW_BC_REFLECT && !euler) return fail(DGW_EINVAL, "bc[%d]: reflecting walls are for the Euler system", f);
         if (m.bc[f] == DGW_BC_INFLOW_ZERO && euler) return fail(DGW_EINVAL, "bc[%d]: inflow_zero is for scalar laws", f);
+        if (m.bc[f] == DGW_BC_STATE) {
+            if (!euler || m.dim != 2) return fail(DGW_EUNSUPPORTED, "bc[%d]: prescribed states are built for the 2D Euler system", f);
+            if (flux->bbelow[f] < 0 || flux->bbelow[f] > 2 || flux->babove[f] < 0 || flux->babove[f] > 2)
+                return fail(DGW_EINVAL, "bc[%d]: bbelow / babove must be 0, 1 (a state) or 2 (a wall)", f);
+            if (!std::isfinite(flux->bsplit[f]) || !std::isfinite(flux->bspeed[f]))
+                return fail(DGW_EINVAL, "bc[%d]: bsplit and bspeed must be finite", f);
+            state_sides = true;
+        }
     }
+    if (state_sides && params->rk_order == 4)
+        return fail(DGW_EUNSUPPORTED, "prescribed states with rk_order 4: the stage times are built for orders 2 and 3");
     if (euler && !(flux->gas_gamma > 1.0 && std::isfinite(flux->gas_gamma)))
         return fail(DGW_EINVAL, "gas_gamma must be a finite number > 1");
     dgw_status st = check_params(params, m.dim);
@@ -180,7 +193,8 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
     const size_t bytes = (size_t)c->K * E * c->eb;
     if (ce == cudaSuccess) ce = cudaMalloc(&c->S1, bytes);
     if (ce == cudaSuccess) ce = cudaMalloc(&c->S2, bytes);
-    if (ce == cudaSuccess) ce = cudaMalloc(&c->partial, sizeof(double) * (kMassBlocks + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc(&c->partial, sizeof(double) * (kMassBlocks + 2));
+    if (ce == cudaSuccess) ce = cudaMemset(c->partial + kMassBlocks + 1, 0, sizeof(double));   // t = 0
     if (ce == cudaSuccess) ce = cudaMalloc(&c->flag, sizeof(unsigned));
     if (ce == cudaSuccess) ce = cudaMemset(c->flag, 0, sizeof(unsigned));
     if (ce != cudaSuccess) {
@@ -190,6 +204,8 @@ extern "C" dgw_status dgw_create(const dgw_mesh* mesh, int p, const dgw_flux* fl
         return s;
     }
     c->mass_dev = c->partial + kMassBlocks;
+    c->t_dev = c->partial + kMassBlocks + 1;
+    c->state_sides = state_sides;
     *out = c;
     return DGW_OK;
 }
@@ -243,6 +259,8 @@ extern "C" dgw_status dgw_set_params(dgw_ctx* c, const dgw_params* s)
     dgw_status st = check_params(s, c->mesh.dim);
     if (st != DGW_OK) return st;
     if (s->prec != c->params.prec) return fail(DGW_EINVAL, "precision is fixed at dgw_create");
+    if (c->state_sides && s->rk_order == 4)
+        return fail(DGW_EUNSUPPORTED, "prescribed states with rk_order 4: the stage times are built for orders 2 and 3");
     c->params = *s;
     drop_graphs(c);
     return DGW_OK;
@@ -340,8 +358,21 @@ static StageArgs base_args(const dgw_ctx* c)
     a.gas_gamma = c->flux.gas_gamma;
     a.flag = c->flag;
     a.wait_limit = c->wait_limit;
+    a.t_dev = c->t_dev;
+    a.t_off = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 4; ++k) a.bstate[i][k] = c->flux.bstate[i][k];
+    for (int f = 0; f < 4; ++f) {
+        a.bsplit[f] = c->flux.bsplit[f];
+        a.bspeed[f] = c->flux.bspeed[f];
+        a.bbelow[f] = c->flux.bbelow[f];
+        a.babove[f] = c->flux.babove[f];
+    }
     return a;
 }
+
+// t += dt on the device, after each step of a context with prescribed-state sides
+__global__ void advance_time_kernel(double* t, double dt) { *t += dt; }
 
 static cudaError_t launch(const dgw_ctx* c, const StageArgs& a0, int mode, cudaStream_t s)
 {
@@ -419,13 +450,18 @@ static cudaError_t enqueue_steps_rk24(const dgw_ctx* c, void* U, double dt, int 
     for (int n = 0; n < nsteps; ++n) {
         if (c->params.rk_order == 2) {
             a.Uk = U; a.Un = nullptr; a.Uout = c->S1;
-            a.cn = 0.0; a.ck = 1.0; a.cl = dt;
+            a.cn = 0.0; a.ck = 1.0; a.cl = dt; a.t_off = 0.0;
             cudaError_t e = launch(c, a, 0, s);
             if (e != cudaSuccess) return e;
             a.Uk = c->S1; a.Un = U; a.Uout = U;
-            a.cn = 0.5; a.ck = 0.5; a.cl = 0.5 * dt;
+            a.cn = 0.5; a.ck = 0.5; a.cl = 0.5 * dt; a.t_off = dt;
             e = launch(c, a, 0, s);
             if (e != cudaSuccess) return e;
+            if (c->state_sides) {
+                advance_time_kernel<<<1, 1, 0, s>>>(c->t_dev, dt);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
             continue;
         }
         void* q[2] = {c->S1, c->S2};
@@ -463,17 +499,22 @@ static cudaError_t enqueue_steps(const dgw_ctx* c, void* U, double dt, int nstep
     StageArgs a = base_args(c);
     for (int n = 0; n < nsteps; ++n) {
         a.Uk = U; a.Un = nullptr; a.Uout = c->S1;
-        a.cn = 0.0; a.ck = 1.0; a.cl = dt;
+        a.cn = 0.0; a.ck = 1.0; a.cl = dt; a.t_off = 0.0;
         cudaError_t e = launch(c, a, 0, s);
         if (e != cudaSuccess) return e;
         a.Uk = c->S1; a.Un = U; a.Uout = c->S2;
-        a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt;
+        a.cn = 0.75; a.ck = 0.25; a.cl = 0.25 * dt; a.t_off = dt;
         e = launch(c, a, 0, s);
         if (e != cudaSuccess) return e;
         a.Uk = c->S2; a.Un = U; a.Uout = U;
-        a.cn = 1.0 / 3.0; a.ck = 2.0 / 3.0; a.cl = 2.0 / 3.0 * dt;
+        a.cn = 1.0 / 3.0; a.ck = 2.0 / 3.0; a.cl = 2.0 / 3.0 * dt; a.t_off = 0.5 * dt;
         e = launch(c, a, 0, s);
         if (e != cudaSuccess) return e;
+        if (c->state_sides) {
+            advance_time_kernel<<<1, 1, 0, s>>>(c->t_dev, dt);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -1387,6 +1428,7 @@ extern "C" dgw_status dgw_rk_step_stages(dgw_ctx* c, const void* U, double dt, v
         return fail(DGW_EINVAL, "the stage states must not overlap U, U_next or each other");
     if (!std::isfinite(dt)) return fail(DGW_EINVAL, "dt must be finite");
     if (c->params.rk_order != 3) return fail(DGW_EUNSUPPORTED, "stage states of the SSP-RK3 step (rk_order 3)");
+    if (c->state_sides) return fail(DGW_EUNSUPPORTED, "dgw_rk_step_stages keeps no time (prescribed-state sides)");
     cudaStream_t s = (cudaStream_t)stream;
     StageArgs a = base_args(c);
     a.Uk = U; a.Un = nullptr; a.Uout = U1;
@@ -1482,6 +1524,30 @@ extern "C" dgw_status dgw_sync_status(dgw_ctx* c, void* stream)
     DGW_CUDA(cudaStreamSynchronize(s));
     if (v & 2u) return fail(DGW_ETIMEOUT, "a stage kernel's bounded wait for its TMA copy gave up (its tile was skipped)");
     if (v & 1u) return fail(DGW_ENONFINITE, "a stage produced a non-finite value");
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_set_time(dgw_ctx* c, double t, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!std::isfinite(t)) return fail(DGW_EINVAL, "t must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    static thread_local double host_t;       // pageable source: the copy reads it before returning
+    host_t = t;
+    DGW_CUDA(cudaMemcpyAsync(c->t_dev, &host_t, sizeof(double), cudaMemcpyHostToDevice, s));
+    DGW_CUDA(cudaStreamSynchronize(s));
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_get_time(dgw_ctx* c, double* t, void* stream)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (!t) return fail(DGW_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    DGW_CUDA(cudaMemcpyAsync(t, c->t_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DGW_CUDA(cudaStreamSynchronize(s));
     return DGW_OK;
 }
 

@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(ENT, (P == 3 || !kF32) ? 2 : 3) euler2d_kernel
 
     // ---- 2. faces: x-faces f = 0..EX of each row, y-faces r = 0..EY of each column ----
     constexpr int NFX = (EX + 1) * EY, NFY = EX * (EY + 1);
+    // prescribed-state sides read the stage's time
+    const bool state_sides = A.bc[0] == BC_STATE || A.bc[1] == BC_STATE || A.bc[2] == BC_STATE || A.bc[3] == BC_STATE;
+    const Real tnow = state_sides ? (Real)(*A.t_dev + A.t_off) : Real(0);
     for (int item = tid; item < NFX + NFY; item += ENT) {
         const bool xf = item < NFX;
         int rm, cm, rp, cp, fr, fc;       // staged positions of the minus / plus cell; face index
@@ -319,18 +322,26 @@ __global__ void __launch_bounds__(ENT, (P == 3 || !kF32) ? 2 : 3) euler2d_kernel
         for (int q = 0; q < NQ; ++q) {
             Real um[4] = {um2[0][q].x, um2[0][q].y, um2[1][q].x, um2[1][q].y};
             Real up[4] = {up2[0][q].x, up2[0][q].y, up2[1][q].x, up2[1][q].y};
-            if (!has_m) {          // ghost for the plus cell (outward normal -e_axis)
-                const bool refl = A.bc[xf ? 0 : 2] == BC_REFLECT;
+            if (!has_m || !has_p) {
+                // ghost: the inner state, mirrored at a wall; on a prescribed-state side one
+                // of two states or a wall, by the point's coordinate along the side against
+                // the split bsplit + bspeed t
+                const int side = (xf ? 0 : 2) + (has_m ? 1 : 0);
+                bool refl = A.bc[side] == BC_REFLECT;
+                int ch = -1;
+                if (A.bc[side] == BC_STATE) {
+                    const Real along = xf ? A.y0 + (Real(ty0 + fr) + Real(0.5)) * A.h + A.hh * T.g[q]
+                                          : A.x0 + (Real(tx0 + fc) + Real(0.5)) * A.h + A.hh * T.g[q];
+                    ch = along < A.bsplit[side] + A.bspeed[side] * tnow ? A.bbelow[side] : A.babove[side];
+                    refl = ch == 2;
+                }
+                Real* gh = has_m ? up : um;                 // the ghost side
+                const Real* in_ = has_m ? um : up;          // the inner side
 #pragma unroll
-                for (int comp = 0; comp < 4; ++comp) um[comp] = up[comp];
-                if (refl && axis == 0) um[1] = -up[1];     // constant indices keep um in registers
-                if (refl && axis == 1) um[2] = -up[2];
-            } else if (!has_p) {   // ghost for the minus cell (outward normal +e_axis)
-                const bool refl = A.bc[xf ? 1 : 3] == BC_REFLECT;
-#pragma unroll
-                for (int comp = 0; comp < 4; ++comp) up[comp] = um[comp];
-                if (refl && axis == 0) up[1] = -um[1];
-                if (refl && axis == 1) up[2] = -um[2];
+                for (int comp = 0; comp < 4; ++comp)
+                    gh[comp] = (ch == 0 || ch == 1) ? A.bstate[ch][comp] : in_[comp];
+                if (refl && axis == 0) gh[1] = -in_[1];
+                if (refl && axis == 1) gh[2] = -in_[2];
             }
             const Euler2State sl = euler2_prim(A, um), sr = euler2_prim(A, up);
             Real Fl[4], Fr[4];

@@ -27,7 +27,7 @@ constexpr int stage_lanes(bool f64) { return f64 ? 1 : 2; }
 constexpr int stage_thread_rows(bool f64) { return f64 ? kTileY2 : 2 * kTileY2; }
 constexpr int stage_rows(bool f64) { return stage_thread_rows(f64) * stage_lanes(f64); }
 
-enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2, BC_REFLECT = 3 };
+enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2, BC_REFLECT = 3, BC_STATE = 4 };
 enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3, FLUX_EULER = 4 };
 enum : int { STAB_DG = 0, STAB_LO = 1, STAB_WENO = 2, STAB_ZHAO = 3 };
 
@@ -74,6 +74,12 @@ struct StageArgs {
     int tile_rows;         // 2D: tile rows of the launch (0: through the last row of the mesh)
     int wait_limit;        // polls of a bounded TMA wait: 0 the default limit, < 0 none (the
                            // wait gives up at once; diagnostic)
+    // prescribed-state sides (2D Euler, DGW_BC_STATE): the stage's time is *t_dev + t_off
+    const double* t_dev;
+    double t_off;
+    double bstate[2][4];
+    double bsplit[4], bspeed[4];
+    int bbelow[4], babove[4];
 };
 
 // ------------------------------------------------------------------------------------

@@ -137,6 +137,12 @@ struct alignas(64) KParams {
     int theta_one;       // theta == 1
     Real gam, gm1;       // Euler system: gamma and gamma - 1
     Real cn, ck, cl;
+    // prescribed-state sides (2D Euler): the stage's time is *t_dev + t_off
+    const double* t_dev;
+    double t_off;
+    Real bstate[2][4];
+    Real bsplit[4], bspeed[4];
+    int bbelow[4], babove[4];
 };
 
 // ------------------------------------------------------------------------------------
@@ -1163,6 +1169,16 @@ static KParams make_params(const StageArgs& s)
     a.gam = (Real)s.gas_gamma;
     a.gm1 = (Real)(s.gas_gamma - 1.0);
     a.cn = (Real)s.cn; a.ck = (Real)s.ck; a.cl = (Real)s.cl;
+    a.t_dev = s.t_dev;
+    a.t_off = s.t_off;
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 4; ++k) a.bstate[i][k] = (Real)s.bstate[i][k];
+    for (int f = 0; f < 4; ++f) {
+        a.bsplit[f] = (Real)s.bsplit[f];
+        a.bspeed[f] = (Real)s.bspeed[f];
+        a.bbelow[f] = s.bbelow[f];
+        a.babove[f] = s.babove[f];
+    }
     return a;
 }
 

@@ -17,7 +17,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3}
+BC = {"periodic": 0, "inflow_zero": 1, "outflow": 2, "reflect": 3, "state": 4}
 FLUX = {"advect": 0, "rotation": 1, "burgers": 2, "kpp": 3, "euler": 4}
 STAB = {"dg": 0, "lo": 1, "weno": 2, "zhao": 3}
 PREC = {"fp64": 0, "fp32": 1}
@@ -47,7 +47,9 @@ class Mesh(ctypes.Structure):
 
 class Flux(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double * 2), ("center", ctypes.c_double * 2),
-                ("omega", ctypes.c_double), ("lambda_nu", ctypes.c_double), ("gas_gamma", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("lambda_nu", ctypes.c_double), ("gas_gamma", ctypes.c_double),
+                ("bstate", (ctypes.c_double * 4) * 2), ("bsplit", ctypes.c_double * 4),
+                ("bspeed", ctypes.c_double * 4), ("bbelow", ctypes.c_int * 4), ("babove", ctypes.c_int * 4)]
 
 
 class Params(ctypes.Structure):
@@ -59,7 +61,7 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_debug", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_rk_step_stages", "dgw_adjoint_step_stages", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
+           "dgw_sync_status", "dgw_debug", "dgw_set_time", "dgw_get_time", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_rk_step_stages", "dgw_adjoint_step_stages", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
            "dgw_batch_schedule", "dgw_batch_set_schedule", "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos", "dgw_selftest_tc_volume",
            "dgw_last_error", "dgw_version")
@@ -90,6 +92,8 @@ def load(build: bool = True):
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
         L.dgw_debug.argtypes = [vp, ctypes.c_int]
+        L.dgw_set_time.argtypes = [vp, ctypes.c_double, vp]
+        L.dgw_get_time.argtypes = [vp, dp, vp]
         L.dgw_residual_vjp.argtypes = [vp, vp, vp, vp, vp]
         L.dgw_adjoint_step.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp]
         L.dgw_misfit.argtypes = [vp, vp, vp, dp, vp, vp]
@@ -162,6 +166,13 @@ class Problem:
     theta: float = 1.0
     rk_order: int = 3
     gas_gamma: float = 1.4
+    # bc "state" sides (2D Euler): see dgw_flux in include/dgw.h; t is the start time
+    t: float = 0.0
+    bstate: tuple = ((0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0))
+    bsplit: tuple = (0.0, 0.0, 0.0, 0.0)
+    bspeed: tuple = (0.0, 0.0, 0.0, 0.0)
+    bbelow: tuple = (0, 0, 0, 0)
+    babove: tuple = (0, 0, 0, 0)
 
     def __post_init__(self):
         if self.b is None:
@@ -192,6 +203,12 @@ class Problem:
         f.center[0], f.center[1] = self.center
         f.omega, f.lambda_nu = self.omega, self.lambda_nu
         f.gas_gamma = self.gas_gamma
+        for i in range(2):
+            for c in range(4):
+                f.bstate[i][c] = self.bstate[i][c]
+        for k in range(4):
+            f.bsplit[k], f.bspeed[k] = self.bsplit[k], self.bspeed[k]
+            f.bbelow[k], f.babove[k] = self.bbelow[k], self.babove[k]
         s = Params()
         s.stab, s.q, s.b, s.w_nbr = STAB[self.stab], self.q, self.b, self.w_nbr
         s.eps_w, s.eps_s, s.prec, s.theta = self.eps_w, self.eps_s, PREC[self.prec], self.theta
@@ -212,6 +229,8 @@ class Context:
         E, K, eb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
         _check(L.dgw_sizes(h, ctypes.byref(E), ctypes.byref(K), ctypes.byref(eb)))
         self.E, self.K, self.elem_bytes = E.value, K.value, eb.value
+        if problem.t != 0.0:
+            self.set_time(problem.t, stream=0)
 
     @property
     def dtype(self):
@@ -274,6 +293,15 @@ class Context:
 
     def sync_status(self, stream=None):
         _check(load().dgw_sync_status(self._h, _stream(stream)))
+
+    def set_time(self, t: float, stream=None):
+        """The context's time, read by "state" sides (dgw_set_time)."""
+        _check(load().dgw_set_time(self._h, float(t), _stream(stream)))
+
+    def get_time(self, stream=None) -> float:
+        t = ctypes.c_double()
+        _check(load().dgw_get_time(self._h, ctypes.byref(t), _stream(stream)))
+        return t.value
 
     def debug(self, wait_limit: int):
         """Poll limit of the stage kernels' bounded TMA waits (dgw_debug)."""

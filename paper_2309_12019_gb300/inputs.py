@@ -340,7 +340,29 @@ EULER_2D = {
     "rarefaction_2": dict(box=(0.0, 1.0, 0.0, 1.0), bc=("outflow",) * 4, t_end=0.25, nx=256, ny=256, p=2, lam=3.0,
                           states=((1.0, 0.0312, 0.0312, 0.5), (0.927, -0.0312, 0.0312, 0.45),
                                   (1.0, -0.0312, -0.0312, 0.5), (0.927, 0.0312, -0.0312, 0.45))),
+    # double Mach reflection: the Mach 10 shock at 60 degrees to the wall y = 0; post-shock
+    # (L) left of x = 1/6 + y / sqrt 3, pre-shock (R) right of it; sides prescribed (reading
+    # R19): x = 0 post-shock; x = 4 outflow (supersonic); y = 0 post-shock for x < 1/6, wall
+    # beyond; y = 1 post-shock for x < 1/6 + (1 + 20 t) / sqrt 3, pre-shock beyond.  The
+    # paper's finest mesh of its figure, 384 x 96, p = 2, t = 0.2; |v| + c stays below 20.
+    "double_mach": dict(box=(0.0, 4.0, 0.0, 1.0), bc=("state", "outflow", "state", "state"), t_end=0.2,
+                        nx=384, ny=96, p=2, lam=20.0,
+                        states=((8.0, 8.25 * math.cos(math.pi / 6), -8.25 * math.sin(math.pi / 6), 116.5),
+                                (1.4, 0.0, 0.0, 1.0))),
 }
+
+
+def double_mach_boundary(gamma: float = 1.4):
+    """dgw / oracle Problem fields of the double Mach reflection's prescribed sides:
+    bstate (post-shock, pre-shock; conservative), and per side (-x, +x, -y, +y) the split
+    along the side at t = 0, its speed and the ghost below / from it (0 post-shock,
+    1 pre-shock, 2 wall)."""
+    st = []
+    for rho, vx, vy, pr in EULER_2D["double_mach"]["states"]:
+        st.append((rho, rho * vx, rho * vy, pr / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy)))
+    r3 = math.sqrt(3.0)
+    return dict(bstate=tuple(st), bsplit=(10.0, 0.0, 1.0 / 6.0, 1.0 / 6.0 + 1.0 / r3),
+                bspeed=(0.0, 0.0, 0.0, 20.0 / r3), bbelow=(0, 0, 0, 0), babove=(1, 0, 2, 1))
 
 
 def euler2d_primitive(name: str, x, y):
@@ -356,6 +378,10 @@ def euler2d_primitive(name: str, x, y):
         return np.stack([rho, vx, vy, pr]), inner.astype(np.int64)
     if name.startswith("rarefaction_"):
         region = np.where(x > 0.5, np.where(y > 0.5, 0, 3), np.where(y > 0.5, 1, 2))
+        st = np.asarray(EULER_2D[name]["states"])[region]
+        return np.moveaxis(st, -1, 0), region
+    if name == "double_mach":
+        region = np.where(x < 1.0 / 6.0 + y / math.sqrt(3.0), 0, 1)
         st = np.asarray(EULER_2D[name]["states"])[region]
         return np.moveaxis(st, -1, 0), region
     if name == "triple_point":

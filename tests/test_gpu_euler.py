@@ -364,6 +364,8 @@ def test_2d_residual_fp32(oracle_mod, p, stab):
 def _problem2d(name, nx, ny, p):
     d = I.EULER_2D[name]
     s = dict(dim=2, nx=nx, ny=ny, p=p, box=d["box"], bc=d["bc"], flux="euler", stab="weno")
+    if name == "double_mach":
+        s.update(I.double_mach_boundary())
     dt = I.euler_cfl(p, 2) * (d["box"][1] - d["box"][0]) / nx / d["lam"]
     return s, dt, I.euler2d_samples(name, nx, ny, 8)
 
@@ -527,3 +529,84 @@ def test_2d_rk_orders_fp64(oracle_mod, rk):
     torch.cuda.synchronize()
     ctx.sync_status()
     assert per_comp_rel2(Ud.cpu().numpy(), ref, 2) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------
+# prescribed boundary states (reading R19; the double Mach reflection of Sec. 5.6)
+# ---------------------------------------------------------------------------------
+def _cons(rho, vx, vy, pr):
+    return (rho, rho * vx, rho * vy, pr / 0.4 + 0.5 * rho * (vx * vx + vy * vy))
+
+
+STATE_SIDES = dict(bstate=(_cons(1.1, 0.3, -0.2, 0.9), _cons(1.3, -0.1, 0.25, 1.1)),
+                   bsplit=(0.171, 0.233, 0.313, 0.051), bspeed=(0.0, 0.7, -0.4, 1.3),
+                   bbelow=(0, 2, 1, 0), babove=(1, 0, 2, 1))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("stab", ["dg", "lo", "weno"])
+def test_2d_prescribed_states_residual_fp64(oracle_mod, p, stab):
+    """Every side prescribed (two states and walls, switching along the sides at moving
+    splits), at a time set on the context: the residual against the oracle at 1e-12."""
+    s = spec2(p, stab=stab, bc=("state",) * 4, **STATE_SIDES)
+    U = state2(p, 37 * 11, seed=700 + p)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s, t=0.05), U)
+    ctx = ctx_for(s)
+    ctx.set_time(0.05)
+    assert per_comp_rel2(residual(ctx, U), ref, p) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_2d_prescribed_states_steps(oracle_mod, prec, bar):
+    """Six SSP-RK3 steps with moving splits from t = 0.02: each stage reads its stage time
+    (t, t + dt, t + dt / 2) on the device; the context's time advances by dt per step, and
+    the cached graph replays stay right as it moves."""
+    s = spec2(2, bc=("state",) * 4, **STATE_SIDES)
+    U = state2(2, 37 * 11, seed=733)
+    if prec == "fp32":
+        U = U.astype(np.float32).astype(np.float64)
+    dt, n = 2e-3, 6
+    ref = oracle_mod.rk3(oracle_mod.Problem(**s, t=0.02), U, dt, n)
+    ctx = ctx_for(s, prec)
+    ctx.set_time(0.02)
+    Ud = dev(U, prec)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        ctx.rk_step(Ud, dt, n)
+    st.synchronize()
+    ctx.sync_status()
+    assert per_comp_rel2(Ud.double().cpu().numpy(), ref, 2) <= bar
+    assert abs(ctx.get_time() - (0.02 + n * dt)) < 1e-15
+
+
+def test_2d_prescribed_states_refusals():
+    """Prescribed states are built for the 2D Euler system with SSP-RK of order 2 or 3."""
+    for s, kw in ((dict(dim=1, nx=8, p=2, box=(0.0, 1.0, 0.0, 1.0), bc=("state", "outflow", "periodic", "periodic"),
+                        flux="euler", stab="weno"), {}),
+                  (H.spec(2, 2, 8, bc="outflow"), {}),
+                  (spec2(2, bc=("state",) * 4, **STATE_SIDES), {"rk_order": 4})):
+        if s.get("flux") != "euler":
+            s = dict(s, bc=("state", "outflow", "outflow", "outflow"))
+        with pytest.raises(dgw.DGWError) as ei:
+            dgw.Context(dgw.Problem(**s, **kw))
+        assert ei.value.status == -4
+
+
+@pytest.mark.parametrize("prec,stab,bar", [("fp64", "lo", 1e-12), ("fp64", "weno", 1e-9), ("fp32", "weno", 2e-5)])
+def test_2d_double_mach_reduced_steps(oracle_mod, prec, stab, bar):
+    """The double Mach reflection on a reduced mesh (48 x 12 cells, p = 2): its
+    prescribed sides (the top one moving with the shock), 20 steps from the oracle's
+    projection against the oracle."""
+    s, dt, f = _problem2d("double_mach", 48, 12, 2)
+    s["stab"] = stab
+    P = oracle_mod.Problem(**s)
+    U0 = oracle_mod.project(P, f, 8)
+    if prec == "fp32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    ref = oracle_mod.rk3(P, U0, dt, 20)
+    ctx = ctx_for(s, prec)
+    Ud = dev(U0, prec)
+    ctx.rk_step(Ud, dt, 20)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert rel_to_state(Ud.double().cpu().numpy(), ref, 2) <= bar
