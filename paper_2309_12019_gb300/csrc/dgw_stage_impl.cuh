@@ -455,13 +455,28 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
     return false;
 }
 
+// Asynchronous copy of one word from global to shared memory (cp.async, cached at all
+// levels; 4-byte words may start anywhere a float does, which the bulk copies do not
+// allow).  The batch kernel's copies follow the acquire of its dependency counter.
+__device__ __forceinline__ void cp_async_word(Real* dst, const Real* src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(Real) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Shared memory of one tile of TX x (TYT * L) cells (carved from dynamic shared memory).
 template <int P, int L, int TYT>
 struct TileSmem {
     static constexpr int N1 = P + 1, K = Tab<P>::K, TN = DIM == 1 ? 1 : N1;
     static constexpr int TYC = TYT * L;                   // cell rows
     static constexpr int HYC = DIM == 1 ? 1 : TYC + 2;    // staged rows
-    alignas(128) Real su[K][HYC][HX];
+    using Stage = Real[K][HYC][HX];
+    alignas(128) Stage su;
     // cell index innermost: a warp touches consecutive words (no bank conflicts).
     // The face phase overwrites the minus-side trace of every face with the face's
     // lifted flux: trx[r][1][t][c] becomes the flux of x-face c of row r (between cells
@@ -474,6 +489,59 @@ struct TileSmem {
     int fail_s;
 };
 
+// Pipelined staging of the batch kernel (cp.async, one commit group per call; the
+// caller waits with cp_async_wait_all and a CTA barrier).  stage_tile_async: the tile's
+// cells and their face halo of Uk into su, as the plain staging of process_tile lays
+// them out (zeros where there is no cell).  stage_un_async: the tile's own cells of Un
+// into su, laid out [K][TYC][TX] (zeros outside the mesh).
+template <int P, int L, int TYT>
+__device__ __forceinline__ void stage_tile_async(const KParams& A, const int tx0, const int ty0,
+                                                 typename TileSmem<P, L, TYT>::Stage& su)
+{
+    constexpr int K = Tab<P>::K, NT = TX * TYT, HYC = TileSmem<P, L, TYT>::HYC;
+    const int64_t E = A.E;
+    for (int idx = threadIdx.x; idx < HYC * HX; idx += NT) {
+        const int r = idx / HX, cc = idx - r * HX;
+        if (cc < OX - 1 || cc > OX + TX) continue;
+        const bool corner = DIM == 2 && (r == 0 || r == HYC - 1) && (cc == OX - 1 || cc == OX + TX);
+        if (corner) continue;
+        const int gx = wrap_x(A, tx0 - OX + cc);
+        const int gy = DIM == 2 ? wrap_y(A, ty0 - OY + r) : 0;
+        if (gx < 0 || gy < 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) su[k][r][cc] = Real(0);
+            continue;
+        }
+        const Real* src = A.Uk + (int64_t)gy * A.nx + gx;
+#pragma unroll
+        for (int k = 0; k < K; ++k) cp_async_word(&su[k][r][cc], src + k * E);
+    }
+    cp_async_commit();
+}
+
+template <int P, int L, int TYT>
+__device__ __forceinline__ void stage_un_async(const KParams& A, const int tx0, const int ty0,
+                                               typename TileSmem<P, L, TYT>::Stage& su)
+{
+    constexpr int K = Tab<P>::K, NT = TX * TYT, TYC = TileSmem<P, L, TYT>::TYC;
+    static_assert(TYC * TX <= TileSmem<P, L, TYT>::HYC * HX, "Un tile exceeds the stage buffer");
+    const int64_t E = A.E;
+    Real* sun = &su[0][0][0];
+    for (int idx = threadIdx.x; idx < TYC * TX; idx += NT) {
+        const int r = idx / TX, c = idx - r * TX;
+        const int gx = tx0 + c, gy = ty0 + r;
+        if (gx >= A.nx || (DIM == 2 && gy >= A.ny)) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sun[(k * TYC + r) * TX + c] = Real(0);
+            continue;
+        }
+        const Real* src = A.Un + (int64_t)(DIM == 2 ? gy : 0) * A.nx + gx;
+#pragma unroll
+        for (int k = 0; k < K; ++k) cp_async_word(&sun[(k * TYC + r) * TX + c], src + k * E);
+    }
+    cp_async_commit();
+}
+
 // One tile of one stage.  Called by all TX x TYT threads of a CTA together (it contains
 // CTA barriers); tx0, ty0: first cell of the tile.  MODE 0: stage / residual;
 // MODE 1: sensor only.  Thread (lx, ly) owns the cells (lx, L ly + l), l < L; with
@@ -482,8 +550,13 @@ struct TileSmem {
 // TMA: the TMA staging paths are compiled in (the batch kernel builds its launch scalars
 // per work item in registers and never stages by TMA; taking the tensor map's address
 // would put those scalars in local memory).
-template <int P, int FLUX, int MODE, int L, int TYT, bool TMA = true>
-__device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P, L, TYT>& S)
+// ASYNC (batch kernel): the caller has staged the tile into *su_async with
+// stage_tile_async and made it visible (wait and barrier); the Un tile is copied into
+// the same buffer once the volume phase is done, and every copy still in flight (the
+// caller's prefetch of its next tile too) is waited for before the face-lifting phase.
+template <int P, int FLUX, int MODE, int L, int TYT, bool TMA = true, bool ASYNC = false>
+__device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P, L, TYT>& S,
+                                             typename TileSmem<P, L, TYT>::Stage* su_async = nullptr)
 {
     static_assert(L == 1 || (kF32 && DIM == 2), "two cells per thread: float, 2D only");
     using V = typename VecOf<L>::type;
@@ -497,7 +570,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     constexpr int NFY = DIM == 2 ? TXL * (TYC + 1) : 0;  // y-face items; lanes: columns c + l TXL
     constexpr int TN = DIM == 1 ? 1 : N1;                // trace / face coefficients
     const Tab<P>& T = tab<P>();
-    auto& su = S.su;
+    auto& su = ASYNC ? *su_async : S.su;
     auto& trx = S.trx;
     auto& trys = S.trys;
     auto& lam_s = S.lam_s;
@@ -511,7 +584,9 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     const bool periodic_y = DIM == 2 && A.bc[2] == BC_PERIODIC;
 
     // ---- 0. stage the tile and its face halo ----
-    if (TMA && DIM == 2 && A.use_tma) {
+    if (ASYNC) {
+        // staged by the caller
+    } else if (TMA && DIM == 2 && A.use_tma) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
         if (tid == 0) {
             fail_s = 0;
@@ -850,6 +925,8 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     // The stage array is no longer read: bring the Un tile into it now, so that its
     // load overlaps the face phase (second phase of the same mbarrier).
     const bool un_tma = TMA && DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
+    const bool un_async = ASYNC && A.has_un;
+    if (un_async) stage_un_async<P, L, TYT>(A, tx0, ty0, su);
     if (un_tma && tid == 0) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
         const uint32_t bytes = (uint32_t)(sizeof(Real) * K * TYC * TX);
@@ -1016,6 +1093,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         // takes more than one item above the even share
         for (int f = (tid + NT - NFX % NT) % NT; f < NFY; f += NT) face_item(std::integral_constant<bool, false>(), f);
     }
+    if (ASYNC) cp_async_wait_all();
     __syncthreads();
     if (!any_in) return;
 
@@ -1101,7 +1179,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 #pragma unroll
             for (int l = 0; l < L; ++l) {
                 const Real* un = A.Un + e[l] + k * E;
-                lane(unk, l) = un_tma ? sun[(k * TYC + cy[l]) * TX + lx]
+                lane(unk, l) = (un_tma || un_async) ? sun[(k * TYC + cy[l]) * TX + lx]
                                       : (in[l] ? (A.cg_loads ? __ldcg(un) : *un) : Real(0));
             }
             out = vfma(A.cn, unk, out);
@@ -1189,6 +1267,12 @@ static KParams make_params(const StageArgs& s)
 // float), else one
 constexpr int kBatchLanes = (kF32 && DIM == 2) ? 2 : 1;
 
+template <int P, int TYB>
+constexpr size_t batch_tile_bytes()
+{
+    return (sizeof(TileSmem<P, kBatchLanes, TYB>) + 127) / 128 * 128;
+}
+
 template <int P, int FLUX, int TYB>
 __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst& I, const int r,
                                             const int tile0, const int ntile, unsigned char* smem)
@@ -1228,11 +1312,30 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
     A.cn = (Real)(r == 0 ? 0.0 : (r == 1 ? 0.75 : 1.0 / 3.0));
     A.ck = (Real)(r == 0 ? 1.0 : (r == 1 ? 0.25 : 2.0 / 3.0));
     A.cl = (Real)(r == 0 ? dt : (r == 1 ? 0.25 * dt : 2.0 / 3.0 * dt));
-    TileSmem<P, kBatchLanes, TYB>& S = *reinterpret_cast<TileSmem<P, kBatchLanes, TYB>*>(smem);
-    for (int t = tile0; t < tile0 + ntile; ++t) {
-        const int tx0 = (t % I.ntx) * TX;
-        const int ty0 = DIM == 2 ? (t / I.ntx) * (TYB * kBatchLanes) : 0;
-        process_tile<P, FLUX, 0, kBatchLanes, TYB, false>(A, tx0, ty0, S);
+    using Smem = TileSmem<P, kBatchLanes, TYB>;
+    Smem& S = *reinterpret_cast<Smem*>(smem);
+    // two stage buffers: the tile's own (S.su or the one after the tile's shared
+    // memory) and the next tile's, filled by cp.async while this one is computed
+    typename Smem::Stage* const buf0 = &S.su;
+    typename Smem::Stage* const buf1 = reinterpret_cast<typename Smem::Stage*>(smem + batch_tile_bytes<P, TYB>());
+    auto origin = [&](int t, int& tx0, int& ty0) {
+        tx0 = (t % I.ntx) * TX;
+        ty0 = DIM == 2 ? (t / I.ntx) * (TYB * kBatchLanes) : 0;
+    };
+    int tx0, ty0;
+    origin(tile0, tx0, ty0);
+    stage_tile_async<P, kBatchLanes, TYB>(A, tx0, ty0, *buf0);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = 0; i < ntile; ++i) {
+        origin(tile0 + i, tx0, ty0);
+        if (i + 1 < ntile) {
+            int nx0, ny0;
+            origin(tile0 + i + 1, nx0, ny0);
+            stage_tile_async<P, kBatchLanes, TYB>(A, nx0, ny0, (i & 1) ? *buf0 : *buf1);
+        }
+        process_tile<P, FLUX, 0, kBatchLanes, TYB, false, true>(A, tx0, ty0, S, (i & 1) ? buf1 : buf0);
+        cp_async_wait_all();      // nothing left in flight when the tile had no face phase wait
         __syncthreads();
     }
 }
@@ -1255,7 +1358,8 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 template <int P, int TYB>
 constexpr size_t batch_smem_bytes()
 {
-    return (sizeof(TileSmem<P, kBatchLanes, TYB>) + 127) / 128 * 128 + 128;   // tile + scheduler words
+    // tile, second stage buffer, scheduler words
+    return batch_tile_bytes<P, TYB>() + (sizeof(typename TileSmem<P, kBatchLanes, TYB>::Stage) + 127) / 128 * 128 + 128;
 }
 
 // resident CTAs per SM the register budget is sized for: two cells per thread (2D float)

@@ -464,6 +464,77 @@ def test_full_size_rotation_256_q2_fp64_sampled(oracle_mod):
     assert np.max(np.abs(g - g_ref)) <= 1e-12
 
 
+def _patch_problem(s, nx, ny, ix, iy):
+    """The cells of the mesh of s around (ix, iy) that its residual reads: the cell and
+    its face neighbours, as a mesh of at most 3 x 3 cells with outflow sides (the
+    stencil of one cell's residual and sensor is the cell and its face neighbours, so
+    the patch's own boundary does not reach the centre).  Returns the patch problem, the
+    mesh indices of its cells and the patch index of (ix, iy)."""
+    x0, x1 = max(ix - 1, 0), min(ix + 1, nx - 1)
+    y0, y1 = max(iy - 1, 0), min(iy + 1, ny - 1)
+    h = (s["box"][1] - s["box"][0]) / nx
+    box = (s["box"][0] + x0 * h, s["box"][0] + (x1 + 1) * h, s["box"][2] + y0 * h, s["box"][2] + (y1 + 1) * h)
+    ps = dict(s, nx=x1 - x0 + 1, ny=y1 - y0 + 1, box=box)
+    cols, rows = np.meshgrid(np.arange(x0, x1 + 1), np.arange(y0, y1 + 1))
+    return ps, (rows * nx + cols).reshape(-1), (iy - y0) * ps["nx"] + (ix - x0)
+
+
+def test_indexing_beyond_2_31_elements(oracle_mod):
+    """Largest size: a Q3 KPP mesh of 16384 x 8448 cells whose FP32 state array holds
+    2.2e9 > 2^31 coefficients (8.9 GB), so the coefficient offsets k E + e of the upper
+    rows pass 2^31 and the TMA boxes run at coordinates up to 8447.  The residual and
+    the sensor of sampled cells (the corners, the last row and column, and cells whose
+    mode-15 offset lies past 2^31) against the oracle on the cells' neighbourhoods."""
+    nx, ny, p = 16384, 8448, 3
+    # unit cells: the KPP flux does not depend on position, and with h = 1 the residual
+    # stays O(1), so the float bar of the smaller meshes applies unchanged
+    s = dict(dim=2, nx=nx, ny=ny, p=p, box=(0.0, float(nx), 0.0, float(ny)), bc=("outflow",) * 4,
+             flux="kpp", lambda_nu=2.0, stab="weno")
+    ctx = gpu(s, "fp32")
+    K, E = ctx.K, ctx.E
+    assert K * E > 2 ** 31
+    U = torch.empty((K, E), dtype=torch.float32, device="cuda")
+    e = torch.arange(E, device="cuda")
+    fx = (e % nx).float()
+    fy = torch.div(e, nx, rounding_mode="floor").float()
+    del e
+    for k in range(K):
+        # a smooth field with a few sharp fronts, cell means around 2, modes decaying
+        a = (0.8 if k == 0 else 0.3 / (k + 1))
+        U[k] = a * torch.sin((0.0011 + 0.0003 * k) * fx + (0.0017 - 0.0001 * k) * fy + 0.7 * k)
+        if k == 0:
+            U[0] += 2.0
+        else:
+            U[k] *= torch.where(torch.sin(0.013 * fx + 0.021 * fy) > 0.95, 4.0, 1.0)
+    del fx, fy
+    L = torch.empty_like(U)
+    ctx.residual(U, L)
+    g = torch.empty(E, dtype=torch.float64, device="cuda")
+    ctx.sensor(U, g)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    rng = np.random.default_rng(31)
+    past = int(np.ceil((2 ** 31 - (K - 1) * E) / nx)) + 1          # first row whose mode-15 offset passes 2^31
+    cells = [(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1), (nx // 2, ny - 1), (nx - 1, ny // 2)]
+    cells += [(int(rng.integers(nx)), int(rng.integers(past, ny))) for _ in range(40)]
+    cells += [(int(rng.integers(nx)), int(rng.integers(ny))) for _ in range(20)]
+    got_L, ref_L, worst_g = [], [], 0.0
+    for ix, iy in cells:
+        ps, idx, c = _patch_problem(s, nx, ny, ix, iy)
+        it = torch.tensor(idx, device="cuda")
+        Up = U[:, it].double().cpu().numpy()
+        Pp = oracle_mod.Problem(**ps)
+        L_ref = oracle_mod.residual(Pp, Up)[:, c]
+        g_ref, r_ref, _ = oracle_mod.sensor(Pp, Up)
+        got_L.append(L[:, iy * nx + ix].double().cpu().numpy())
+        ref_L.append(L_ref)
+        if abs(r_ref[c] - Pp.b) >= H.R_FLOAT_ERR:
+            worst_g = max(worst_g, abs(float(g[iy * nx + ix]) - g_ref[c]))
+    err = H.cell_err(np.stack(got_L, axis=1), np.stack(ref_L, axis=1))
+    assert err <= FP32_CELL_TOL, err
+    assert worst_g <= H.R_FLOAT_ERR, worst_g
+
+
 def test_fast_sincos_error_bound():
     """The float sin/cos of the KPP flux (2 pi Cody-Waite reduction + __sincosf) stays
     within 1e-6 of double-precision sin/cos for |x| <= 64 (KPP states reach ~11)."""
