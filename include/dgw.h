@@ -320,7 +320,9 @@ dgw_status dgw_batch_rk_step(dgw_batch* b, void* U, int nsteps, void* stream);
 dgw_status dgw_batch_autotune(dgw_batch* b, void* U, int steps, int* chosen_chunk, void* stream);
 
 /* Schedule of the group of instances of dimension dim and degree p: the tile height of its
- * kernel (*rows) and the tiles per work item (*chunk).  Either pointer may be NULL. */
+ * kernel (*rows) and the tiles per work item (*chunk).  Either pointer may be NULL.  Until
+ * an autotune or dgw_batch_set_schedule: 1D items of 2 tiles; 2D float tiles of 8 rows and
+ * items of 16 tiles; 2D double tiles of 4 rows and items of 16 tiles. */
 dgw_status dgw_batch_schedule(const dgw_batch* b, int dim, int p, int* rows, int* chunk);
 
 /* Sets that schedule (a tile height that is built, chunk >= 1; DGW_EINVAL otherwise), e.g.

@@ -1021,8 +1021,11 @@ extern "C" dgw_status dgw_batch_create(int n, const dgw_mesh* meshes, const int*
     }
     for (int d = 0; d < 2 && st == DGW_OK; ++d)
         for (int p = 1; p <= kMaxP && st == DGW_OK; ++p) {
-            b->rows[d][p] = d == 0 ? 1 : kTileY2;
-            b->chunk[d][p] = 4;
+            // default schedule (the autotuner's usual pick with pipelined staging): 1D
+            // items of 2 tiles; 2D float tiles of 8 cell rows, items of 16 tiles
+            const bool f64 = b->eb == 8;
+            b->rows[d][p] = d == 0 ? 1 : (f64 ? kTileY2 : 8);
+            b->chunk[d][p] = d == 0 ? 2 : 16;
             if (!batch_group_used(b, d, p)) continue;
             st = batch_layout(b, d, p);
             if (st == DGW_OK) st = batch_build_items(b, d, p);
