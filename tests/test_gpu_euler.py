@@ -574,17 +574,18 @@ def test_2d_prescribed_states_residual_fp64(oracle_mod, p, stab):
     assert per_comp_rel2(residual(ctx, U), ref, p) <= 1e-12
 
 
-@pytest.mark.parametrize("prec,bar", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_2d_prescribed_states_steps(oracle_mod, prec, bar):
-    """Six SSP-RK3 steps with moving splits from t = 0.02: each stage reads its stage time
-    (t, t + dt, t + dt / 2) on the device; the context's time advances by dt per step, and
-    the cached graph replays stay right as it moves."""
-    s = spec2(2, bc=("state",) * 4, **STATE_SIDES)
+@pytest.mark.parametrize("prec,bar,order", [("fp64", 1e-12, 3), ("fp32", 1e-5, 3), ("fp64", 1e-12, 2)])
+def test_2d_prescribed_states_steps(oracle_mod, prec, bar, order):
+    """Six SSP-RK3 (or SSP-RK2) steps with moving splits from t = 0.02: each stage reads
+    its stage time (t, t + dt, t + dt / 2; RK2: t, t + dt) on the device; the context's
+    time advances by dt per step, and the cached graph replays stay right as it moves."""
+    s = spec2(2, bc=("state",) * 4, rk_order=order, **STATE_SIDES)
     U = smooth_state2(2, 37, 11, seed=733)
     if prec == "fp32":
         U = U.astype(np.float32).astype(np.float64)
     dt, n = 2e-3, 6
-    ref = oracle_mod.rk3(oracle_mod.Problem(**s, t=0.02), U, dt, n)
+    so = {k: v for k, v in s.items() if k != "rk_order"}
+    ref = oracle_mod.rk(oracle_mod.Problem(**so, t=0.02), U, dt, n, order=order)
     ctx = ctx_for(s, prec)
     ctx.set_time(0.02)
     Ud = dev(U, prec)

@@ -410,7 +410,7 @@ def test_2d_prescribed_states_match_brute_force(p, stab):
 def test_2d_prescribed_states_free_stream_and_time(p):
     """A constant state equal to the prescribed one on every side is steady; a residual at
     time t equals the one at t = 0 with the splits moved by speed x t; one SSP-RK3 step
-    evaluates its stages at t, t + dt and t + dt / 2."""
+    evaluates its stages at t, t + dt and t + dt / 2, one SSP-RK2 step at t and t + dt."""
     K = (p + 1) ** 2
     P = _problem2(5, 4, p, "weno", ("state",) * 4, box=(0.0, 5 / 8.0, 0.0, 0.5), bstate=(_ST[0], _ST[0]),
                   bsplit=(0.1, 0.2, 0.3, 0.4), bspeed=(1.0, -1.0, 2.0, 0.5), bbelow=(0, 1, 0, 1), babove=(1, 0, 1, 0), t=0.3)
@@ -430,3 +430,7 @@ def test_2d_prescribed_states_free_stream_and_time(p):
     U3 = U / 3.0 + 2.0 / 3.0 * U2 + 2.0 / 3.0 * dt * O.residual(at(0.07 + 0.5 * dt), U2)
     assert np.abs(O.rk3(P, U, dt, 1) - U3).max() < 1e-14 * np.abs(U3).max()
     assert not np.array_equal(O.rk3(P, U, dt, 1), O.rk3(dataclasses.replace(P, bspeed=(0.0,) * 4), U, dt, 1))
+    # SSP-RK2 (Heun): stages at t and t + dt
+    V1 = U + dt * O.residual(at(0.07), U)
+    V2 = 0.5 * U + 0.5 * V1 + 0.5 * dt * O.residual(at(0.07 + dt), V1)
+    assert np.abs(O.rk(P, U, dt, 1, order=2) - V2).max() < 1e-14 * np.abs(V2).max()
