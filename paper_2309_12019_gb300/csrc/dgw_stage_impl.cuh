@@ -326,22 +326,24 @@ __device__ __forceinline__ void project_sym(const Real (&W)[NQ][N1], const V (&f
 // (n.F = sin u, |F'.n| = |cos u|), a y-face sh = pi/2 (n.F = cos u = sin(u + pi/2),
 // |F'.n| = |sin u| = |cos(u + pi/2)|), so that one body serves both orientations.  The
 // wave speed is exact: 1 if [min, max] of the two states holds a multiple of pi (a
-// maximiser of |cos|), else the larger end value.
+// maximiser of |cos|), else the larger end value.  The segment holds a multiple of pi
+// exactly when it is at least pi long or sin changes sign over it (sin vanishes only
+// there, and a shorter segment holds at most one zero); near a zero, where the computed
+// sign of sin may err, both answers are 1 to within the square of the distance.
 template <class V>
 __device__ __forceinline__ V llf_kpp(V uL, V uR)
 {
     V sL, cL, sR, cR;
     sincos_v(uL, sL, cL);
     sincos_v(uR, sR, cR);
+    const V d = vsub(uR, uL), ss = vmul(sL, sR);
     V spd;
 #pragma unroll
-    for (int l = 0; l < Lanes<V>::n; ++l) {
-        const Real a = lane(uL, l), b = lane(uR, l);
-        const Real k = ceil(fmin(a, b) * Real(1.0 / kPi));
-        lane(spd, l) = k * Real(kPi) <= fmax(a, b) ? Real(1) : fmax(fabs(lane(cL, l)), fabs(lane(cR, l)));
-    }
+    for (int l = 0; l < Lanes<V>::n; ++l)
+        lane(spd, l) = (lane(ss, l) <= Real(0) || fabs(lane(d, l)) >= Real(kPi))
+                           ? Real(1) : fmax(fabs(lane(cL, l)), fabs(lane(cR, l)));
     // H = (sin uL' + sin uR') / 2 - s+ (uR' - uL') / 2
-    return vfma(vmul(Real(-0.5), spd), vsub(uR, uL), vmul(Real(0.5), vadd(sL, sR)));
+    return vfma(vmul(Real(-0.5), spd), d, vmul(Real(0.5), vadd(sL, sR)));
 }
 
 // F'(u) along the axis (inflow test of the ghost state).
