@@ -287,8 +287,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 // box kind 0: tile plus halo (kBoxX2 x (rows + 2) x K); 1: tile (kTileX2 x rows x K),
-// rows = stage_rows() of the context's precision.  True and the descriptor in *out if TMA
-// applies.  The descriptor is copied out: the cache evicts all its entries when it grows
+// rows = stage_rows() of the context's precision; kinds 2 and 3: the same with rows =
+// kPRows (the persistent float kernel).  True and the descriptor in *out if TMA applies.  The descriptor is copied out: the cache evicts all its entries when it grows
 // past 64 arrays, so a pointer into it would not outlive the next lookup.
 static bool tensor_map(const dgw_ctx* cc, const void* U, int kind, CUtensorMap* out)
 {
@@ -313,8 +313,9 @@ static bool tensor_map(const dgw_ctx* cc, const void* U, int kind, CUtensorMap* 
     }
     cuuint64_t dims[3] = {nx, ny, (cuuint64_t)c->K};
     cuuint64_t strides[2] = {nx * eb, nx * ny * eb};
-    const int rows = stage_rows(eb == 8);
-    cuuint32_t box[3] = {(cuuint32_t)(kind == 0 ? kBoxX2 : kTileX2), (cuuint32_t)(kind == 0 ? rows + 2 : rows),
+    const int rows = kind >= 2 ? kPRows : stage_rows(eb == 8);
+    const bool halo = kind == 0 || kind == 2;
+    cuuint32_t box[3] = {(cuuint32_t)(halo ? kBoxX2 : kTileX2), (cuuint32_t)(halo ? rows + 2 : rows),
                          (cuuint32_t)c->K};
     cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap m;
@@ -377,10 +378,21 @@ __global__ void advance_time_kernel(double* t, double dt) { *t += dt; }
 static cudaError_t launch(const dgw_ctx* c, const StageArgs& a0, int mode, cudaStream_t s)
 {
     StageArgs a = a0;
-    CUtensorMap m_k, m_n;      // copies: the launch parameters take them by value
+    CUtensorMap m_k, m_n, m_pk, m_pn;      // copies: the launch parameters take them by value
     a.tmap = tensor_map(c, a.Uk, 0, &m_k) ? &m_k : nullptr;
     a.tmap_un = (a.cn != 0.0 && a.Un && tensor_map(c, a.Un, 1, &m_n)) ? &m_n : nullptr;
     const bool f64 = c->params.prec == DGW_FP64;
+    a.tmap_p = a.tmap_un_p = nullptr;
+    // whole-mesh float stage launches run the persistent kernel when its boxes apply
+    // (the Un box too, where the stage reads Un)
+    if (!f64 && c->mesh.dim == 2 && mode == 0 && a.tile_row0 == 0 && a.tile_rows == 0 && a.tmap &&
+        tensor_map(c, a.Uk, 2, &m_pk)) {
+        const bool need_un = a.cn != 0.0 && a.Un;
+        if (!need_un || (a.tmap_un && tensor_map(c, a.Un, 3, &m_pn))) {
+            a.tmap_p = &m_pk;
+            a.tmap_un_p = need_un ? &m_pn : nullptr;
+        }
+    }
     if (c->mesh.dim == 1)
         return f64 ? launch_stage_f64_d1(a, c->p, c->flux.kind, mode, s)
                    : launch_stage_f32_d1(a, c->p, c->flux.kind, mode, s);

@@ -26,6 +26,10 @@ constexpr int kBoxX2 = kTileX2 + 8;
 constexpr int stage_lanes(bool f64) { return f64 ? 1 : 2; }
 constexpr int stage_thread_rows(bool f64) { return f64 ? kTileY2 : 2 * kTileY2; }
 constexpr int stage_rows(bool f64) { return stage_thread_rows(f64) * stage_lanes(f64); }
+// The persistent float stage kernel (whole-mesh launches): one CTA of 512 threads per SM
+// walks tiles of kTileX2 x kPRows cells; its boxes are kBoxX2 x (kPRows + 2) x K (Uk) and
+// kTileX2 x kPRows x K (Un).
+constexpr int kPRows = 32;
 
 enum : int { BC_PERIODIC = 0, BC_INFLOW_ZERO = 1, BC_OUTFLOW = 2, BC_REFLECT = 3, BC_STATE = 4 };
 enum : int { FLUX_ADVECT = 0, FLUX_ROTATION = 1, FLUX_BURGERS = 2, FLUX_KPP = 3, FLUX_EULER = 4 };
@@ -70,6 +74,9 @@ struct StageArgs {
     unsigned* flag;        // bit 0: non-finite output; bit 1 (value 2): a bounded wait gave up
     const CUtensorMap* tmap;   // 2D: TMA descriptor of Uk (box kBoxX2 x (stage_rows + 2) x K), or null
     const CUtensorMap* tmap_un;  // 2D: TMA descriptor of Un (box kTileX2 x stage_rows x K), or null
+    const CUtensorMap* tmap_p;   // 2D float: descriptor of Uk for the persistent kernel (box kBoxX2 x
+                                 // (kPRows + 2) x K), or null: that kernel runs only when given
+    const CUtensorMap* tmap_un_p;  // and of Un (box kTileX2 x kPRows x K), or null
     int tile_row0;         // 2D: first tile row of the launch
     int tile_rows;         // 2D: tile rows of the launch (0: through the last row of the mesh)
     int wait_limit;        // polls of a bounded TMA wait: 0 the default limit, < 0 none (the

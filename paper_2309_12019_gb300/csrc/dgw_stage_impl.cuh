@@ -117,8 +117,11 @@ static cudaError_t upload(const HostTables& h)
 struct KParams {
     CUtensorMap tmap;    // TMA descriptor of Uk (valid when use_tma)
     CUtensorMap tmap_un; // TMA descriptor of Un, tile box (valid when use_tma_un)
+    CUtensorMap tmap_p;  // persistent kernel: Uk box of kPRows + 2 rows, Un box of kPRows rows
+    CUtensorMap tmap_un_p;
     int use_tma;
     int use_tma_un;
+    int use_p_un;        // the persistent kernel stages Un (tmap_un_p valid)
     int cg_loads;        // load Uk / Un through L2 only (data written earlier in the same launch)
     int wait_limit;      // polls of a TMA mbarrier wait before it gives up (kWaitLimit)
     int tile_row0;       // first tile row of a stage launch over a band of rows
@@ -492,6 +495,7 @@ struct TileSmem {
     Real trys[DIM == 2 ? TYC + 2 : 1][2][TN][TX];         // y-traces, row = cell row + 1
     Real lam_s[TYC][TX];
     alignas(8) uint64_t mbar;
+    alignas(8) uint64_t mbar_un;   // persistent kernel: the Un box
     int fail_s;
 };
 
@@ -556,14 +560,22 @@ __device__ __forceinline__ void stage_un_async(const KParams& A, const int tx0, 
 // TMA: the TMA staging paths are compiled in (the batch kernel builds its launch scalars
 // per work item in registers and never stages by TMA; taking the tensor map's address
 // would put those scalars in local memory).
-// ASYNC (batch kernel): the caller has staged the tile into *su_async with
+// PIPE 0: the tile stages itself (TMA box, or plain loads).
+// PIPE 1 (batch kernel): the caller has staged the tile into *su_async with
 // stage_tile_async and made it visible (wait and barrier); the Un tile is copied into
 // the same buffer once the volume phase is done, and every copy still in flight (the
 // caller's prefetch of its next tile too) is waited for before the face-lifting phase.
-template <int P, int FLUX, int MODE, int L, int TYT, bool TMA = true, bool ASYNC = false>
+// PIPE 2 (persistent kernel): the caller has waited for the tile's box in S.su; once the
+// volume phase is done the box of the next tile (origin nxt_x, nxt_y; nxt_x < 0: none) is
+// requested into S.su on S.mbar, and Un, requested by the caller into un_p on S.mbar_un,
+// is waited for (phase parity un_parity) before the Runge-Kutta combination.
+template <int P, int FLUX, int MODE, int L, int TYT, bool TMA = true, int PIPE = 0>
 __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, const int ty0, TileSmem<P, L, TYT>& S,
-                                             typename TileSmem<P, L, TYT>::Stage* su_async = nullptr)
+                                             typename TileSmem<P, L, TYT>::Stage* su_async = nullptr,
+                                             const int nxt_x = -1, const int nxt_y = 0, const Real* un_p = nullptr,
+                                             const uint32_t un_parity = 0)
 {
+    constexpr bool ASYNC = PIPE == 1;
     static_assert(L == 1 || (kF32 && DIM == 2), "two cells per thread: float, 2D only");
     using V = typename VecOf<L>::type;
     constexpr int N1 = P + 1, NQ = P + 2;
@@ -592,36 +604,38 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
     // ---- 0. stage the tile and its face halo ----
     if (ASYNC) {
         // staged by the caller
-    } else if (TMA && DIM == 2 && A.use_tma) {
-        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
-        if (tid == 0) {
-            fail_s = 0;
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t bytes = (uint32_t)(sizeof(Real) * K * HYC * HX);
-            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         :: "r"(bar), "r"(bytes) : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3, %4}], [%5];"
-                :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&A.tmap)), "r"(tx0 - OX), "r"(ty0 - OY),
-                   "r"(0), "r"(bar)
-                : "memory");
-        }
-        if (!mbar_wait(bar, 0, A.wait_limit)) {
-            // gave up: the tile is skipped and the flag reports it, but the copy still
-            // lands in this CTA's shared memory, so wait for it (bounded) before leaving
-            fail_s = 1;
-            mbar_wait(bar, 0);
-        }
-        __syncthreads();
-        if (fail_s) {
-            if (tid == 0) atomicOr(A.flag, 2u);
-            return;
+    } else if (PIPE == 2 || (TMA && DIM == 2 && A.use_tma)) {
+        if constexpr (PIPE != 2) {
+            const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+            if (tid == 0) {
+                fail_s = 0;
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const uint32_t bytes = (uint32_t)(sizeof(Real) * K * HYC * HX);
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(bar), "r"(bytes) : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];"
+                    :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&A.tmap)), "r"(tx0 - OX), "r"(ty0 - OY),
+                       "r"(0), "r"(bar)
+                    : "memory");
+            }
+            if (!mbar_wait(bar, 0, A.wait_limit)) {
+                // gave up: the tile is skipped and the flag reports it, but the copy still
+                // lands in this CTA's shared memory, so wait for it (bounded) before leaving
+                fail_s = 1;
+                mbar_wait(bar, 0);
+            }
+            __syncthreads();
+            if (fail_s) {
+                if (tid == 0) atomicOr(A.flag, 2u);
+                return;
+            }
         }
         // periodic images of halo cells that lie outside the box's wrap-free view
         const bool edge = (periodic_x && (tx0 == 0 || tx0 + TX >= A.nx)) ||
@@ -930,9 +944,24 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 
     // The stage array is no longer read: bring the Un tile into it now, so that its
     // load overlaps the face phase (second phase of the same mbarrier).
-    const bool un_tma = TMA && DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
+    const bool un_tma = PIPE == 0 && TMA && DIM == 2 && A.use_tma && A.use_tma_un && A.has_un;
     const bool un_async = ASYNC && A.has_un;
     if (un_async) stage_un_async<P, L, TYT>(A, tx0, ty0, su);
+    const bool un_pipe = PIPE == 2 && A.has_un;
+    if (PIPE == 2 && tid == 0 && nxt_x >= 0) {
+        // the stage array is dead: request the next tile's box into it
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+        const uint32_t bytes = (uint32_t)(sizeof(Real) * K * HYC * HX);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&su[0][0][0]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];"
+            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&A.tmap_p)), "r"(nxt_x - OX), "r"(nxt_y - OY), "r"(0),
+               "r"(bar)
+            : "memory");
+    }
     if (un_tma && tid == 0) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
         const uint32_t bytes = (uint32_t)(sizeof(Real) * K * TYC * TX);
@@ -1145,10 +1174,15 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         any_gamma = any_gamma || lane(gamma, l) != Real(0);
     }
     V chk = vbc<V>(0);         // becomes NaN if any output is not finite
-    const Real* sun = reinterpret_cast<const Real*>(&su[0][0][0]);   // Un tile [K][TYC][TX]
+    const Real* sun = PIPE == 2 ? un_p : reinterpret_cast<const Real*>(&su[0][0][0]);   // Un tile [K][TYC][TX]
     if (un_tma && !mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1, A.wait_limit)) {
         atomicOr(A.flag, 2u);
         mbar_wait((uint32_t)__cvta_generic_to_shared(&mbar), 1);   // let the copy land first
+        return;
+    }
+    if (un_pipe && !mbar_wait((uint32_t)__cvta_generic_to_shared(&S.mbar_un), un_parity, A.wait_limit)) {
+        atomicOr(A.flag, 2u);
+        fail_s = 1;            // the caller stops after this tile (its copies drained)
         return;
     }
     int64_t e[L];
@@ -1185,7 +1219,7 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 #pragma unroll
             for (int l = 0; l < L; ++l) {
                 const Real* un = A.Un + e[l] + k * E;
-                lane(unk, l) = (un_tma || un_async) ? sun[(k * TYC + cy[l]) * TX + lx]
+                lane(unk, l) = (un_tma || un_async || un_pipe) ? sun[(k * TYC + cy[l]) * TX + lx]
                                       : (in[l] ? (A.cg_loads ? __ldcg(un) : *un) : Real(0));
             }
             out = vfma(A.cn, unk, out);
@@ -1212,6 +1246,103 @@ __global__ void __launch_bounds__(NTS, LS == 2 ? 512 / NTS : (kF32 ? 6 : 3)) sta
     process_tile<P, FLUX, MODE, LS, TYS>(A, blockIdx.x * TX, DIM == 2 ? (blockIdx.y + A.tile_row0) * (TYS * LS) : 0, S);
 }
 
+#if DGW_DIM == 2
+// Persistent float stage kernel (whole-mesh launches, 2D): one CTA of 512 threads per SM
+// walks the tiles of kTileX2 x kPRows cells (tile t, t + gridDim.x, ...).  The next tile's
+// box is requested into the stage array as soon as the volume phase has read the current
+// one, and the tile's Un box into a buffer of its own at the tile's start, so that both
+// loads overlap the arithmetic, and all sixteen warps of an SM work in the same phase
+// (one copy of the phase's code in the instruction caches).  Every wait is bounded; a wait
+// that gives up sets flag bit 2, and the CTA waits (bounded) for its copies in flight and
+// stops.
+constexpr int kPThreadRows = kPRows / 2;
+
+template <int P>
+constexpr size_t p_tile_bytes() { return (sizeof(TileSmem<P, 2, kPThreadRows>) + 127) / 128 * 128; }
+template <int P>
+constexpr size_t p_smem_bytes() { return p_tile_bytes<P>() + sizeof(Real) * Tab<P>::K * kPRows * TX; }
+
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(bar)
+        : "memory");
+}
+
+template <int P, int FLUX>
+__global__ void __launch_bounds__(TX * kPThreadRows, 1) stage_kernel_p(const __grid_constant__ KParams A)
+{
+    using Smem = TileSmem<P, 2, kPThreadRows>;
+    constexpr int K = Tab<P>::K;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    if ((__cvta_generic_to_shared(smem_raw) & 127u) != 0) {   // TMA needs aligned boxes
+        if (threadIdx.x == 0) atomicOr(A.flag, 2u);
+        return;
+    }
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    Real* un = reinterpret_cast<Real*>(smem_raw + p_tile_bytes<P>());
+    const int ntx = (A.nx + TX - 1) / TX, nty = (A.ny + kPRows - 1) / kPRows, ntiles = ntx * nty;
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    const int tid = threadIdx.x;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.mbar);
+    const uint32_t bar_un = (uint32_t)__cvta_generic_to_shared(&S.mbar_un);
+    const uint32_t su_dst = (uint32_t)__cvta_generic_to_shared(&S.su[0][0][0]);
+    const uint32_t un_dst = (uint32_t)__cvta_generic_to_shared(un);
+    constexpr uint32_t box_bytes = (uint32_t)(sizeof(Real) * K * Smem::HYC * HX);
+    constexpr uint32_t un_bytes = (uint32_t)(sizeof(Real) * K * kPRows * TX);
+    const bool has_un = A.has_un != 0;
+    if (tid == 0) {
+        S.fail_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_un) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        tma_box(su_dst, &A.tmap_p, (t % ntx) * TX - OX, (t / ntx) * kPRows - OY, bar, box_bytes);
+        if (has_un) tma_box(un_dst, &A.tmap_un_p, (t % ntx) * TX, (t / ntx) * kPRows, bar_un, un_bytes);
+    }
+    uint32_t ph = 0, ph_un = 0;
+    bool box_pending = true, un_pending = has_un;
+    for (;;) {
+        const bool ok = mbar_wait(bar, ph, A.wait_limit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(A.flag, 2u);
+            break;
+        }
+        ph ^= 1u;
+        box_pending = false;
+        const int nt = t + (int)gridDim.x;
+        const bool more = nt < ntiles;
+        process_tile<P, FLUX, 0, 2, kPThreadRows, true, 2>(A, (t % ntx) * TX, (t / ntx) * kPRows, S, nullptr,
+                                                          more ? (nt % ntx) * TX : -1, more ? (nt / ntx) * kPRows : 0,
+                                                          un, ph_un);
+        box_pending = more;
+        if (__syncthreads_or(S.fail_s)) break;     // a Un wait gave up (flag set)
+        if (has_un) {
+            ph_un ^= 1u;
+            un_pending = false;
+        }
+        if (!more) break;
+        t = nt;
+        if (has_un) {
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_box(un_dst, &A.tmap_un_p, (t % ntx) * TX, (t / ntx) * kPRows, bar_un, un_bytes);
+            }
+            un_pending = true;
+        }
+    }
+    // copies still in flight land in this CTA's shared memory: wait for them (bounded)
+    if (box_pending) mbar_wait(bar, ph);
+    if (un_pending) mbar_wait(bar_un, ph_un);
+}
+#endif
+
 static KParams make_params(const StageArgs& s)
 {
     KParams a;
@@ -1228,6 +1359,11 @@ static KParams make_params(const StageArgs& s)
     if (s.tmap_un) {
         a.tmap_un = *s.tmap_un;
         a.use_tma_un = 1;
+    }
+    if (s.tmap_p) a.tmap_p = *s.tmap_p;
+    if (s.tmap_un_p) {
+        a.tmap_un_p = *s.tmap_un_p;
+        a.use_p_un = 1;
     }
     a.Uk = static_cast<const Real*>(s.Uk);
     a.Un = static_cast<const Real*>(s.Un);
@@ -1340,7 +1476,7 @@ __device__ __forceinline__ void batch_tiles(const BatchArgs& B, const BatchInst&
             origin(tile0 + i + 1, nx0, ny0);
             stage_tile_async<P, kBatchLanes, TYB>(A, nx0, ny0, (i & 1) ? *buf0 : *buf1);
         }
-        process_tile<P, FLUX, 0, kBatchLanes, TYB, false, true>(A, tx0, ty0, S, (i & 1) ? buf1 : buf0);
+        process_tile<P, FLUX, 0, kBatchLanes, TYB, false, 1>(A, tx0, ty0, S, (i & 1) ? buf1 : buf0);
         cp_async_wait_all();      // nothing left in flight when the tile had no face phase wait
         __syncthreads();
     }
@@ -1588,6 +1724,27 @@ __device__ __forceinline__ Real max_nan(Real a, Real b)
 #include "dgw_tc_volume.cuh"
 #endif
 
+#if DGW_DIM == 2
+template <int P, int FLUX>
+static cudaError_t launch_persistent(const KParams& a, cudaStream_t st)
+{
+    constexpr size_t smem = p_smem_bytes<P>();
+    static_assert(smem <= 227 * 1024, "persistent tile exceeds the shared memory of an SM");
+    static int nsm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (nsm[dev] == 0) {
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel_p<P, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int ntiles = ((a.nx + TX - 1) / TX) * ((a.ny + kPRows - 1) / kPRows);
+    if (ntiles == 0) return cudaSuccess;
+    stage_kernel_p<P, FLUX><<<ntiles < nsm[dev] ? ntiles : nsm[dev], TX * kPThreadRows, smem, st>>>(a);
+    return cudaGetLastError();
+}
+#endif
+
 template <int P, int FLUX>
 static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
 {
@@ -1611,6 +1768,12 @@ static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
         if (e != cudaSuccess) return e;
         opted[mode] = true;
     }
+#if DGW_DIM == 2
+    if constexpr (kF32) {
+        if (mode == 0 && s.tmap_p && s.tile_row0 == 0 && s.tile_rows == 0 && (!a.has_un || a.use_p_un))
+            return launch_persistent<P, FLUX>(a, st);
+    }
+#endif
     if (mode == 0) stage_kernel<P, FLUX, 0><<<grid, NTS, smem, st>>>(a);
     else stage_kernel<P, FLUX, 1><<<grid, NTS, smem, st>>>(a);
     return cudaGetLastError();
