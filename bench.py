@@ -112,7 +112,7 @@ def dt_of(w):
 # kernel in its current form measured them (dram__bytes_read.sum + dram__bytes_write.sum).
 # None until the current kernel has been captured: the figure of an earlier kernel is
 # not reported.
-STAGE_TRAFFIC_BYTES = 138.5e6
+STAGE_TRAFFIC_BYTES = 132.0e6
 
 # FP32 peak of one GB300 from its unit counts and maximum clock: 152 SMs x 128 FP32
 # lanes x 2 flops per FMA x 2.07 GHz.
@@ -653,7 +653,7 @@ def main():
                          "traffic": STAGE_TRAFFIC_BYTES if args.workload == "kpp_1024x1024_q3" else None,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
                          "flops_per_cell": fpc, "sincos_per_cell": sincos,
-                         "kernel": "stage_kernel (3 launches per step)",
+                         "kernel": "stage_kernel_p, persistent (3 launches per step)",
                          "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                                  "peak_source": src, "bytes_per_launch": alg_bytes}},
             "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": r32.get("bytes"),
