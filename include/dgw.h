@@ -235,6 +235,15 @@ dgw_status dgw_sync_status(dgw_ctx* ctx, void* stream);
  * a hang.  Drops the context's cached graphs. */
 dgw_status dgw_debug(dgw_ctx* ctx, int wait_limit);
 
+/* Which kernel runs the context's whole-mesh stage launches on 2D FP32 meshes whose rows
+ * are 16-byte multiples: 0 (the default) the persistent kernel (one 512-thread CTA per
+ * SM walking tiles of 32 x 32 cells, the next tile's data loaded during the current
+ * one's arithmetic) when the mesh has at least four such tiles per SM, else the tile
+ * kernel (one CTA per 32 x 16-cell tile); 1 always the tile kernel; 2 the persistent
+ * kernel wherever it applies.  The two kernels give bitwise the same results.  Any
+ * other choice is DGW_EINVAL.  Drops the context's cached graphs. */
+dgw_status dgw_set_stage_kernel(dgw_ctx* ctx, int choice);
+
 /* ------------------------------------------------------------------------------------
  * Discrete adjoint (the paper has no counterpart: it differentiates the discrete scheme
  * of Sec. 2-4).  Built for periodic meshes with the advection and Burgers fluxes;

@@ -70,6 +70,7 @@ struct dgw_ctx {
     double* t_dev = nullptr;     // the context's time (DGW_BC_STATE sides), advanced per step
     bool state_sides = false;
     int wait_limit = 0;          // bounded TMA waits: 0 the kernels' default limit (dgw_debug)
+    int stage_kernel = 0;        // dgw_set_stage_kernel
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<std::pair<const void*, int>, CUtensorMap> tmaps;   // TMA descriptors (2D): (array, box kind)
     void* adj_ws = nullptr;      // adjoint: per-cell partials (own), K*E
@@ -359,6 +360,7 @@ static StageArgs base_args(const dgw_ctx* c)
     a.gas_gamma = c->flux.gas_gamma;
     a.flag = c->flag;
     a.wait_limit = c->wait_limit;
+    a.kernel_choice = c->stage_kernel;
     a.t_dev = c->t_dev;
     a.t_off = 0.0;
     for (int i = 0; i < 2; ++i)
@@ -385,8 +387,8 @@ static cudaError_t launch(const dgw_ctx* c, const StageArgs& a0, int mode, cudaS
     a.tmap_p = a.tmap_un_p = nullptr;
     // whole-mesh float stage launches run the persistent kernel when its boxes apply
     // (the Un box too, where the stage reads Un)
-    if (!f64 && c->mesh.dim == 2 && mode == 0 && a.tile_row0 == 0 && a.tile_rows == 0 && a.tmap &&
-        tensor_map(c, a.Uk, 2, &m_pk)) {
+    if (!f64 && c->mesh.dim == 2 && mode == 0 && a.kernel_choice != 1 && a.tile_row0 == 0 && a.tile_rows == 0 &&
+        a.tmap && tensor_map(c, a.Uk, 2, &m_pk)) {
         const bool need_un = a.cn != 0.0 && a.Un;
         if (!need_un || (a.tmap_un && tensor_map(c, a.Un, 3, &m_pn))) {
             a.tmap_p = &m_pk;
@@ -1572,6 +1574,16 @@ extern "C" dgw_status dgw_debug(dgw_ctx* c, int wait_limit)
     if (st != DGW_OK) return st;
     c->wait_limit = wait_limit;
     drop_graphs(c);          // the cached graphs hold the old launch parameters
+    return DGW_OK;
+}
+
+extern "C" dgw_status dgw_set_stage_kernel(dgw_ctx* c, int choice)
+{
+    dgw_status st = check_ctx(c);
+    if (st != DGW_OK) return st;
+    if (choice < 0 || choice > 2) return fail(DGW_EINVAL, "stage kernel choice %d (0, 1 or 2)", choice);
+    c->stage_kernel = choice;
+    drop_graphs(c);          // the cached graphs hold the old kernels
     return DGW_OK;
 }
 

@@ -77,6 +77,7 @@ struct StageArgs {
     const CUtensorMap* tmap_p;   // 2D float: descriptor of Uk for the persistent kernel (box kBoxX2 x
                                  // (kPRows + 2) x K), or null: that kernel runs only when given
     const CUtensorMap* tmap_un_p;  // and of Un (box kTileX2 x kPRows x K), or null
+    int kernel_choice;     // whole-mesh float 2D stages: 0 automatic, 1 tile kernel, 2 persistent kernel
     int tile_row0;         // 2D: first tile row of the launch
     int tile_rows;         // 2D: tile rows of the launch (0: through the last row of the mesh)
     int wait_limit;        // polls of a bounded TMA wait: 0 the default limit, < 0 none (the

@@ -170,22 +170,30 @@ __device__ __forceinline__ double div_w(double a, double b) { return a / b; }
 
 constexpr double kPi = 3.14159265358979323846;
 
+// Products and sums rounded one way in every kernel that inlines them (intrinsics are not
+// contracted into FMAs by the compiler): the positions and velocities of the
+// position-dependent flux, so that the tile and persistent kernels round them alike.
+__device__ __forceinline__ float mul_x(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_x(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Flux F(u) at (x, y) and |F'(u)|_2 (1D: only the x component).
 template <int FLUX>
 __device__ __forceinline__ void vol_flux(const KParams& A, Real u, Real x, Real y, Real& fx, Real& fy,
                                          Real& spd)
 {
     if (FLUX == FLUX_ADVECT) {
-        fx = A.a0 * u; fy = A.a1 * u;
-        spd = DIM == 1 ? fabs(A.a0) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1);
+        fx = mul_x(A.a0, u); fy = mul_x(A.a1, u);
+        spd = DIM == 1 ? fabs(A.a0) : sqrt_r(fma_x(A.a0, A.a0, mul_x(A.a1, A.a1)));
     } else if (FLUX == FLUX_ROTATION) {
-        const Real vx = A.omega * (A.cy - y), vy = A.omega * (x - A.cx);
-        fx = vx * u; fy = vy * u;
-        spd = DIM == 1 ? fabs(vx) : sqrt_r(vx * vx + vy * vy);
+        const Real vx = mul_x(A.omega, A.cy - y), vy = mul_x(A.omega, x - A.cx);
+        fx = mul_x(vx, u); fy = mul_x(vy, u);
+        spd = DIM == 1 ? fabs(vx) : sqrt_r(fma_x(vx, vx, mul_x(vy, vy)));
     } else if (FLUX == FLUX_BURGERS) {
-        const Real hu2 = Real(0.5) * u * u;
-        fx = A.a0 * hu2; fy = A.a1 * hu2;
-        spd = DIM == 1 ? fabs(A.a0 * u) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1) * fabs(u);
+        const Real hu2 = mul_x(mul_x(Real(0.5), u), u);
+        fx = mul_x(A.a0, hu2); fy = mul_x(A.a1, hu2);
+        spd = DIM == 1 ? fabs(mul_x(A.a0, u)) : mul_x(sqrt_r(fma_x(A.a0, A.a0, mul_x(A.a1, A.a1))), fabs(u));
     } else {  // KPP: F = (sin u, cos u), |F'| = 1 in 2D
         Real s, c;
         sincos_r(u, &s, &c);
@@ -354,7 +362,7 @@ template <int FLUX>
 __device__ __forceinline__ Real dflux_axis(const KParams& A, int axis, Real u, Real x, Real y)
 {
     if (FLUX == FLUX_ADVECT) return axis == 0 ? A.a0 : A.a1;
-    if (FLUX == FLUX_ROTATION) return axis == 0 ? A.omega * (A.cy - y) : A.omega * (x - A.cx);
+    if (FLUX == FLUX_ROTATION) return axis == 0 ? mul_x(A.omega, A.cy - y) : mul_x(A.omega, x - A.cx);
     if (FLUX == FLUX_BURGERS) return (axis == 0 ? A.a0 : A.a1) * u;
     Real s, c;
     sincos_r(u, &s, &c);
@@ -366,14 +374,15 @@ __device__ __forceinline__ Real dflux_axis(const KParams& A, int axis, Real u, R
 template <int FLUX>
 __device__ __forceinline__ Real llf(const KParams& A, int axis, Real uL, Real uR, Real x, Real y)
 {
+    // (products and sums in a fixed order: the tile and persistent kernels round alike)
     if (FLUX == FLUX_ADVECT || FLUX == FLUX_ROTATION) {
         const Real v = FLUX == FLUX_ADVECT ? (axis == 0 ? A.a0 : A.a1)
-                                           : (axis == 0 ? A.omega * (A.cy - y) : A.omega * (x - A.cx));
-        return Real(0.5) * v * (uL + uR) - Real(0.5) * fabs(v) * (uR - uL);
+                                           : (axis == 0 ? mul_x(A.omega, A.cy - y) : mul_x(A.omega, x - A.cx));
+        return fma_x(mul_x(Real(-0.5), fabs(v)), uR - uL, mul_x(mul_x(Real(0.5), v), uL + uR));
     } else if (FLUX == FLUX_BURGERS) {
         const Real an = axis == 0 ? A.a0 : A.a1;
-        const Real s = fabs(an) * fmax(fabs(uL), fabs(uR));
-        return Real(0.25) * an * (uL * uL + uR * uR) - Real(0.5) * s * (uR - uL);
+        const Real s = mul_x(fabs(an), fmax(fabs(uL), fabs(uR)));
+        return fma_x(mul_x(Real(-0.5), s), uR - uL, mul_x(mul_x(Real(0.25), an), fma_x(uL, uL, mul_x(uR, uR))));
     } else {
         // x-normal: n.F = sin u, |F'.n| = |cos u| (maximal at multiples of pi);
         // y-normal: n.F = cos u, |F'.n| = |sin u| (maximal at pi/2 + multiples of pi).
@@ -879,17 +888,17 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = vbc<V>(0);
     V lam = vbc<V>(0);
-    const Real xc = A.x0 + (Real(gx) + Real(0.5)) * A.h;
+    const Real xc = fma_x(Real(gx) + Real(0.5), A.h, A.x0);
     V yc;
 #pragma unroll
-    for (int l = 0; l < L; ++l) lane(yc, l) = DIM == 2 ? A.y0 + (Real(gy[l]) + Real(0.5)) * A.h : Real(0);
+    for (int l = 0; l < L; ++l) lane(yc, l) = DIM == 2 ? fma_x(Real(gy[l]) + Real(0.5), A.h, A.y0) : Real(0);
     if constexpr (DIM == 1) {
         V u[NQ], fx[NQ];
         interp_sym<N1, NQ>(T.B, c, u);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             V fy, spd;
-            vol_flux_v<FLUX>(A, u[q], xc + A.hh * T.g[q], vbc<V>(0), fx[q], fy, spd);
+            vol_flux_v<FLUX>(A, u[q], fma_x(A.hh, T.g[q], xc), vbc<V>(0), fx[q], fy, spd);
             lam = vmax(lam, spd);
         }
         project_sym<true, N1, NQ>(T.WD, fx, acc);
@@ -902,13 +911,13 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
         auto row = [&](const int qy, const V (&rr)[N1]) {
             V y;
 #pragma unroll
-            for (int l = 0; l < L; ++l) lane(y, l) = lane(yc, l) + A.hh * T.g[qy];
+            for (int l = 0; l < L; ++l) lane(y, l) = fma_x(A.hh, T.g[qy], lane(yc, l));
             V u[NQ], fx[NQ], fy[NQ];
             interp_sym<N1, NQ>(T.B, rr, u);
 #pragma unroll
             for (int qx = 0; qx < NQ; ++qx) {
                 V spd;
-                vol_flux_v<FLUX>(A, u[qx], xc + A.hh * T.g[qx], y, fx[qx], fy[qx], spd);
+                vol_flux_v<FLUX>(A, u[qx], fma_x(A.hh, T.g[qx], xc), y, fx[qx], fy[qx], spd);
                 lam = vmax(lam, spd);
             }
             V px[N1], py[N1];
@@ -1070,8 +1079,13 @@ __device__ __forceinline__ void process_tile(const KParams& A, const int tx0, co
                     Real x = Real(0), y = Real(0);
                     if (FLUX == FLUX_ROTATION || need_lam || !minus_in || !plus_in) {
                         const int fgx = tx0 + flx[l], fgy = ty0 + fly[l];
-                        if (xf) { x = A.x0 + Real(fgx) * A.h; y = DIM == 2 ? A.y0 + (Real(fgy) + Real(0.5)) * A.h + A.hh * T.g[q] : Real(0); }
-                        else { x = A.x0 + (Real(fgx) + Real(0.5)) * A.h + A.hh * T.g[q]; y = A.y0 + Real(fgy) * A.h; }
+                        if (xf) {
+                            x = fma_x(Real(fgx), A.h, A.x0);
+                            y = DIM == 2 ? fma_x(A.hh, T.g[q], fma_x(Real(fgy) + Real(0.5), A.h, A.y0)) : Real(0);
+                        } else {
+                            x = fma_x(A.hh, T.g[q], fma_x(Real(fgx) + Real(0.5), A.h, A.x0));
+                            y = fma_x(Real(fgy), A.h, A.y0);
+                        }
                     }
                     Real ul = lane(uLq[q], l), ur = lane(uRq[q], l);
                     if (!minus_in) {
@@ -1725,22 +1739,42 @@ __device__ __forceinline__ Real max_nan(Real a, Real b)
 #endif
 
 #if DGW_DIM == 2
+// SMs of the current device (0 if it cannot be read)
+static int sm_count()
+{
+    static int nsm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (nsm[dev] == 0 && cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm[dev] = 0;
+    return nsm[dev];
+}
+
+// The persistent kernel pays where every SM walks several of its tiles; on smaller meshes
+// (fewer than four tiles of 32 x 32 cells per SM) the tile kernel's smaller tiles keep
+// more SMs busy.
+static bool persistent_pays(int nx, int ny)
+{
+    const int nsm = sm_count();
+    const long long ntiles = (long long)((nx + TX - 1) / TX) * ((ny + kPRows - 1) / kPRows);
+    return nsm > 0 && ntiles >= 4LL * nsm;
+}
+
 template <int P, int FLUX>
 static cudaError_t launch_persistent(const KParams& a, cudaStream_t st)
 {
     constexpr size_t smem = p_smem_bytes<P>();
     static_assert(smem <= 227 * 1024, "persistent tile exceeds the shared memory of an SM");
-    static int nsm[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (nsm[dev] == 0) {
+    static bool opted = false;
+    if (!opted) {
         cudaError_t e = cudaFuncSetAttribute(stage_kernel_p<P, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
+        opted = true;
     }
+    const int nsm = sm_count();
     const int ntiles = ((a.nx + TX - 1) / TX) * ((a.ny + kPRows - 1) / kPRows);
     if (ntiles == 0) return cudaSuccess;
-    stage_kernel_p<P, FLUX><<<ntiles < nsm[dev] ? ntiles : nsm[dev], TX * kPThreadRows, smem, st>>>(a);
+    stage_kernel_p<P, FLUX><<<ntiles < nsm ? ntiles : nsm, TX * kPThreadRows, smem, st>>>(a);
     return cudaGetLastError();
 }
 #endif
@@ -1770,7 +1804,8 @@ static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
     }
 #if DGW_DIM == 2
     if constexpr (kF32) {
-        if (mode == 0 && s.tmap_p && s.tile_row0 == 0 && s.tile_rows == 0 && (!a.has_un || a.use_p_un))
+        if (mode == 0 && s.tmap_p && s.tile_row0 == 0 && s.tile_rows == 0 && (!a.has_un || a.use_p_un) &&
+            (s.kernel_choice == 2 || persistent_pays(s.nx, s.ny)))
             return launch_persistent<P, FLUX>(a, st);
     }
 #endif

@@ -61,7 +61,7 @@ class Params(ctypes.Structure):
 # every symbol declared in include/dgw.h
 EXPORTS = ("dgw_defaults", "dgw_create", "dgw_destroy", "dgw_sizes", "dgw_set_params", "dgw_project",
            "dgw_residual", "dgw_sensor", "dgw_rk_step", "dgw_rk_step_host", "dgw_mass",
-           "dgw_sync_status", "dgw_debug", "dgw_set_time", "dgw_get_time", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_rk_step_stages", "dgw_adjoint_step_stages", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
+           "dgw_sync_status", "dgw_debug", "dgw_set_stage_kernel", "dgw_set_time", "dgw_get_time", "dgw_residual_vjp", "dgw_adjoint_step", "dgw_rk_step_stages", "dgw_adjoint_step_stages", "dgw_misfit", "dgw_batch_create", "dgw_batch_destroy", "dgw_batch_sizes",
            "dgw_batch_set_dt", "dgw_batch_project", "dgw_batch_rk_step", "dgw_batch_autotune",
            "dgw_batch_schedule", "dgw_batch_set_schedule", "dgw_batch_sync_status", "dgw_batch_debug", "dgw_rk_step_noalloc", "dgw_selftest_sincos", "dgw_selftest_tc_volume",
            "dgw_last_error", "dgw_version")
@@ -92,6 +92,7 @@ def load(build: bool = True):
         L.dgw_mass.argtypes = [vp, vp, dp, vp]
         L.dgw_sync_status.argtypes = [vp, vp]
         L.dgw_debug.argtypes = [vp, ctypes.c_int]
+        L.dgw_set_stage_kernel.argtypes = [vp, ctypes.c_int]
         L.dgw_set_time.argtypes = [vp, ctypes.c_double, vp]
         L.dgw_get_time.argtypes = [vp, dp, vp]
         L.dgw_residual_vjp.argtypes = [vp, vp, vp, vp, vp]
@@ -306,6 +307,10 @@ class Context:
     def debug(self, wait_limit: int):
         """Poll limit of the stage kernels' bounded TMA waits (dgw_debug)."""
         _check(load().dgw_debug(self._h, int(wait_limit)))
+
+    def set_stage_kernel(self, choice: int):
+        """0 automatic, 1 the tile kernel, 2 the persistent kernel (dgw_set_stage_kernel)."""
+        _check(load().dgw_set_stage_kernel(self._h, int(choice)))
 
     def residual_vjp(self, U, lam, out, stream=None):
         """out = J_L(U)^T lam (dgw_residual_vjp)."""

@@ -388,8 +388,61 @@ def test_nonfinite_detected():
     ctx.sync_status()   # cleared
 
 
+# Meshes whose 32 x 32-cell tiles outnumber the SMs (each persistent CTA walks several
+# tiles), ragged in x and y, with the boundary sets of the scalar tests.
+PERSISTENT_CASES = [(3, "kpp", "outflow", "weno"), (2, "burgers", "periodic", "weno"), (1, "advect", "periodic", "lo"),
+                    (3, "rotation", "inflow_zero", "zhao"), (2, "kpp", "outflow", "dg")]
+
+
+@pytest.mark.parametrize("p,flux,bc,stab", PERSISTENT_CASES)
+def test_persistent_kernel_bitwise_equals_tile_kernel(p, flux, bc, stab):
+    """The persistent float kernel (dgw_set_stage_kernel 2: 512-thread CTAs walking
+    32 x 32-cell tiles, boxes prefetched) and the tile kernel (1) give bitwise the same
+    residual and the same state after 5 SSP-RK3 steps, on a 600 x 300 mesh (190 tiles for
+    152 SMs, ragged in x and y) and on a 44 x 36 mesh (two by two ragged tiles)."""
+    for nx, ny in ((600, 300), (44, 36)):
+        s = H.spec(2, p, nx, ny=ny, flux=flux, bc=bc, stab=stab)
+        if flux == "kpp":
+            s["lambda_nu"] = 2.0
+        U = H.state_for(s, seed=41 + p)
+        out = []
+        for choice in (1, 2):
+            ctx = gpu(s, "fp32")
+            ctx.set_stage_kernel(choice)
+            Ud = to_dev(U, "fp32")
+            L = torch.empty_like(Ud)
+            ctx.residual(Ud, L)
+            ctx.rk_step(Ud, 2e-4 * 44 / nx, 5)
+            torch.cuda.synchronize()
+            ctx.sync_status()
+            out.append((L, Ud))
+        assert torch.equal(out[0][0], out[1][0]), (nx, ny)
+        assert torch.equal(out[0][1], out[1][1]), (nx, ny)
+
+
+def test_persistent_kernel_residual_per_cell(oracle_mod):
+    """The persistent kernel's FP32 residual against the oracle cell by cell on a ragged
+    44 x 36 Q3 KPP mesh (float-rounded state on both sides)."""
+    s = H.spec(2, 3, 44, ny=36, flux="kpp", bc="outflow", stab="weno", lambda_nu=2.0)
+    U = H.state_for(s, seed=77).astype(np.float32).astype(np.float64)
+    ref = oracle_mod.residual(oracle_mod.Problem(**s), U)
+    ctx = gpu(s, "fp32")
+    ctx.set_stage_kernel(2)
+    got = gpu_residual(ctx, U)
+    ok = ~H.near_threshold(oracle_mod, s, U)
+    assert H.cell_err(got[:, ok], ref[:, ok]) <= FP32_CELL_TOL
+
+
+def test_stage_kernel_choice_checked():
+    ctx = gpu(H.spec(2, 2, 16), "fp32")
+    with pytest.raises(dgw.DGWError) as ei:
+        ctx.set_stage_kernel(3)
+    assert ei.value.status == -1
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_tma_wait_give_up_reported(prec):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_tma_wait_give_up_reported(prec, kernel):
     """A stage kernel's bounded wait on its TMA tile copy that gives up (forced through
     dgw_debug: the wait stops at once, the copy still lands and is waited for) skips the
     tile and sets the flag that dgw_sync_status reports as DGW_ETIMEOUT, without a hang;
@@ -397,6 +450,7 @@ def test_tma_wait_give_up_reported(prec):
     s = H.spec(2, 2, 64, ny=40, flux="burgers")           # 16-byte rows: TMA staging
     U = H.state_for(s, seed=13)
     ctx = gpu(s, prec)
+    ctx.set_stage_kernel(kernel)
     ctx.debug(-1)
     Ud = to_dev(U, prec)
     ctx.rk_step(Ud, 1e-3, 2)
@@ -409,7 +463,9 @@ def test_tma_wait_give_up_reported(prec):
     ctx.rk_step(Ud, 1e-3, 2)
     ctx.sync_status()
     ref = to_dev(U, prec)
-    gpu(s, prec).rk_step(ref, 1e-3, 2)
+    fresh = gpu(s, prec)
+    fresh.set_stage_kernel(kernel)
+    fresh.rk_step(ref, 1e-3, 2)
     torch.cuda.synchronize()
     assert torch.equal(Ud, ref)
 
