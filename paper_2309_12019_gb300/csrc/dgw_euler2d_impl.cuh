@@ -450,12 +450,13 @@ static cudaError_t launch_euler2d_p(const StageArgs& s, int mode, cudaStream_t s
     dim3 grid((s.nx + EX - 1) / EX, (s.ny + EY - 1) / EY);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     const size_t smem = sizeof(Euler2Smem<P>);
-    static bool opted[2] = {false, false};
-    if (!opted[mode]) {
+    static bool opted[64][2] = {{false, false}};
+    const int dev = cur_device();
+    if (!opted[dev][mode]) {
         const void* fn = mode == 0 ? (const void*)euler2d_kernel<P, 0> : (const void*)euler2d_kernel<P, 1>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        opted[mode] = true;
+        opted[dev][mode] = true;
     }
     if (mode == 0) euler2d_kernel<P, 0><<<grid, ENT, smem, st>>>(a);
     else euler2d_kernel<P, 1><<<grid, ENT, smem, st>>>(a);

@@ -1357,6 +1357,15 @@ __global__ void __launch_bounds__(TX * kPThreadRows, 1) stage_kernel_p(const __g
 }
 #endif
 
+// Current device, for per-device caches of kernel attributes (0 if it cannot be read or
+// lies beyond the caches' 64 entries).
+static int cur_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    return dev;
+}
+
 static KParams make_params(const StageArgs& s)
 {
     KParams a;
@@ -1765,11 +1774,12 @@ static cudaError_t launch_persistent(const KParams& a, cudaStream_t st)
 {
     constexpr size_t smem = p_smem_bytes<P>();
     static_assert(smem <= 227 * 1024, "persistent tile exceeds the shared memory of an SM");
-    static bool opted = false;
-    if (!opted) {
+    static bool opted[64] = {false};
+    const int dev = cur_device();
+    if (!opted[dev]) {
         cudaError_t e = cudaFuncSetAttribute(stage_kernel_p<P, FLUX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        opted = true;
+        opted[dev] = true;
     }
     const int nsm = sm_count();
     const int ntiles = ((a.nx + TX - 1) / TX) * ((a.ny + kPRows - 1) / kPRows);
@@ -1790,17 +1800,18 @@ static cudaError_t launch_pf(const StageArgs& s, int mode, cudaStream_t st)
     dim3 grid((s.nx + TX - 1) / TX, grows);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     const size_t smem = sizeof(TileSmem<P, LS, TYS>);
-    // once per instantiation: opt in to more than 48 KB of dynamic shared memory where
-    // needed, and prefer the largest shared-memory carveout (several tiles per SM)
-    static bool opted[2] = {false, false};
-    if (!opted[mode]) {
+    // once per instantiation and device: opt in to more than 48 KB of dynamic shared
+    // memory where needed, and prefer the largest shared-memory carveout (several tiles per SM)
+    static bool opted[64][2] = {{false, false}};
+    const int dev = cur_device();
+    if (!opted[dev][mode]) {
         const void* fn = mode == 0 ? (const void*)stage_kernel<P, FLUX, 0> : (const void*)stage_kernel<P, FLUX, 1>;
         cudaError_t e = cudaSuccess;
         if (smem > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        opted[mode] = true;
+        opted[dev][mode] = true;
     }
 #if DGW_DIM == 2
     if constexpr (kF32) {
