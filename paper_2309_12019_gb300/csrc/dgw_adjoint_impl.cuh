@@ -273,11 +273,13 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
 #pragma unroll
         for (int k = 0; k < K; ++k) cbar[k] = Real(0);
         if (A.stab == STAB_WENO) {
-            Real cl[NF][K], beta[NF + 1], what[NF + 1];
+            // (each divisor is inverted once and its quotients taken as products)
+            Real cl[NF][K], beta[NF + 1], what[NF + 1], ib[NF + 1];   // ib: 1 / (eps_w + beta)
             const Real beta0 = qform<P>(T, c);
             beta[0] = beta0;
             const Real lin0 = Real(1) - Real(NF) * A.w_nbr;
-            what[0] = lin0 / ((A.eps_w + beta0) * (A.eps_w + beta0));
+            ib[0] = Real(1) / (A.eps_w + beta0);
+            what[0] = lin0 * ib[0] * ib[0];
             Real W = what[0];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -297,10 +299,11 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
                 }
                 cl[f][0] = Real(0);
                 beta[f + 1] = qform<P>(T, cl[f]);
-                const Real dl = A.eps_w + beta[f + 1];
-                what[f + 1] = A.w_nbr / (dl * dl);
+                ib[f + 1] = Real(1) / (A.eps_w + beta[f + 1]);
+                what[f + 1] = A.w_nbr * ib[f + 1] * ib[f + 1];
                 W += what[f + 1];
             }
+            const Real iW = Real(1) / W;
             Real d[K];
             d[0] = Real(0);
 #pragma unroll
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
                 Real s = Real(0);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) s = fma(what[f + 1], c[k] - cl[f][k], s);
-                d[k] = s / W;
+                d[k] = s * iW;
             }
             const Real num = sqrt_r(fmax(qform<P>(T, d), Real(0)));
             bool smooth_part = false;
@@ -323,14 +326,14 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
                 if (r < A.b) gamma = Real(0);
             }
             // reverse sweep of gamma with gbar = d out / d gamma
-            const Real gbar = -z * lamv / Real(P);
+            const Real gbar = -z * lamv * Real(1.0 / P);
             if (smooth_part && gbar != Real(0)) {
-                const Real den = sqrt_r(beta0);
+                const Real iden = Real(1) / sqrt_r(beta0);
                 const Real rbar = A.q_one ? gbar : gbar * A.q * pow(r, A.q - Real(1));
-                const Real numbar = rbar / den;
-                const Real denbar = -rbar * r / den;
+                const Real numbar = rbar * iden;
+                const Real denbar = -rbar * r * iden;
                 const Real n2bar = numbar / (Real(2) * num);
-                Real b0bar = denbar / (Real(2) * den);
+                Real b0bar = denbar * (Real(0.5) * iden);
                 Real gd[K];
                 gram_mv<P>(T, d, gd);
                 Real dbar[K];
@@ -343,14 +346,14 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
 #pragma unroll
                     for (int k = 1; k < K; ++k) s = fma(dbar[k], c[k] - cl[f][k], s);
                     omb[f] = s;
-                    S = fma(s, what[f + 1] / W, S);
+                    S = fma(s, what[f + 1] * iW, S);
                 }
-                const Real w1 = (W - what[0]) / W;   // sum of the neighbour weights
+                const Real w1 = (W - what[0]) * iW;   // sum of the neighbour weights
 #pragma unroll
                 for (int k = 1; k < K; ++k) cbar[k] = fma(w1, dbar[k], cbar[k]);
                 // own weight: what_0 only enters through the normalisation
-                const Real what0bar = -S / W;
-                b0bar += Real(-2) * what0bar * what[0] / (A.eps_w + beta0);
+                const Real what0bar = -S * iW;
+                b0bar += Real(-2) * what0bar * what[0] * ib[0];
                 Real gc[K];
                 gram_mv<P>(T, c, gc);
 #pragma unroll
@@ -358,9 +361,9 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     const int axis = f >> 1, side = f & 1;
-                    const Real omega = what[f + 1] / W;
-                    const Real whatbar = (omb[f] - S) / W;
-                    const Real bbar = Real(-2) * whatbar * what[f + 1] / (A.eps_w + beta[f + 1]);
+                    const Real omega = what[f + 1] * iW;
+                    const Real whatbar = (omb[f] - S) * iW;
+                    const Real bbar = Real(-2) * whatbar * what[f + 1] * ib[f + 1];
                     Real gl[K];
                     gram_mv<P>(T, cl[f], gl);
                     Real clbar[K];
@@ -385,12 +388,12 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
                 }
             }
         }
-        const Real gs = gamma * lamv / Real(P);
+        const Real gs = gamma * lamv * Real(1.0 / P);
 #pragma unroll
         for (int k = 0; k < K; ++k) ws[k] = ws[k] - gs * kv[k] + cbar[k];
         // nu_e through lambda_e = |F'(U_h)| at the maximising point
         if (need_lam && gamma != Real(0)) {
-            const Real lbar = -z * gamma / Real(P);
+            const Real lbar = -z * gamma * Real(1.0 / P);
             const Real ds = lbar * dspeed<FLUX>(A, u_at);
             if (ds != Real(0)) {
 #pragma unroll
