@@ -112,7 +112,7 @@ def dt_of(w):
 # kernel in its current form measured them (dram__bytes_read.sum + dram__bytes_write.sum).
 # None until the current kernel has been captured: the figure of an earlier kernel is
 # not reported.
-STAGE_TRAFFIC_BYTES = 132.0e6
+STAGE_TRAFFIC_BYTES = 132.2e6
 
 # FP32 peak of one GB300 from its unit counts and maximum clock: 152 SMs x 128 FP32
 # lanes x 2 flops per FMA x 2.07 GHz.
