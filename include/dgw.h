@@ -194,7 +194,8 @@ dgw_status dgw_sensor(dgw_ctx* ctx, const void* U, double* gamma, void* stream);
 /* nsteps steps of the optimal SSP-RK3 scheme (Eq. ssp) with step dt, in place on U
  * (device, K*E).  Each stage recomputes the sensor from the stage state.  The stage
  * states live in the context's buffers.  Launch sequence is replayed from a CUDA graph
- * cached per (U, dt, nsteps, stream) unless the stream is being captured. */
+ * cached per (U, dt, nsteps, stream) unless the stream is being captured.  nsteps = 0
+ * does nothing; a negative nsteps or a non-finite dt is DGW_EINVAL. */
 dgw_status dgw_rk_step(dgw_ctx* ctx, void* U, double dt, int nsteps, void* stream);
 
 /* As dgw_rk_step for a state held in HOST memory: copies U_in (host, K*E elements,

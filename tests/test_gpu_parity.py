@@ -317,6 +317,31 @@ def test_degenerate_states(oracle_mod):
         assert g[1] == expect and g_ref[1] == expect and np.max(np.abs(g - g_ref)) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_zero_and_negative_step_counts(prec):
+    """nsteps = 0 leaves the state untouched and a negative count is DGW_EINVAL (device
+    entry point); the host entry point takes nsteps >= 1 and refuses 0 without writing."""
+    s = H.spec(2, 2, 40, ny=20, flux="burgers")
+    U = H.state_for(s, seed=5)
+    ctx = gpu(s, prec)
+    Ud = to_dev(U, prec)
+    U0 = Ud.clone()
+    ctx.rk_step(Ud, 1e-3, 0)
+    for dt, n in ((1e-3, -1), (float("nan"), 1), (float("inf"), 1)):
+        with pytest.raises(dgw.DGWError) as ei:
+            ctx.rk_step(Ud, dt, n)
+        assert ei.value.status == -1
+    torch.cuda.synchronize()
+    assert torch.equal(Ud, U0)
+    Uh, Uo = U0.cpu().pin_memory(), torch.full_like(U0.cpu(), 7.0).pin_memory()
+    with pytest.raises(dgw.DGWError) as ei:
+        ctx.rk_step_host(Uh, Uo, 1e-3, 0)
+    assert ei.value.status == -1
+    torch.cuda.synchronize()
+    assert torch.all(Uo == 7.0)
+    ctx.sync_status()
+
+
 def test_graph_replay_matches_direct_launches():
     """dgw_rk_step replays a cached CUDA graph on a non-default stream and launches
     directly on the default stream: the results are bitwise identical, and repeat runs
