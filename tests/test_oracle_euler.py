@@ -423,14 +423,23 @@ def test_2d_prescribed_states_free_stream_and_time(p):
     moved = dataclasses.replace(P, t=0.0, bspeed=(0.0,) * 4,
                                 bsplit=tuple(s + v * 0.07 for s, v in zip(P.bsplit, P.bspeed)))
     assert np.array_equal(O.residual(P, U), O.residual(moved, U))
-    dt = 1e-3
+    # splits fast enough to cross face points between the stage times of one step, still
+    # inside their sides
+    P = _state_sides(5, 4, p, "weno", t=0.0, speeds=(0.0, 20.0, -12.0, 40.0))
+    dt, t0 = 3e-3, 0.0
     at = lambda t: dataclasses.replace(P, t=t)
-    U1 = U + dt * O.residual(at(0.07), U)
-    U2 = 0.75 * U + 0.25 * U1 + 0.25 * dt * O.residual(at(0.07 + dt), U1)
-    U3 = U / 3.0 + 2.0 / 3.0 * U2 + 2.0 / 3.0 * dt * O.residual(at(0.07 + 0.5 * dt), U2)
+    U1 = U + dt * O.residual(at(t0), U)
+    U2 = 0.75 * U + 0.25 * U1 + 0.25 * dt * O.residual(at(t0 + dt), U1)
+    # each stage time matters: the residual of U2 at t + dt/2 is not the one at t + dt or t
+    R2 = O.residual(at(t0 + 0.5 * dt), U2)
+    assert not np.array_equal(R2, O.residual(at(t0 + dt), U2))
+    assert not np.array_equal(R2, O.residual(at(t0), U2))
+    assert not np.array_equal(O.residual(at(t0 + dt), U1), O.residual(at(t0), U1))
+    U3 = U / 3.0 + 2.0 / 3.0 * U2 + 2.0 / 3.0 * dt * R2
+    assert np.isfinite(U3).all()
     assert np.abs(O.rk3(P, U, dt, 1) - U3).max() < 1e-14 * np.abs(U3).max()
     assert not np.array_equal(O.rk3(P, U, dt, 1), O.rk3(dataclasses.replace(P, bspeed=(0.0,) * 4), U, dt, 1))
     # SSP-RK2 (Heun): stages at t and t + dt
-    V1 = U + dt * O.residual(at(0.07), U)
-    V2 = 0.5 * U + 0.5 * V1 + 0.5 * dt * O.residual(at(0.07 + dt), V1)
+    V1 = U + dt * O.residual(at(t0), U)
+    V2 = 0.5 * U + 0.5 * V1 + 0.5 * dt * O.residual(at(t0 + dt), V1)
     assert np.abs(O.rk(P, U, dt, 1, order=2) - V2).max() < 1e-14 * np.abs(V2).max()
