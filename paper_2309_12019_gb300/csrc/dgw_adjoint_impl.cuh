@@ -102,8 +102,9 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
     }
     const bool need_lam = A.stab != STAB_DG && !A.lam_fixed;
     // maximising Gauss point of |F'(U_h)| (for nu_e): kind 0 volume (qa, qb), 1 face (f, q)
+    // the maximiser as one code, kind * 256 + a * 16 + b (a, b < 16): one select per point
     Real lam_max = Real(-1), u_at = Real(0);
-    int at_kind = 0, at_a = 0, at_b = 0;
+    int at_code = 0;
 
     // ---------------- volume term ----------------
     if (DIM == 1) {
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
             for (int i = 0; i < N1; ++i) ws[i] = fma(T.B[q][i], s, ws[i]);
             if (need_lam) {
                 const Real sp = FLUX == FLUX_ADVECT ? fabs(A.a0) : fabs(A.a0 * u);
-                if (sp > lam_max) { lam_max = sp; u_at = u; at_kind = 0; at_a = q; at_b = 0; }
+                if (sp > lam_max) { lam_max = sp; u_at = u; at_code = q * 16; }
             }
         }
     } else {
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
                 if (need_lam) {
                     const Real sp = FLUX == FLUX_ADVECT ? sqrt_r(A.a0 * A.a0 + A.a1 * A.a1)
                                                         : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1) * fabs(u);
-                    if (sp > lam_max) { lam_max = sp; u_at = u; at_kind = 0; at_a = qa; at_b = qb; }
+                    if (sp > lam_max) { lam_max = sp; u_at = u; at_code = qa * 16 + qb; }
                 }
             }
 #pragma unroll
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
             if (need_lam) {
                 const Real sp = FLUX == FLUX_ADVECT ? (DIM == 1 ? fabs(A.a0) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1))
                                                     : (DIM == 1 ? fabs(A.a0 * uo) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1) * fabs(uo));
-                if (sp > lam_max) { lam_max = sp; u_at = uo; at_kind = 1; at_a = f; at_b = q; }
+                if (sp > lam_max) { lam_max = sp; u_at = uo; at_code = 256 + f * 16 + q; }
             }
         }
 #pragma unroll
@@ -315,11 +316,12 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
             }
             const Real num = sqrt_r(fmax(qform<P>(T, d), Real(0)));
             bool smooth_part = false;
-            Real r = Real(0);
+            Real r = Real(0), sb0 = Real(1);
             if (num <= A.eps_s) gamma = Real(0);
             else if (beta0 <= Real(0)) gamma = Real(1);
             else {
-                r = num / sqrt_r(beta0);
+                sb0 = sqrt_r(beta0);
+                r = num / sb0;
                 gamma = r < Real(1) ? r : Real(1);
                 if (!A.q_one) gamma = pow(gamma, A.q);
                 smooth_part = r < Real(1) && !(r < A.b);
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
             // reverse sweep of gamma with gbar = d out / d gamma
             const Real gbar = -z * lamv * Real(1.0 / P);
             if (smooth_part && gbar != Real(0)) {
-                const Real iden = Real(1) / sqrt_r(beta0);
+                const Real iden = Real(1) / sb0;
                 const Real rbar = A.q_one ? gbar : gbar * A.q * pow(r, A.q - Real(1));
                 const Real numbar = rbar * iden;
                 const Real denbar = -rbar * r * iden;
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
         if (need_lam && gamma != Real(0)) {
             const Real lbar = -z * gamma * Real(1.0 / P);
             const Real ds = lbar * dspeed<FLUX>(A, u_at);
+            const int at_kind = at_code >> 8, at_a = (at_code >> 4) & 15, at_b = at_code & 15;
             if (ds != Real(0)) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
