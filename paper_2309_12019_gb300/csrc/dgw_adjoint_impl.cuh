@@ -102,9 +102,12 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
     }
     const bool need_lam = A.stab != STAB_DG && !A.lam_fixed;
     // maximising Gauss point of |F'(U_h)| (for nu_e): kind 0 volume (qa, qb), 1 face (f, q)
-    // the maximiser as one code, kind * 256 + a * 16 + b (a, b < 16): one select per point
-    Real lam_max = Real(-1), u_at = Real(0);
+    // lambda_e = |F'(U_h)| over the volume and face points is |a| (advection) or |a| |u|
+    // (Burgers): the points are compared by the key |u| (0 for advection) and the
+    // maximiser kept as one code, kind * 256 + a * 16 + b (a, b < 16)
+    Real kmax = Real(-1), u_at = Real(0);
     int at_code = 0;
+    const Real speed_scale = DIM == 1 ? fabs(A.a0) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1);
 
     // ---------------- volume term ----------------
     if (DIM == 1) {
@@ -118,8 +121,8 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
 #pragma unroll
             for (int i = 0; i < N1; ++i) ws[i] = fma(T.B[q][i], s, ws[i]);
             if (need_lam) {
-                const Real sp = FLUX == FLUX_ADVECT ? fabs(A.a0) : fabs(A.a0 * u);
-                if (sp > lam_max) { lam_max = sp; u_at = u; at_code = q * 16; }
+                const Real key = FLUX == FLUX_ADVECT ? Real(0) : fabs(u);
+                if (key > kmax) { kmax = key; u_at = u; at_code = q * 16; }
             }
         }
     } else {
@@ -159,9 +162,8 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
 #pragma unroll
                 for (int i = 0; i < N1; ++i) row[i] = fma(T.B[qa][i], s, row[i]);
                 if (need_lam) {
-                    const Real sp = FLUX == FLUX_ADVECT ? sqrt_r(A.a0 * A.a0 + A.a1 * A.a1)
-                                                        : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1) * fabs(u);
-                    if (sp > lam_max) { lam_max = sp; u_at = u; at_code = qa * 16 + qb; }
+                    const Real key = FLUX == FLUX_ADVECT ? Real(0) : fabs(u);
+                    if (key > kmax) { kmax = key; u_at = u; at_code = qa * 16 + qb; }
                 }
             }
 #pragma unroll
@@ -227,9 +229,8 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
                 en[t] = fma(gn, bt, en[t]);
             }
             if (need_lam) {
-                const Real sp = FLUX == FLUX_ADVECT ? (DIM == 1 ? fabs(A.a0) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1))
-                                                    : (DIM == 1 ? fabs(A.a0 * uo) : sqrt_r(A.a0 * A.a0 + A.a1 * A.a1) * fabs(uo));
-                if (sp > lam_max) { lam_max = sp; u_at = uo; at_code = 256 + f * 16 + q; }
+                const Real key = FLUX == FLUX_ADVECT ? Real(0) : fabs(uo);
+                if (key > kmax) { kmax = key; u_at = uo; at_code = 256 + f * 16 + q; }
             }
         }
 #pragma unroll
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(128, P <= 2 ? 4 : 1) vjp_kernel(const KParams 
         Real z = Real(0);
 #pragma unroll
         for (int k = 0; k < K; ++k) z = fma(v[k], kc[k], z);
+        const Real lam_max = FLUX == FLUX_ADVECT ? speed_scale : speed_scale * kmax;
         const Real lamv = A.lam_fixed ? A.lambda_nu : lam_max;
 
         // sensor forward (Sec. 4), keeping what the reverse sweep needs
